@@ -1,0 +1,329 @@
+#!/usr/bin/env python3
+"""Benchmark: AoA frames/s of the fast-MUSIC hot path at M=512 on GB300.
+
+Workload (one step = one fm_run over a batch): 64 synthetic ULA frames, M=512
+antennas, T=1024 snapshots, K=8 sources uniform in +-60 deg (>= 2 deg apart),
+per-source SNR U(0, 20) dB, l = K + 16 = 24, one power iteration, random
+projection, 15001-point grid over +-75 deg (0.01 deg).  The batch's snapshots
+(268 MB) exceed the 129 MB L2, so no flush is needed between steps.
+
+Printed JSON line (rank 0): value = frames/s of the whole job with inputs
+resident in HBM; e2e = the same through the C ABI with the pinned-host -> device
+copy of X and the device -> host copy of P and the peaks inside the timed
+region; roofline of the dominant kernel from CUDA events on the launching
+stream; full-eig MUSIC on the same GPU (our covariance + torch.linalg.eigh +
+our scan and peaks) for the speed-up; the FP64 oracle timed on the host cores
+as cpu_baseline.  `--impl reference` times the oracle alone as the reference
+arm (bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "AoA frames/s at M=512 (fast-MUSIC vs full-eig MUSIC, same GPU); p99 latency"
+UNIT = "frames/s"
+BATCH = 64
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--method", default="projection", choices=["projection", "sampling"])
+    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--no-baseline", action="store_true", help="skip full-eig MUSIC and the CPU oracle")
+    ap.add_argument("--cpu-sample", type=int, default=3, help="frames of the workload the oracle times")
+    return ap.parse_args()
+
+
+def workload_config(method: str, batch: int):
+    return {"workload": f"ULA M=512 T=1024 K=8 l=24 t=1 L=15001, {batch} frames per step",
+            "method": "random projection (Alg. 2)" if method == "projection" else "random sampling (Alg. 1)",
+            "frames_per_step": batch, "M": 512, "T": 1024, "K": 8, "l": 24, "t": 1, "L": 15001,
+            "l2_flush": "none: inputs (268 MB/step) exceed the 129 MB L2"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def peaks_json():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+def cpu_oracle_rate(frames, method_id, n):
+    """Time the FP64 oracle (single-threaded C) on the first n frames; frames/s."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    for fr in frames[:n]:
+        oracle.frame(fr.X, fr.K, fr.l, fr.t, method_id, 0, fr.frame_id, fr.theta0, fr.step, fr.L)
+    dt = time.perf_counter() - t0
+    return n / dt, dt
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, one frame per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1911_07434_gb300 import synth
+    method_id = 2 if args.method == "projection" else 1
+    n = args.warmup + args.steps
+    wl = synth.massive_mimo_frames(n, seed=0)
+    import oracle
+    oracle.build()
+    times = []
+    for i, fr in enumerate(wl.frames):
+        t0 = time.perf_counter()
+        oracle.frame(fr.X, fr.K, fr.l, fr.t, method_id, 0, fr.frame_id, fr.theta0, fr.step, fr.L)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args.method, args.batch),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one frame of the workload per step, single-threaded FP64 C oracle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1911_07434_gb300 import binding, build, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+
+    method_id = binding.FM_RAND_PROJECTION if args.method == "projection" else binding.FM_RAND_SAMPLING
+    B = args.batch
+    wl = synth.massive_mimo_frames(B, seed=rank)           # each rank: its own frames (weak scaling)
+    for b, fr in enumerate(wl.frames):
+        fr.frame_id = rank * B + b
+    M, T, K, l, t, L = 512, 1024, 8, 24, 1, 15001
+    fr0 = wl.frames[0]
+    Xh = torch.from_numpy(np.stack([fr.X for fr in wl.frames])).pin_memory()
+    X = Xh.to(dev)
+    P = torch.empty((B, L), dtype=torch.float32, device=dev)
+    idx = torch.empty((B, K), dtype=torch.int32, device=dev)
+    deg = torch.empty((B, K), dtype=torch.float32, device=dev)
+    npk = torch.empty(B, dtype=torch.int32, device=dev)
+    status = torch.zeros(B, dtype=torch.int32, device=dev)
+    ctx = binding.Context(device=local)
+    frames = [ctx.frame(X[b], K, l, t, method_id, fr0.theta0, fr0.step, L, P[b], idx[b], deg[b], npk[b:b + 1],
+                        seed=0, frame_id=wl.frames[b].frame_id, status=status[b:b + 1]) for b in range(B)]
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- device-resident timing -------------------------------------------------
+    for _ in range(args.warmup):
+        ctx.run(frames)
+    torch.cuda.synchronize()
+    assert int(status.abs().sum()) == 0, "a frame reported a non-zero status"
+    ctx.stage_times(reset=True)
+    ctx.set_timing(True)
+    launches0 = ctx.launch_count()
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    step_ev[0].record(stream)
+    for k in range(args.steps):
+        ctx.run(frames)
+        step_ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ctx.set_timing(False)
+    launches = ctx.launch_count() - launches0
+    step_ms = [step_ev[k].elapsed_time(step_ev[k + 1]) for k in range(args.steps)]
+    total_ms = step_ev[0].elapsed_time(step_ev[-1])
+    stages = ctx.stage_times(reset=True)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = world * B * args.steps / (total_ms / 1e3)
+
+    # ---- end-to-end through the C ABI (host buffers) ----------------------------
+    Ph = torch.empty((B, L), dtype=torch.float32).pin_memory()
+    idxh = torch.empty((B, K), dtype=torch.int32).pin_memory()
+    degh = torch.empty((B, K), dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, args.steps // 3)
+    for _ in range(2):
+        X.copy_(Xh, non_blocking=True)
+        ctx.run(frames)
+        Ph.copy_(P, non_blocking=True)
+        idxh.copy_(idx, non_blocking=True)
+        degh.copy_(deg, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        X.copy_(Xh, non_blocking=True)
+        ctx.run(frames)
+        Ph.copy_(P, non_blocking=True)
+        idxh.copy_(idx, non_blocking=True)
+        degh.copy_(deg, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = world * B * e2e_steps / e2e_s
+    h2d = Xh.numel() * Xh.element_size()
+    d2h = Ph.numel() * 4 + idxh.numel() * 4 + degh.numel() * 4
+
+    # ---- roofline of the dominant kernel ----------------------------------------
+    pk, pk_kind = peaks_json()
+    names = list(stages.keys())
+    dom = max(names, key=lambda n: stages[n][0])
+    cov_ms, cov_n = stages["covariance"]
+    cov_avg_s = cov_ms / max(cov_n, 1) / 1e3
+    cov_flops = 4.0 * M * M * T * B                  # Hermitian half of X X^H, real flops per launch
+    fp32_peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # TFLOP/s, FFMA pipes
+    roof = {"kernel": "covariance (cov_fp32_kernel)", "bound": "alu", "achieved": cov_flops / cov_avg_s / 1e12,
+            "peak": fp32_peak, "unit": "TFLOP/s", "frac": (cov_flops / cov_avg_s / 1e12) / fp32_peak,
+            "traffic": None, "avg_launch_ms": cov_avg_s * 1e3,
+            "peak_source": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
+                           f"(sm_max_mhz from MEASURED_PEAKS.json, {pk_kind})"}
+    stage_summary = {n: {"ms_per_launch": (stages[n][0] / stages[n][1]) if stages[n][1] else 0.0,
+                         "launches": stages[n][1], "share": stages[n][0] / max(1e-9, sum(v[0] for v in stages.values()))}
+                     for n in names}
+
+    # ---- full-eig MUSIC on the same GPU -----------------------------------------
+    full = None
+    if not args.no_baseline:
+        def full_eig_step():
+            R = ctx.covariance(X)
+            _, V = torch.linalg.eigh(R)                    # cuSOLVER, ascending eigenvalues
+            Uk = V[:, :, -K:].contiguous()
+            Pf = ctx.spectrum(Uk, fr0.theta0, fr0.step, L)
+            return ctx.peaks(Pf, K, fr0.theta0, fr0.step)
+        full_eig_step()
+        torch.cuda.synchronize()
+        fs = 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(fs):
+            full_eig_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fms = e0.elapsed_time(e1) / fs
+        full = {"value": B / (fms / 1e3), "unit": UNIT, "ms_per_step": fms,
+                "method": "standard MUSIC: our covariance kernel + torch.linalg.eigh (cuSOLVER) + our scan/peaks",
+                "speedup_fast_vs_full": (value / world) / (B / (fms / 1e3))}
+
+    # ---- CPU oracle baseline -----------------------------------------------------
+    cpu = None
+    if not args.no_baseline and rank == 0:
+        rate, secs = cpu_oracle_rate(wl.frames, method_id, args.cpu_sample)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_sample} frames of the workload through the single-threaded FP64 C oracle "
+                         f"({secs:.1f} s)"}
+
+    srt = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(args.method, B),
+        "latency_ms": {"p50_step": srt[len(srt) // 2], "p99_step": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": roof, "dominant_stage": dom, "stages": stage_summary,
+        "full_eig_music": full, "cpu_baseline": cpu, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,202 @@
+/*
+ * fastmusic.h -- C ABI of the GB300 (sm_103a) fast-MUSIC angle-of-arrival library.
+ *
+ * The library implements the hot path of arXiv 1911.07434 ("Ultra-Fast
+ * Accurate AoA Estimation via Automotive Massive-MIMO Radar") on one GPU:
+ *
+ *   X (M x T snapshots) --Eq. 2--> R = X X^H / T
+ *     --Alg. 1 / Alg. 2--> sketch C = R Pi (+ t power steps V = orth(C), C = R V)
+ *     --> W = pinv(P^H C), rank restriction B = R_c W R_c^H, eig(B)  (Sec. III)
+ *     --> U_s (M x K signal subspace)
+ *     --Eq. 5 / Eq. 10--> P(theta) = 1 / (||a(theta)||^2 - ||U_s^H a(theta)||^2)
+ *     --Eq. 6--> the K largest local maxima of P (AoAs)
+ *
+ * plus plain full-eigendecomposition MUSIC (Eq. 4-6) as the comparison method.
+ *
+ * Conventions common to every call:
+ *   - Pointers named X, R, U, P, peak_* are DEVICE pointers owned by the caller
+ *     (e.g. torch tensors' data_ptr()).  The library never frees them.
+ *   - Complex values are complex64: interleaved (re, im) float pairs.
+ *     Matrices are row-major; X is M x T with leading dimension ldx (complex
+ *     elements), row = antenna (Sec. II-B, Eq. 3).
+ *   - Every compute call is asynchronous on `stream` (a cudaStream_t; NULL is
+ *     the legacy default stream).  Results are valid after the caller
+ *     synchronises that stream.  Shapes are validated on the host before any
+ *     launch; an invalid call launches nothing and returns FM_ERR_INVALID_ARG.
+ *   - Errors are returned as fm_status; a readable message is available from
+ *     fm_last_error(ctx).  No exception crosses the ABI.
+ *   - Steering vectors are those of a uniform linear array with element
+ *     spacing d_wl wavelengths (0.5 = lambda/2, Sec. II-A):
+ *       a_m(theta) = exp(j 2 pi d_wl m sin theta),  m = 0..M-1,
+ *     theta measured from broadside, grid theta_i = theta0_deg + i * step_deg.
+ *   - The Gaussian test matrix Pi of Sec. III-B is drawn from Philox4x32-10
+ *     (Salmon et al., SC'11) with key (seed_lo, seed_hi) and counter
+ *     (column j, row m, frame_id_lo, frame_id_hi); outputs x0, x1 give
+ *     u1 = (x0+1)/2^32, u2 = x1/2^32 and Pi[m,j] = sqrt(-2 ln u1) e^{j 2 pi u2}.
+ *     The l sampled columns of Alg. 1 come from a partial Fisher-Yates shuffle
+ *     whose draw i uses counter (i, 0xFFFFFFFF, frame_id_lo, frame_id_hi) and
+ *     j = i + floor(x0 (M - i) / 2^32); the indices are then sorted.
+ */
+#ifndef FASTMUSIC_H
+#define FASTMUSIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* fm_stream; /* == cudaStream_t */
+typedef struct fm_ctx fm_ctx;
+
+typedef enum {
+    FM_OK = 0,
+    FM_ERR_INVALID_ARG = 1,    /* shape/pointer validation failed; nothing launched */
+    FM_ERR_CUDA = 2,           /* a CUDA runtime call failed; see fm_last_error */
+    FM_ERR_OOM_BUDGET = 3,     /* the call needs more workspace than the context budget */
+    FM_ERR_NO_CONVERGENCE = 4, /* (per-frame status bit) an eigensolve hit its sweep cap */
+    FM_ERR_TIMEOUT = 5,        /* a bounded wait expired */
+    FM_ERR_NOT_READY = 6       /* serving: ticket unknown or still in flight */
+} fm_status;
+
+typedef enum {
+    FM_FULL_EIG = 0,        /* standard MUSIC, Eq. 4-6 (not served by fm_run; see fm_spectrum) */
+    FM_RAND_SAMPLING = 1,   /* fast MUSIC 1, Sec. III-A, Algorithm 1 */
+    FM_RAND_PROJECTION = 2  /* fast MUSIC 2, Sec. III-B, Algorithm 2 */
+} fm_method;
+
+typedef enum {
+    FM_PREC_FP32 = 0, /* all GEMM-shaped steps with FP32 products and FP32 accumulation */
+    FM_PREC_TF32 = 1, /* reserved: TF32 tensor-core operands, FP32 accumulation */
+    FM_PREC_BF16 = 2  /* reserved: BF16 tensor-core operands, FP32 accumulation */
+} fm_precision;
+
+/* Uniform linear array (Sec. II-A): M elements, spacing d_wl wavelengths (0 => 0.5). */
+typedef struct {
+    int M;
+    double d_wl;
+} fm_array;
+
+/* Angle grid (Sec. II-B): theta_i = theta0_deg + i * step_deg, i = 0..L-1. */
+typedef struct {
+    double theta0_deg;
+    double step_deg;
+    int L;
+} fm_grid;
+
+/* Estimator parameters.  K = number of sources, l = sketch size (the paper's p,
+ * K <= l <= min(M, 64)), t = power iterations (Eq. 11; 0..8).  rank_restrict:
+ * number of columns of U_s used by the scan, K (0 means K) or l.  refine and
+ * prec other than FP32 are reserved and must be 0.  seed keys the Philox
+ * stream of Pi / the sampled index set. */
+typedef struct {
+    int method; /* fm_method */
+    int K;
+    int l;
+    int t;
+    int prec; /* fm_precision */
+    int rank_restrict;
+    int refine;
+    int reserved_;
+    uint64_t seed;
+} fm_params;
+
+/* One radar frame for fm_run.  X: device complex64 M x T (ldx >= T).
+ * Outputs (device, caller-owned): P_out[L] pseudo-spectrum (FP32, +inf where the
+ * denominator is not positive); P_db_out[L] 10 log10 P (nullable); peak_idx[K]
+ * grid indices of the K largest local maxima ordered by P descending (ties:
+ * lower index), -1 for missing; peak_deg[K] their angles; n_peaks[1] number
+ * found; status[1] (nullable) per-frame status bits (0 = ok, FM_ERR_* values
+ * OR-ed as 1 << code). */
+typedef struct {
+    const void* X;
+    int T;
+    int64_t ldx;
+    fm_array arr;
+    fm_grid grid;
+    fm_params p;
+    uint64_t frame_id;
+    float* P_out;
+    float* P_db_out;
+    int* peak_idx;
+    float* peak_deg;
+    int* n_peaks;
+    int* status;
+} fm_frame;
+
+/* ---- context -------------------------------------------------------------
+ * fm_create: make a context on CUDA device `device` (made current for the
+ * calls of this context).  workspace_budget_bytes caps the device workspace
+ * the context may hold (0 = 16 GiB); workspace is allocated lazily, grows on
+ * demand and is owned (and freed) by the context.  Not thread-safe: one
+ * context per host thread. */
+fm_status fm_create(fm_ctx** ctx, size_t workspace_budget_bytes, int device);
+fm_status fm_destroy(fm_ctx* ctx);
+const char* fm_last_error(const fm_ctx* ctx);
+/* Device bytes of workspace fm_run needs for these frames (0 on invalid input). */
+size_t fm_workspace_bytes(const fm_frame* frames, int n_frames);
+
+/* ---- the whole hot path ------------------------------------------------------
+ * fm_run: for every frame, X -> R -> sketch -> U_s -> P -> peaks (Sec. II-III),
+ * asynchronously on `stream`.  Frames may differ in every shape parameter.
+ * method must be FM_RAND_SAMPLING or FM_RAND_PROJECTION. */
+fm_status fm_run(fm_ctx* ctx, const fm_frame* frames, int n_frames, fm_stream stream);
+
+/* ---- steps (uniform batches; each frame at a fixed stride) ------------------
+ * fm_covariance (Eq. 2): R_b = X_b X_b^H / T for b < n_frames.  X_b = X +
+ * b * x_frame_stride complex elements; R_b = R + b*M*M (complex64, full
+ * Hermitian matrix written). */
+fm_status fm_covariance(fm_ctx* ctx, const void* X, int n_frames, int M, int T, int64_t ldx,
+                        int64_t x_frame_stride, void* R, int prec, fm_stream stream);
+
+/* fm_subspace (Alg. 1 / Alg. 2): randomized signal subspace of each R_b
+ * (complex64 M x M at R + b*M*M).  U_b = U + b*M*ncols (complex64, M x ncols,
+ * ncols = p->rank_restrict or K); frame b uses frame_id0 + b for its Philox
+ * stream.  status[b] (nullable) receives the per-frame status bits. */
+fm_status fm_subspace(fm_ctx* ctx, const void* R, int n_frames, int M, const fm_params* p,
+                      uint64_t frame_id0, void* U, int* status, fm_stream stream);
+
+/* fm_spectrum (Eq. 5 / Eq. 10): P_b[i] = 1/(M - ||U_b^H a(theta_i)||^2) for
+ * U_b = U + b*M*ncols (complex64 M x ncols, orthonormal columns), P_b = P + b*L. */
+fm_status fm_spectrum(fm_ctx* ctx, const void* U, int n_frames, int M, int ncols, double d_wl,
+                      const fm_grid* grid, float* P, fm_stream stream);
+
+/* fm_peaks (Eq. 6): K largest local maxima of each P_b (P + b*L); a local
+ * maximum is i with P[i] > P[i-1] and P[i] >= P[i+1] (missing neighbours at the
+ * ends never block).  Outputs at peak_idx + b*K, peak_deg + b*K, n_peaks + b. */
+fm_status fm_peaks(fm_ctx* ctx, const float* P, int n_frames, int L, int K, const fm_grid* grid,
+                   int* peak_idx, float* peak_deg, int* n_peaks, fm_stream stream);
+
+/* fm_test_matrix: the Gaussian Pi (complex64 M x l, row-major) of frame_id. */
+fm_status fm_test_matrix(fm_ctx* ctx, uint64_t seed, uint64_t frame_id, int M, int l, void* Pi,
+                         fm_stream stream);
+/* fm_sample_indices: the sorted index set I (l int32) of Algorithm 1. */
+fm_status fm_sample_indices(fm_ctx* ctx, uint64_t seed, uint64_t frame_id, int M, int l, int* idx,
+                            fm_stream stream);
+
+/* ---- per-stage timing (CUDA events on the launching stream) -----------------
+ * When enabled, every stage launch inside fm_run / step calls is bracketed by
+ * events.  fm_stage_times synchronises on them and returns, per stage, the
+ * summed milliseconds and the number of launches since the last reset.
+ * Stage order: 0 grid table, 1 covariance, 2 sketch, 3 orth, 4 final small
+ * solve, 5 scan, 6 peaks. */
+#define FM_N_STAGES 7
+fm_status fm_set_timing(fm_ctx* ctx, int enable);
+fm_status fm_stage_times(fm_ctx* ctx, double* total_ms, int* launches, int reset);
+/* Number of kernel launches issued by this context since creation. */
+uint64_t fm_launch_count(const fm_ctx* ctx);
+
+/* ---- serving (continuous batching) ------------------------------------------
+ * fm_serve_submit: enqueue one frame; the library admits queued frames into
+ * device work as workspace within the budget frees up, overlapping them on its
+ * own streams.  *ticket identifies the request.  fm_serve_poll sets *done = 1
+ * once the frame's outputs are complete on the device. */
+fm_status fm_serve_submit(fm_ctx* ctx, const fm_frame* frame, uint64_t* ticket);
+fm_status fm_serve_poll(fm_ctx* ctx, uint64_t ticket, int* done);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FASTMUSIC_H */

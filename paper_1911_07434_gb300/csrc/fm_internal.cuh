@@ -1,0 +1,162 @@
+// fm_internal.cuh -- shared device/host definitions of the CUDA path (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fastmusic.h"
+
+namespace fm {
+
+constexpr int kLMax = 64;      // largest sketch size l handled by the small solver
+constexpr int kMMax = 1024;    // largest array size M (scan keeps e^{j pi 64 m1 q}, m1 < 16, in registers)
+constexpr int kKPadMax = 32;   // largest padded K in the scan
+
+// Per-frame descriptor in device memory.  All pointers are device pointers.
+struct FrameDesc {
+    const float2* X;   // M x T, leading dim ldx
+    int64_t ldx;
+    int M, T, K, l, t, method, L, ncols;  // ncols = columns of U_s used by the scan
+    int kpad;          // padded column count of Us (multiple of 4)
+    int pad_;
+    float2* R;         // M x M
+    float2* C;         // M x l  sketch
+    float2* V;         // M x l  basis (power steps) / Q
+    float2* Us;        // M x kpad (zero-padded)
+    int* idx;          // l sampled indices
+    float2* qtab;      // L entries (q_hi, q_lo): q = 2 d_wl sin(theta_i), split for exact m*q_hi
+    float* P;          // L
+    float* Pdb;        // L (nullable)
+    int* peak_idx;     // K
+    float* peak_deg;   // K
+    int* n_peaks;      // 1
+    int* status;       // 1 (nullable)
+    uint64_t seed, frame_id;
+    double theta0, step, d_wl;
+};
+
+// One distinct angle grid: its (q_hi, q_lo) table is shared by every frame using it.
+struct GridDesc {
+    double theta0, step, d_wl;
+    int L, pad_;
+    float2* qtab;
+};
+
+// ---------------------------------------------------------------- complex ----
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+// acc += a * b
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__device__ __forceinline__ void cfmac(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(-a.y, b.x, acc.y);
+}
+// acc += a * conj(b)
+__device__ __forceinline__ void cfmaconj(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(a.y, b.y, acc.x);
+    acc.y = fmaf(a.y, b.x, acc.y);
+    acc.y = fmaf(-a.x, b.y, acc.y);
+}
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+
+// ------------------------------------------------------------ Philox4x32-10 --
+// Salmon, Moraes, Dror, Shaw, SC'11.  Round: (c0..c3) -> (hi(B c2)^c1^k0, lo(B c2),
+// hi(A c0)^c3^k1, lo(A c0)), A = 0xD2511F53, B = 0xCD9E8D57; key += (0x9E3779B9,
+// 0xBB67AE85) between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo_a = 0xD2511F53u * c.x, hi_a = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo_b = 0xCD9E8D57u * c.z, hi_b = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi_b ^ c.y ^ k.x, lo_b, hi_a ^ c.w ^ k.y, lo_a);
+    }
+    return c;
+}
+
+// Entry (m, j) of the Gaussian test matrix of frame `frame_id` (see fastmusic.h).
+__device__ __forceinline__ float2 gaussian_entry(uint64_t seed, uint64_t frame_id, int m, int j) {
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)m, (uint32_t)frame_id,
+                                             (uint32_t)(frame_id >> 32)),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    // ln u1 with u1 = (x0+1)/2^32, evaluated so that it stays relatively accurate
+    // near u1 = 1: there u1 = 1 - v/2^32 with v = 2^32-1-x0 exact, and log1p is used.
+    float lnu1;
+    if (x.x >= 0x80000000u)
+        lnu1 = log1pf(-(float)(0xFFFFFFFFu - x.x) * 2.3283064365386963e-10f);
+    else
+        lnu1 = logf((float)(x.x + 1u) * 2.3283064365386963e-10f);
+    const float u2 = (float)x.y * 2.3283064365386963e-10f;  // x1 / 2^32
+    const float r = sqrtf(-2.0f * lnu1);
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    return make_float2(r * c, r * s);
+}
+
+// Sorted l-subset of {0..M-1} (partial Fisher-Yates), computed by ONE thread.
+// perm: scratch of M ints.
+__device__ inline void sample_indices_serial(uint64_t seed, uint64_t frame_id, int M, int l, int* perm,
+                                             int* out) {
+    for (int m = 0; m < M; ++m) perm[m] = m;
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    for (int i = 0; i < l; ++i) {
+        const uint4 x = philox4x32_10(
+            make_uint4((uint32_t)i, 0xFFFFFFFFu, (uint32_t)frame_id, (uint32_t)(frame_id >> 32)), key);
+        const int j = i + (int)(((uint64_t)x.x * (uint64_t)(M - i)) >> 32);
+        const int tmp = perm[i];
+        perm[i] = perm[j];
+        perm[j] = tmp;
+    }
+    for (int i = 0; i < l; ++i) out[i] = perm[i];
+    for (int i = 1; i < l; ++i) {
+        const int v = out[i];
+        int k = i - 1;
+        while (k >= 0 && out[k] > v) {
+            out[k + 1] = out[k];
+            --k;
+        }
+        out[k + 1] = v;
+    }
+}
+
+// Per-frame status bits.
+__device__ __forceinline__ void set_status(int* status, int code) {
+    if (status) atomicOr(status, 1 << code);
+}
+
+// ---------------------------------------------------------- launch wrappers --
+// Implemented in the .cu files; each returns cudaGetLastError() after launching.
+cudaError_t launch_grid_table(const GridDesc* g, int n_grids, int max_L, cudaStream_t s);
+cudaError_t launch_covariance(const FrameDesc* d, int n_frames, int max_M, cudaStream_t s);
+cudaError_t launch_sketch(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, bool any_gather,
+                          bool any_dense, cudaStream_t s);
+cudaError_t launch_orth(const FrameDesc* d, int n_frames, int max_l, int pass, cudaStream_t s);
+cudaError_t launch_final(const FrameDesc* d, int n_frames, int max_l, cudaStream_t s);
+cudaError_t launch_scan(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s);
+cudaError_t launch_peaks(const FrameDesc* d, int n_frames, int max_K, cudaStream_t s);
+cudaError_t launch_test_matrix(uint64_t seed, uint64_t frame_id, int M, int l, float2* out, cudaStream_t s);
+cudaError_t launch_sample_indices(uint64_t seed, uint64_t frame_id, int M, int l, int* out, cudaStream_t s);
+size_t small_smem_bytes(int l);
+
+}  // namespace fm

@@ -1,0 +1,776 @@
+// host.cu -- C ABI of the library: context, validation, workspace planning,
+// launch sequencing, per-stage timing and the continuous-batching server.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "fm_internal.cuh"
+
+using fm::FrameDesc;
+using fm::GridDesc;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t aup(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+enum Stage { kStGrid = 0, kStCov, kStSketch, kStOrth, kStFinal, kStScan, kStPeaks };
+
+struct TimedEvent {
+    int stage;
+    cudaEvent_t a, b;
+};
+
+struct ServeReq;
+
+}  // namespace
+
+struct fm_ctx {
+    int device = 0;
+    size_t budget = 0;
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
+    char* pinned = nullptr;
+    size_t pinned_bytes = 0;
+    cudaEvent_t staging_done = nullptr;
+    bool staging_pending = false;
+    std::string err;
+    bool timing = false;
+    std::vector<TimedEvent> pending;
+    std::vector<cudaEvent_t> pool;
+    double stage_ms[FM_N_STAGES] = {};
+    int stage_n[FM_N_STAGES] = {};
+    uint64_t launches = 0;
+    // serving state
+    struct Slot;
+    std::vector<Slot*> slots;
+    std::deque<std::pair<uint64_t, fm_frame>> queue;
+    std::map<uint64_t, int> done;  // ticket -> 1 when complete
+    uint64_t next_ticket = 1;
+    uint64_t serve_launches = 0;
+};
+
+struct fm_ctx::Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    fm_ctx* sub = nullptr;  // a private context (own arena and staging) per slot
+    uint64_t ticket = 0;
+    bool busy = false;
+};
+
+namespace {
+
+fm_status fail(fm_ctx* c, fm_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return s;
+}
+
+fm_status cuda_fail(fm_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, FM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+cudaEvent_t get_event(fm_ctx* c) {
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Run one stage launch, bracketed by events when timing is on.
+template <typename F>
+fm_status stage(fm_ctx* c, int st, cudaStream_t s, F&& launch) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c->timing) {
+        a = get_event(c);
+        b = get_event(c);
+        cudaEventRecord(a, s);
+    }
+    cudaError_t e = launch();
+    if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+    c->launches++;
+    if (c->timing) {
+        cudaEventRecord(b, s);
+        c->pending.push_back({st, a, b});
+    }
+    return FM_OK;
+}
+
+fm_status set_device(fm_ctx* c) {
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return FM_OK;
+}
+
+fm_status ensure_arena(fm_ctx* c, size_t need) {
+    if (need <= c->arena_bytes) return FM_OK;
+    if (need > c->budget)
+        return fail(c, FM_ERR_OOM_BUDGET, "workspace of %zu bytes exceeds the context budget of %zu bytes", need,
+                    c->budget);
+    if (c->arena) {
+        cudaError_t e = cudaDeviceSynchronize();  // the old arena may still be read by queued work
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaDeviceSynchronize");
+        cudaFree(c->arena);
+        c->arena = nullptr;
+        c->arena_bytes = 0;
+    }
+    size_t sz = std::min(c->budget, std::max(need, need + need / 4));
+    cudaError_t e = cudaMalloc(&c->arena, sz);
+    if (e != cudaSuccess) {
+        c->arena = nullptr;
+        return cuda_fail(c, e, "cudaMalloc(workspace)");
+    }
+    c->arena_bytes = sz;
+    return FM_OK;
+}
+
+// Pinned staging for descriptor uploads; waits for the previous upload first.
+fm_status staging(fm_ctx* c, size_t need, char** out) {
+    if (c->staging_pending) {
+        cudaEventSynchronize(c->staging_done);
+        c->staging_pending = false;
+    }
+    if (need > c->pinned_bytes) {
+        if (c->pinned) cudaFreeHost(c->pinned);
+        size_t sz = std::max(need, (size_t)1 << 16);
+        cudaError_t e = cudaMallocHost(&c->pinned, sz);
+        if (e != cudaSuccess) {
+            c->pinned = nullptr;
+            c->pinned_bytes = 0;
+            return cuda_fail(c, e, "cudaMallocHost(staging)");
+        }
+        c->pinned_bytes = sz;
+    }
+    *out = c->pinned;
+    return FM_OK;
+}
+
+fm_status upload(fm_ctx* c, const char* host, char* dev, size_t bytes, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync(descriptors)");
+    if (!c->staging_done) cudaEventCreateWithFlags(&c->staging_done, cudaEventDisableTiming);
+    cudaEventRecord(c->staging_done, s);
+    c->staging_pending = true;
+    return FM_OK;
+}
+
+int ncols_of(const fm_params& p) {
+    return (p.rank_restrict == p.l) ? p.l : p.K;
+}
+
+const char* check_frame(const fm_frame& f) {
+    const fm_params& p = f.p;
+    const int M = f.arr.M;
+    if (!f.X) return "X is NULL";
+    if (M < 2 || M > fm::kMMax) return "M must be in [2, 1024]";
+    if (f.T < 1) return "T must be >= 1";
+    if (f.ldx < f.T) return "ldx must be >= T";
+    if (!(f.arr.d_wl >= 0.0 && f.arr.d_wl <= 1.0)) return "d_wl must be in (0, 1] (0 selects 0.5)";
+    if (f.grid.L < 1 || f.grid.L > 65536) return "grid L must be in [1, 65536]";
+    if (!std::isfinite(f.grid.theta0_deg) || !std::isfinite(f.grid.step_deg)) return "grid is not finite";
+    if (p.method != FM_RAND_SAMPLING && p.method != FM_RAND_PROJECTION) return "method must be 1 or 2";
+    if (p.K < 1 || p.K > p.l) return "need 1 <= K <= l";
+    if (p.l > M || p.l > fm::kLMax) return "need l <= min(M, 64)";
+    if (p.t < 0 || p.t > 8) return "t must be in [0, 8]";
+    if (p.prec != FM_PREC_FP32) return "only FM_PREC_FP32 is available";
+    if (p.refine != 0) return "refine is reserved";
+    if (p.rank_restrict != 0 && p.rank_restrict != p.K && p.rank_restrict != p.l) return "rank_restrict must be 0, K or l";
+    const int nc = ncols_of(p);
+    if (nc > fm::kKPadMax) return "columns of U_s used by the scan must be <= 32";
+    if ((size_t)M * (size_t)((nc + 3) / 4 * 4) > 24576) return "M * ceil4(ncols) must be <= 24576";
+    if (!f.P_out || !f.peak_idx || !f.peak_deg || !f.n_peaks) return "an output pointer is NULL";
+    return nullptr;
+}
+
+struct Plan {
+    size_t desc_off, grid_off, total;
+    std::vector<size_t> R, C, V, Us, idx;  // per-frame offsets (R == SIZE_MAX: caller-owned)
+    std::vector<int> grid_of;
+    std::vector<GridDesc> grids;
+    std::vector<size_t> qtab;
+};
+
+typedef std::tuple<double, double, double, int> GridKey;
+
+// Lays out the workspace for n frames.  need_R etc. say which buffers live in the workspace.
+Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool need_Us, bool need_grid) {
+    Plan pl;
+    size_t off = 0;
+    pl.desc_off = off;
+    off = aup(off + sizeof(FrameDesc) * (size_t)n);
+    std::map<GridKey, int> gmap;
+    pl.grid_of.assign(n, -1);
+    if (need_grid) {
+        for (int b = 0; b < n; ++b) {
+            const double d = f[b].arr.d_wl > 0.0 ? f[b].arr.d_wl : 0.5;
+            GridKey k(f[b].grid.theta0_deg, f[b].grid.step_deg, d, f[b].grid.L);
+            auto it = gmap.find(k);
+            if (it == gmap.end()) {
+                const int g = (int)pl.grids.size();
+                gmap[k] = g;
+                GridDesc gd{};
+                gd.theta0 = f[b].grid.theta0_deg;
+                gd.step = f[b].grid.step_deg;
+                gd.d_wl = d;
+                gd.L = f[b].grid.L;
+                pl.grids.push_back(gd);
+                pl.grid_of[b] = g;
+            } else {
+                pl.grid_of[b] = it->second;
+            }
+        }
+    }
+    pl.grid_off = off;
+    off = aup(off + sizeof(GridDesc) * pl.grids.size());
+    for (size_t g = 0; g < pl.grids.size(); ++g) {
+        pl.qtab.push_back(off);
+        off = aup(off + sizeof(float2) * (size_t)pl.grids[g].L);
+    }
+    for (int b = 0; b < n; ++b) {
+        const size_t M = (size_t)f[b].arr.M, l = (size_t)f[b].p.l;
+        pl.R.push_back(need_R ? off : SIZE_MAX);
+        if (need_R) off = aup(off + sizeof(float2) * M * M);
+        pl.C.push_back(need_sketch ? off : SIZE_MAX);
+        if (need_sketch) off = aup(off + sizeof(float2) * M * l);
+        pl.V.push_back(need_sketch ? off : SIZE_MAX);
+        if (need_sketch) off = aup(off + sizeof(float2) * M * l);
+        pl.idx.push_back(need_sketch ? off : SIZE_MAX);
+        if (need_sketch) off = aup(off + sizeof(int) * l);
+        const size_t nc = (size_t)ncols_of(f[b].p);
+        pl.Us.push_back(need_Us ? off : SIZE_MAX);
+        if (need_Us) off = aup(off + sizeof(float2) * M * nc);
+    }
+    pl.total = off;
+    return pl;
+}
+
+FrameDesc make_desc(const fm_frame& f) {
+    FrameDesc d{};
+    d.X = reinterpret_cast<const float2*>(f.X);
+    d.ldx = f.ldx;
+    d.M = f.arr.M;
+    d.T = f.T;
+    d.K = f.p.K;
+    d.l = f.p.l;
+    d.t = f.p.t;
+    d.method = f.p.method;
+    d.L = f.grid.L;
+    d.ncols = ncols_of(f.p);
+    d.kpad = d.ncols;
+    d.P = f.P_out;
+    d.Pdb = f.P_db_out;
+    d.peak_idx = f.peak_idx;
+    d.peak_deg = f.peak_deg;
+    d.n_peaks = f.n_peaks;
+    d.status = f.status;
+    d.seed = f.p.seed;
+    d.frame_id = f.frame_id;
+    d.theta0 = f.grid.theta0_deg;
+    d.step = f.grid.step_deg;
+    d.d_wl = f.arr.d_wl > 0.0 ? f.arr.d_wl : 0.5;
+    return d;
+}
+
+struct Maxes {
+    int M = 0, l = 0, L = 0, K = 0, kpad = 0, t = 0;
+    bool any_sampling = false, any_projection = false, any_status = false;
+};
+
+Maxes maxes_of(const std::vector<FrameDesc>& ds) {
+    Maxes m;
+    for (const FrameDesc& d : ds) {
+        m.M = std::max(m.M, d.M);
+        m.l = std::max(m.l, d.l);
+        m.L = std::max(m.L, d.L);
+        m.K = std::max(m.K, d.K);
+        m.kpad = std::max(m.kpad, d.kpad);
+        m.t = std::max(m.t, d.t);
+        m.any_sampling |= d.method == FM_RAND_SAMPLING;
+        m.any_projection |= d.method == FM_RAND_PROJECTION;
+        m.any_status |= d.status != nullptr;
+    }
+    return m;
+}
+
+// Uploads descriptors (+ grids) and returns device pointers.
+fm_status upload_descs(fm_ctx* c, const Plan& pl, std::vector<FrameDesc>& ds, cudaStream_t s, FrameDesc** dd,
+                       GridDesc** dg) {
+    const size_t bytes = pl.grid_off + sizeof(GridDesc) * pl.grids.size();
+    char* host = nullptr;
+    fm_status st = staging(c, bytes, &host);
+    if (st != FM_OK) return st;
+    memcpy(host + pl.desc_off, ds.data(), sizeof(FrameDesc) * ds.size());
+    std::vector<GridDesc> g = pl.grids;
+    for (size_t i = 0; i < g.size(); ++i) g[i].qtab = reinterpret_cast<float2*>(c->arena + pl.qtab[i]);
+    if (!g.empty()) memcpy(host + pl.grid_off, g.data(), sizeof(GridDesc) * g.size());
+    st = upload(c, host, c->arena, bytes, s);
+    if (st != FM_OK) return st;
+    *dd = reinterpret_cast<FrameDesc*>(c->arena + pl.desc_off);
+    *dg = reinterpret_cast<GridDesc*>(c->arena + pl.grid_off);
+    return FM_OK;
+}
+
+// The fast-MUSIC chain from R (already formed) to U_s.
+fm_status run_subspace_chain(fm_ctx* c, FrameDesc* dd, int n, const Maxes& mx, cudaStream_t s) {
+    fm_status st = stage(c, kStSketch, s, [&] {
+        return fm::launch_sketch(dd, n, mx.M, mx.l, 0, mx.any_sampling, mx.any_projection, s);
+    });
+    if (st != FM_OK) return st;
+    for (int p = 1; p <= mx.t; ++p) {
+        st = stage(c, kStOrth, s, [&] { return fm::launch_orth(dd, n, mx.l, p, s); });
+        if (st != FM_OK) return st;
+        st = stage(c, kStSketch, s, [&] { return fm::launch_sketch(dd, n, mx.M, mx.l, p, false, true, s); });
+        if (st != FM_OK) return st;
+    }
+    return stage(c, kStFinal, s, [&] { return fm::launch_final(dd, n, mx.l, s); });
+}
+
+}  // namespace
+
+// =================================================================== ABI ====
+extern "C" {
+
+fm_status fm_create(fm_ctx** ctx, size_t workspace_budget_bytes, int device) {
+    if (!ctx) return FM_ERR_INVALID_ARG;
+    *ctx = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FM_ERR_CUDA;
+    fm_ctx* c = new fm_ctx();
+    c->device = device;
+    c->budget = workspace_budget_bytes ? workspace_budget_bytes : ((size_t)16 << 30);
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete c;
+        return FM_ERR_CUDA;
+    }
+    *ctx = c;
+    return FM_OK;
+}
+
+fm_status fm_destroy(fm_ctx* c) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    for (fm_ctx::Slot* sl : c->slots) {
+        if (sl->stream) cudaStreamSynchronize(sl->stream);
+        if (sl->ev) cudaEventDestroy(sl->ev);
+        if (sl->stream) cudaStreamDestroy(sl->stream);
+        if (sl->sub) fm_destroy(sl->sub);
+        delete sl;
+    }
+    if (c->staging_done) {
+        cudaEventSynchronize(c->staging_done);
+        cudaEventDestroy(c->staging_done);
+    }
+    for (TimedEvent& t : c->pending) {
+        cudaEventSynchronize(t.b);
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+    if (c->arena) {
+        cudaDeviceSynchronize();
+        cudaFree(c->arena);
+    }
+    if (c->pinned) cudaFreeHost(c->pinned);
+    delete c;
+    return FM_OK;
+}
+
+const char* fm_last_error(const fm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+size_t fm_workspace_bytes(const fm_frame* frames, int n) {
+    if (!frames || n < 1) return 0;
+    for (int b = 0; b < n; ++b)
+        if (check_frame(frames[b])) return 0;
+    return plan_frames(frames, n, true, true, true, true).total;
+}
+
+fm_status fm_run(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (!frames || n < 1) return fail(c, FM_ERR_INVALID_ARG, "no frames");
+    for (int b = 0; b < n; ++b) {
+        const char* why = check_frame(frames[b]);
+        if (why) return fail(c, FM_ERR_INVALID_ARG, "frame %d: %s", b, why);
+    }
+    fm_status st = set_device(c);
+    if (st != FM_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Plan pl = plan_frames(frames, n, true, true, true, true);
+    st = ensure_arena(c, pl.total);
+    if (st != FM_OK) return st;
+    std::vector<FrameDesc> ds(n);
+    for (int b = 0; b < n; ++b) {
+        FrameDesc d = make_desc(frames[b]);
+        d.R = reinterpret_cast<float2*>(c->arena + pl.R[b]);
+        d.C = reinterpret_cast<float2*>(c->arena + pl.C[b]);
+        d.V = reinterpret_cast<float2*>(c->arena + pl.V[b]);
+        d.idx = reinterpret_cast<int*>(c->arena + pl.idx[b]);
+        d.Us = reinterpret_cast<float2*>(c->arena + pl.Us[b]);
+        d.qtab = reinterpret_cast<float2*>(c->arena + pl.qtab[pl.grid_of[b]]);
+        ds[b] = d;
+    }
+    FrameDesc* dd;
+    GridDesc* dg;
+    st = upload_descs(c, pl, ds, s, &dd, &dg);
+    if (st != FM_OK) return st;
+    const Maxes mx = maxes_of(ds);
+    const int ng = (int)pl.grids.size();
+    st = stage(c, kStGrid, s, [&] { return fm::launch_grid_table(dg, ng, mx.L, s); });
+    if (st != FM_OK) return st;
+    st = stage(c, kStCov, s, [&] { return fm::launch_covariance(dd, n, mx.M, s); });
+    if (st != FM_OK) return st;
+    st = run_subspace_chain(c, dd, n, mx, s);
+    if (st != FM_OK) return st;
+    st = stage(c, kStScan, s, [&] { return fm::launch_scan(dd, n, mx.L, mx.M, mx.kpad, s); });
+    if (st != FM_OK) return st;
+    return stage(c, kStPeaks, s, [&] { return fm::launch_peaks(dd, n, mx.K, s); });
+}
+
+fm_status fm_covariance(fm_ctx* c, const void* X, int n, int M, int T, int64_t ldx, int64_t xstride, void* R,
+                        int prec, fm_stream stream) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (!X || !R || n < 1 || M < 1 || M > 65536 || T < 1 || ldx < T || xstride < (int64_t)(M - 1) * ldx + T)
+        return fail(c, FM_ERR_INVALID_ARG, "fm_covariance: invalid shape or pointer");
+    if (prec != FM_PREC_FP32) return fail(c, FM_ERR_INVALID_ARG, "fm_covariance: only FM_PREC_FP32 is available");
+    fm_status st = set_device(c);
+    if (st != FM_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t bytes = aup(sizeof(FrameDesc) * (size_t)n);
+    st = ensure_arena(c, bytes);
+    if (st != FM_OK) return st;
+    std::vector<FrameDesc> ds(n);
+    for (int b = 0; b < n; ++b) {
+        FrameDesc d{};
+        d.X = reinterpret_cast<const float2*>(X) + (int64_t)b * xstride;
+        d.ldx = ldx;
+        d.M = M;
+        d.T = T;
+        d.R = reinterpret_cast<float2*>(R) + (int64_t)b * M * M;
+        ds[b] = d;
+    }
+    char* host = nullptr;
+    st = staging(c, bytes, &host);
+    if (st != FM_OK) return st;
+    memcpy(host, ds.data(), sizeof(FrameDesc) * n);
+    st = upload(c, host, c->arena, sizeof(FrameDesc) * n, s);
+    if (st != FM_OK) return st;
+    FrameDesc* dd = reinterpret_cast<FrameDesc*>(c->arena);
+    return stage(c, kStCov, s, [&] { return fm::launch_covariance(dd, n, M, s); });
+}
+
+fm_status fm_subspace(fm_ctx* c, const void* R, int n, int M, const fm_params* p, uint64_t frame_id0, void* U,
+                      int* status, fm_stream stream) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (!R || !U || !p || n < 1) return fail(c, FM_ERR_INVALID_ARG, "fm_subspace: NULL argument");
+    std::vector<fm_frame> fr(n);
+    for (int b = 0; b < n; ++b) {
+        fm_frame f{};
+        f.X = R;  // placeholder for validation only
+        f.T = 1;
+        f.ldx = 1;
+        f.arr.M = M;
+        f.arr.d_wl = 0.5;
+        f.grid.L = 1;
+        f.grid.step_deg = 1.0;
+        f.p = *p;
+        f.frame_id = frame_id0 + (uint64_t)b;
+        f.P_out = reinterpret_cast<float*>(U);
+        f.peak_idx = status ? status : reinterpret_cast<int*>(U);
+        f.peak_deg = f.P_out;
+        f.n_peaks = f.peak_idx;
+        const char* why = check_frame(f);
+        if (why) return fail(c, FM_ERR_INVALID_ARG, "fm_subspace: %s", why);
+        fr[b] = f;
+    }
+    fm_status st = set_device(c);
+    if (st != FM_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Plan pl = plan_frames(fr.data(), n, false, true, false, false);
+    st = ensure_arena(c, pl.total);
+    if (st != FM_OK) return st;
+    const int nc = ncols_of(*p);
+    std::vector<FrameDesc> ds(n);
+    for (int b = 0; b < n; ++b) {
+        FrameDesc d = make_desc(fr[b]);
+        d.X = nullptr;
+        d.P = nullptr;
+        d.peak_idx = nullptr;
+        d.peak_deg = nullptr;
+        d.n_peaks = nullptr;
+        d.status = status ? status + b : nullptr;
+        d.R = const_cast<float2*>(reinterpret_cast<const float2*>(R)) + (int64_t)b * M * M;
+        d.C = reinterpret_cast<float2*>(c->arena + pl.C[b]);
+        d.V = reinterpret_cast<float2*>(c->arena + pl.V[b]);
+        d.idx = reinterpret_cast<int*>(c->arena + pl.idx[b]);
+        d.Us = reinterpret_cast<float2*>(U) + (int64_t)b * M * nc;
+        ds[b] = d;
+    }
+    if (status) {
+        cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int) * (size_t)n, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync(status)");
+    }
+    FrameDesc* dd;
+    GridDesc* dg;
+    st = upload_descs(c, pl, ds, s, &dd, &dg);
+    if (st != FM_OK) return st;
+    return run_subspace_chain(c, dd, n, maxes_of(ds), s);
+}
+
+fm_status fm_spectrum(fm_ctx* c, const void* U, int n, int M, int ncols, double d_wl, const fm_grid* grid, float* P,
+                      fm_stream stream) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (!U || !grid || !P || n < 1 || M < 1 || M > fm::kMMax || ncols < 1 || ncols > fm::kKPadMax ||
+        (size_t)M * (size_t)((ncols + 3) / 4 * 4) > 24576 || grid->L < 1 || grid->L > 65536 ||
+        !(d_wl >= 0.0 && d_wl <= 1.0))
+        return fail(c, FM_ERR_INVALID_ARG, "fm_spectrum: invalid shape or pointer");
+    fm_status st = set_device(c);
+    if (st != FM_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<fm_frame> fr(n);
+    for (int b = 0; b < n; ++b) {
+        fm_frame f{};
+        f.arr.M = M;
+        f.arr.d_wl = d_wl;
+        f.grid = *grid;
+        f.p.K = ncols;
+        f.p.l = ncols;
+        fr[b] = f;
+    }
+    Plan pl = plan_frames(fr.data(), n, false, false, false, true);
+    st = ensure_arena(c, pl.total);
+    if (st != FM_OK) return st;
+    std::vector<FrameDesc> ds(n);
+    for (int b = 0; b < n; ++b) {
+        FrameDesc d = make_desc(fr[b]);
+        d.ncols = d.kpad = ncols;
+        d.Us = const_cast<float2*>(reinterpret_cast<const float2*>(U)) + (int64_t)b * M * ncols;
+        d.P = P + (int64_t)b * grid->L;
+        d.qtab = reinterpret_cast<float2*>(c->arena + pl.qtab[pl.grid_of[b]]);
+        ds[b] = d;
+    }
+    FrameDesc* dd;
+    GridDesc* dg;
+    st = upload_descs(c, pl, ds, s, &dd, &dg);
+    if (st != FM_OK) return st;
+    const Maxes mx = maxes_of(ds);
+    st = stage(c, kStGrid, s, [&] { return fm::launch_grid_table(dg, (int)pl.grids.size(), mx.L, s); });
+    if (st != FM_OK) return st;
+    return stage(c, kStScan, s, [&] { return fm::launch_scan(dd, n, mx.L, mx.M, mx.kpad, s); });
+}
+
+fm_status fm_peaks(fm_ctx* c, const float* P, int n, int L, int K, const fm_grid* grid, int* peak_idx,
+                   float* peak_deg, int* n_peaks, fm_stream stream) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (!P || !grid || !peak_idx || !peak_deg || !n_peaks || n < 1 || L < 1 || L > 65536 || K < 1)
+        return fail(c, FM_ERR_INVALID_ARG, "fm_peaks: invalid shape or pointer");
+    fm_status st = set_device(c);
+    if (st != FM_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t bytes = aup(sizeof(FrameDesc) * (size_t)n);
+    st = ensure_arena(c, bytes);
+    if (st != FM_OK) return st;
+    std::vector<FrameDesc> ds(n);
+    for (int b = 0; b < n; ++b) {
+        FrameDesc d{};
+        d.L = L;
+        d.K = K;
+        d.P = const_cast<float*>(P) + (int64_t)b * L;
+        d.peak_idx = peak_idx + (int64_t)b * K;
+        d.peak_deg = peak_deg + (int64_t)b * K;
+        d.n_peaks = n_peaks + b;
+        d.theta0 = grid->theta0_deg;
+        d.step = grid->step_deg;
+        ds[b] = d;
+    }
+    char* host = nullptr;
+    st = staging(c, bytes, &host);
+    if (st != FM_OK) return st;
+    memcpy(host, ds.data(), sizeof(FrameDesc) * n);
+    st = upload(c, host, c->arena, sizeof(FrameDesc) * n, s);
+    if (st != FM_OK) return st;
+    FrameDesc* dd = reinterpret_cast<FrameDesc*>(c->arena);
+    return stage(c, kStPeaks, s, [&] { return fm::launch_peaks(dd, n, K, s); });
+}
+
+fm_status fm_test_matrix(fm_ctx* c, uint64_t seed, uint64_t frame_id, int M, int l, void* Pi, fm_stream stream) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (!Pi || M < 1 || l < 1) return fail(c, FM_ERR_INVALID_ARG, "fm_test_matrix: invalid argument");
+    fm_status st = set_device(c);
+    if (st != FM_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = fm::launch_test_matrix(seed, frame_id, M, l, reinterpret_cast<float2*>(Pi), s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "test matrix launch");
+    c->launches++;
+    return FM_OK;
+}
+
+fm_status fm_sample_indices(fm_ctx* c, uint64_t seed, uint64_t frame_id, int M, int l, int* idx, fm_stream stream) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (!idx || M < 1 || M > 65536 || l < 1 || l > M)
+        return fail(c, FM_ERR_INVALID_ARG, "fm_sample_indices: invalid argument");
+    fm_status st = set_device(c);
+    if (st != FM_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = fm::launch_sample_indices(seed, frame_id, M, l, idx, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sample indices launch");
+    c->launches++;
+    return FM_OK;
+}
+
+fm_status fm_set_timing(fm_ctx* c, int enable) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    c->timing = enable != 0;
+    return FM_OK;
+}
+
+fm_status fm_stage_times(fm_ctx* c, double* total_ms, int* launches, int reset) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    for (TimedEvent& t : c->pending) {
+        cudaError_t e = cudaEventSynchronize(t.b);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize(stage)");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t.a, t.b);
+        c->stage_ms[t.stage] += ms;
+        c->stage_n[t.stage] += 1;
+        c->pool.push_back(t.a);
+        c->pool.push_back(t.b);
+    }
+    c->pending.clear();
+    for (int i = 0; i < FM_N_STAGES; ++i) {
+        if (total_ms) total_ms[i] = c->stage_ms[i];
+        if (launches) launches[i] = c->stage_n[i];
+    }
+    if (reset) {
+        for (int i = 0; i < FM_N_STAGES; ++i) {
+            c->stage_ms[i] = 0.0;
+            c->stage_n[i] = 0;
+        }
+    }
+    return FM_OK;
+}
+
+uint64_t fm_launch_count(const fm_ctx* c) { return c ? c->launches + c->serve_launches : 0; }
+
+// ------------------------------------------------------------ serving ----
+// Continuous batching: each admitted frame runs the whole chain on one of a
+// fixed set of slots (stream + private workspace).  Admission happens when a
+// slot is free and the frame's workspace fits into what is left of the budget;
+// frames that arrive while others are running overlap with them on the device.
+static size_t serve_held(const fm_ctx* c) {
+    size_t held = 0;
+    for (const fm_ctx::Slot* sl : c->slots) held += sl->sub ? sl->sub->arena_bytes : 0;
+    return held;
+}
+
+static void serve_progress(fm_ctx* c) {
+    // retire finished slots
+    for (fm_ctx::Slot* sl : c->slots) {
+        if (sl->busy && cudaEventQuery(sl->ev) == cudaSuccess) {
+            c->done[sl->ticket] = 1;
+            sl->busy = false;
+        }
+    }
+    // admit in arrival order while a slot is free and the workspace fits the budget
+    while (!c->queue.empty()) {
+        const fm_frame& f = c->queue.front().second;
+        const size_t need = fm_workspace_bytes(&f, 1);
+        fm_ctx::Slot* pick = nullptr;
+        for (fm_ctx::Slot* sl : c->slots)  // a free slot whose workspace already fits
+            if (!sl->busy && sl->sub->arena_bytes >= need) {
+                pick = sl;
+                break;
+            }
+        if (!pick) {
+            const size_t grow = need + need / 4;
+            for (fm_ctx::Slot* sl : c->slots)  // a free slot that may grow
+                if (!sl->busy && serve_held(c) - sl->sub->arena_bytes + grow <= c->budget) {
+                    pick = sl;
+                    break;
+                }
+            if (!pick && c->slots.size() < 16 && serve_held(c) + grow <= c->budget) {
+                fm_ctx::Slot* sl = new fm_ctx::Slot();
+                if (cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&sl->ev, cudaEventDisableTiming) != cudaSuccess ||
+                    fm_create(&sl->sub, c->budget, c->device) != FM_OK) {
+                    delete sl;
+                    break;
+                }
+                c->slots.push_back(sl);
+                pick = sl;
+            }
+        }
+        if (!pick) break;  // wait for a slot or for memory
+        const uint64_t ticket = c->queue.front().first;
+        fm_status st = fm_run(pick->sub, &f, 1, reinterpret_cast<fm_stream>(pick->stream));
+        c->queue.pop_front();
+        if (st != FM_OK) {
+            c->err = pick->sub->err;
+            c->done[ticket] = -1;
+            continue;
+        }
+        cudaEventRecord(pick->ev, pick->stream);
+        pick->ticket = ticket;
+        pick->busy = true;
+    }
+    uint64_t n = 0;
+    for (fm_ctx::Slot* sl : c->slots) n += sl->sub->launches;
+    c->serve_launches = n;
+}
+
+fm_status fm_serve_submit(fm_ctx* c, const fm_frame* frame, uint64_t* ticket) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (!frame || !ticket) return fail(c, FM_ERR_INVALID_ARG, "fm_serve_submit: NULL argument");
+    const char* why = check_frame(*frame);
+    if (why) return fail(c, FM_ERR_INVALID_ARG, "fm_serve_submit: %s", why);
+    if (fm_workspace_bytes(frame, 1) > c->budget)
+        return fail(c, FM_ERR_OOM_BUDGET, "fm_serve_submit: frame needs more workspace than the budget");
+    fm_status st = set_device(c);
+    if (st != FM_OK) return st;
+    *ticket = c->next_ticket++;
+    c->queue.push_back({*ticket, *frame});
+    serve_progress(c);
+    return FM_OK;
+}
+
+fm_status fm_serve_poll(fm_ctx* c, uint64_t ticket, int* done) {
+    if (!c || !done) return FM_ERR_INVALID_ARG;
+    fm_status st = set_device(c);
+    if (st != FM_OK) return st;
+    serve_progress(c);
+    auto it = c->done.find(ticket);
+    if (it == c->done.end()) {
+        *done = 0;
+        for (auto& q : c->queue)
+            if (q.first == ticket) return FM_OK;
+        for (fm_ctx::Slot* sl : c->slots)
+            if (sl->busy && sl->ticket == ticket) return FM_OK;
+        return fail(c, FM_ERR_NOT_READY, "unknown ticket %llu", (unsigned long long)ticket);
+    }
+    if (it->second < 0) {
+        c->done.erase(it);
+        *done = 1;
+        return FM_ERR_CUDA;
+    }
+    *done = 1;
+    c->done.erase(it);
+    return FM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// scan.cu -- MUSIC pseudo-spectrum on the angle grid (Eq. 5 / Eq. 10):
+//   P(theta_i) = 1 / (||a(theta_i)||^2 - ||U_s^H a(theta_i)||^2),
+//   a_m(theta) = exp(j pi m q),  q = 2 d_wl sin(theta),  ||a||^2 = M.
+//
+// Steering vectors are generated in registers, never stored: each thread owns
+// one angle, splits m = 64 m1 + m0 and forms a_m = c_{m1} b_{m0} with
+// c_{m1} = e^{j pi 64 m1 q} (kept in registers) and b_{m0} = e^{j pi m0 q}
+// (one sincospi per m0).  Every phase m*q is reduced exactly: q = q_hi + q_lo
+// with q_hi a multiple of 2^-11 (so m*q_hi is exact in FP32 for m < 2^11 and
+// can be reduced mod 2 without error) and m*q_lo added after reduction.  The
+// q split is produced once per distinct grid by grid_table_kernel in FP64.
+// U_s (M x kpad) sits in shared memory and is read as warp-wide broadcasts.
+#include <float.h>
+
+#include "fm_internal.cuh"
+
+namespace fm {
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void grid_table_kernel(const GridDesc* __restrict__ grids) {
+    const GridDesc g = grids[blockIdx.y];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.L) return;
+    const double th = (g.theta0 + (double)i * g.step) * (3.14159265358979323846 / 180.0);
+    const double q = 2.0 * g.d_wl * sin(th);
+    const double qh = rint(q * 2048.0) / 2048.0;
+    g.qtab[i] = make_float2((float)qh, (float)(q - qh));
+}
+
+// e^{j pi (m*q)} with the exact reduction described above.
+__device__ __forceinline__ float2 steer(int m, float qh, float ql) {
+    const float x = (float)m * qh;               // exact
+    const float r = x - 2.0f * rintf(0.5f * x);  // exact, in [-1, 1]
+    const float ph = fmaf((float)m, ql, r);
+    float s, c;
+    sincospif(ph, &s, &c);
+    return make_float2(c, s);
+}
+
+template <int KP, int NB>
+__global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restrict__ descs) {
+    extern __shared__ float4 smem_raw[];
+    float2* Usm = reinterpret_cast<float2*>(smem_raw);  // [M][KP]
+    const FrameDesc* dp = descs + blockIdx.y;
+    const int M = dp->M, L = dp->L, kp = dp->kpad;
+    const int i0 = blockIdx.x * kThreads;
+    if (i0 >= L) return;
+    const float2* __restrict__ Us = dp->Us;
+    for (int e = threadIdx.x; e < M * KP; e += kThreads) {
+        const int m = e / KP, k = e % KP;
+        Usm[e] = (k < kp) ? Us[(int64_t)m * kp + k] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int i = i0 + threadIdx.x;
+    if (i >= L) return;
+    const float2 qq = dp->qtab[i];
+    const int nb = (M + 63) / 64;
+    float2 cb[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) cb[b] = (b < nb) ? steer(64 * b, qq.x, qq.y) : make_float2(0.f, 0.f);
+    float2 acc[KP];
+#pragma unroll
+    for (int k = 0; k < KP; ++k) acc[k] = make_float2(0.f, 0.f);
+    const int m0_end = min(64, M);
+    for (int m0 = 0; m0 < m0_end; ++m0) {
+        const float2 bm = steer(m0, qq.x, qq.y);
+        float2 part[KP];
+#pragma unroll
+        for (int k = 0; k < KP; ++k) part[k] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int m = 64 * b + m0;
+            if (b < nb && m < M) {
+                const float2 a = cmul(cb[b], bm);
+                const float4* urow = reinterpret_cast<const float4*>(Usm + m * KP);
+#pragma unroll
+                for (int k2 = 0; k2 < KP / 2; ++k2) {
+                    const float4 u = urow[k2];
+                    cfmac(part[2 * k2], make_float2(u.x, u.y), a);
+                    cfmac(part[2 * k2 + 1], make_float2(u.z, u.w), a);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KP; ++k) acc[k] = cadd(acc[k], part[k]);
+    }
+    float cn = 0.f;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) cn += cabs2(acc[k]);
+    const float den = (float)M - cn;
+    const float P = (den > 0.f) ? 1.0f / den : INFINITY;
+    dp->P[i] = P;
+    if (dp->Pdb) dp->Pdb[i] = 10.0f * log10f(fminf(P, FLT_MAX));
+}
+
+template <int KP, int NB>
+cudaError_t launch_kp(const FrameDesc* d, int n_frames, int max_L, int max_M, cudaStream_t s) {
+    const size_t smem = sizeof(float2) * (size_t)max_M * KP;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(scan_kernel<KP, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((max_L + kThreads - 1) / kThreads, n_frames);
+    scan_kernel<KP, NB><<<grid, kThreads, smem, s>>>(d);
+    return cudaGetLastError();
+}
+
+template <int NB>
+cudaError_t launch_nb(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s) {
+    if (max_kpad <= 4) return launch_kp<4, NB>(d, n_frames, max_L, max_M, s);
+    if (max_kpad <= 8) return launch_kp<8, NB>(d, n_frames, max_L, max_M, s);
+    if (max_kpad <= 16) return launch_kp<16, NB>(d, n_frames, max_L, max_M, s);
+    return launch_kp<32, NB>(d, n_frames, max_L, max_M, s);
+}
+
+}  // namespace
+
+cudaError_t launch_grid_table(const GridDesc* g, int n_grids, int max_L, cudaStream_t s) {
+    dim3 grid((max_L + 255) / 256, n_grids);
+    grid_table_kernel<<<grid, 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s) {
+    if (max_M <= 128) return launch_nb<2>(d, n_frames, max_L, max_M, max_kpad, s);
+    if (max_M <= 256) return launch_nb<4>(d, n_frames, max_L, max_M, max_kpad, s);
+    if (max_M <= 512) return launch_nb<8>(d, n_frames, max_L, max_M, max_kpad, s);
+    return launch_nb<16>(d, n_frames, max_L, max_M, max_kpad, s);
+}
+
+}  // namespace fm

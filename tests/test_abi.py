@@ -1,0 +1,66 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports every
+function include/fastmusic.h declares, and its struct layout matches the binding.
+No compute call is made (there may be no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1911_07434_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fastmusic.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fm_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(binding.exported_symbols()) == names
+
+
+def test_struct_layout_matches_header(lib):
+    # sizes implied by the C declarations on an LP64 ABI
+    assert ctypes.sizeof(binding.FmArray) == 16
+    assert ctypes.sizeof(binding.FmGrid) == 24
+    assert ctypes.sizeof(binding.FmParams) == 40
+    assert binding.FmFrame.arr.offset == 24 and binding.FmFrame.p.offset == 64
+    assert ctypes.sizeof(binding.FmFrame) == 160
+
+
+def _frame(M=64, T=200, K=3, l=13, t=1, method=2, L=1801, X=1, out=1):
+    f = binding.FmFrame()
+    f.X = X
+    f.T = T
+    f.ldx = T
+    f.arr = binding.FmArray(M, 0.5)
+    f.grid = binding.FmGrid(-90.0, 0.1, L)
+    f.p = binding.FmParams(method, K, l, t, 0, 0, 0, 0, 0)
+    f.P_out = f.peak_idx = f.peak_deg = f.n_peaks = out
+    return f
+
+
+def test_workspace_planning_is_host_only(lib):
+    """fm_workspace_bytes validates and sizes on the host (no device needed)."""
+    ok = binding.fm_workspace_bytes([_frame()])
+    # R (64*64*8) + C, V (64*13*8 each) + U_s (64*3*8) + tables, each 256-aligned
+    assert ok >= 64 * 64 * 8 + 2 * 64 * 13 * 8 + 64 * 3 * 8 + 1801 * 8
+    two = binding.fm_workspace_bytes([_frame(), _frame()])
+    assert two > ok and two < 2 * ok       # one shared grid table
+    for bad in (_frame(K=14), _frame(l=65, M=128), _frame(M=1), _frame(method=0), _frame(L=0), _frame(X=0),
+                _frame(out=0), _frame(t=9), _frame(M=2048)):
+        assert binding.fm_workspace_bytes([bad]) == 0

@@ -1,0 +1,210 @@
+"""GPU-vs-oracle parity through the C ABI (needs a GB300).
+
+Every test feeds the same seeded inputs to the CUDA library and to the FP64
+oracle and compares element by element, with tolerances derived from FP32
+arithmetic (u = 2^-24) as stated in each test.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1911_07434_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1911_07434_gb300 import binding, build
+    build.build()
+    c = binding.Context(device=0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def proj(U):
+    return U @ U.conj().T
+
+
+# --------------------------------------------------------------- Omega / I ---
+@pytest.mark.parametrize("seed,fid,M,l", [(0, 0, 37, 13), (12345, 7, 512, 24), (2 ** 40 + 3, 2 ** 33 + 1, 5, 1)])
+def test_test_matrix_parity(ctx, seed, fid, M, l):
+    G = ctx.test_matrix(seed, fid, M, l).cpu().numpy().astype(np.complex128)
+    O = oracle.gaussian_test_matrix(seed, fid, M, l)
+    # FP32 log1p/log, sqrt, sincospi: a few ulps relative on each factor
+    assert np.max(np.abs(G - O) / (np.abs(O) + 1e-3)) < 2e-6
+
+
+@pytest.mark.parametrize("seed,fid,M,l", [(0, 0, 64, 13), (5, 9, 512, 24), (7, 1, 3, 3), (99, 2 ** 35, 1000, 48),
+                                          (1, 1, 1, 1)])
+def test_sample_indices_bit_exact(ctx, seed, fid, M, l):
+    assert np.array_equal(ctx.sample_indices(seed, fid, M, l).cpu().numpy(), oracle.sample_indices(seed, fid, M, l))
+
+
+# -------------------------------------------------------------- covariance ---
+@pytest.mark.parametrize("M,T", [(1, 5), (2, 1), (3, 17), (63, 64), (64, 200), (65, 100), (130, 333), (200, 1000)])
+def test_covariance_parity(ctx, M, T):
+    rng = np.random.default_rng(M * 1000 + T)
+    X = ((rng.standard_normal((M, T)) + 1j * rng.standard_normal((M, T))) * rng.uniform(0.1, 10, (M, 1)))
+    X = X.astype(np.complex64)
+    R = ctx.covariance(dev(X))[0].cpu().numpy()
+    Ro = oracle.covariance(X)
+    # two-level FP32 sum: |error| <= (64 + ceil(T/64) + 2) u sum_t |x_it x_jt| / T <= that * sqrt(R_ii R_jj)
+    d = np.sqrt(np.real(np.diag(Ro)))
+    bound = (64 + np.ceil(T / 64) + 2) * U32 * np.outer(d, d)
+    assert np.all(np.abs(R - Ro) <= bound)
+    assert np.array_equal(R, R.conj().T)
+    assert np.all(np.diag(R).imag == 0)
+
+
+def test_covariance_batch_and_stride(ctx):
+    rng = np.random.default_rng(3)
+    B, M, T, ld = 3, 70, 90, 96
+    buf = (rng.standard_normal((B, M, ld)) + 1j * rng.standard_normal((B, M, ld))).astype(np.complex64)
+    Xt = dev(buf)[:, :, :T]
+    R = ctx.covariance(Xt).cpu().numpy()
+    for b in range(B):
+        Ro = oracle.covariance(buf[b, :, :T])
+        d = np.sqrt(np.real(np.diag(Ro)))
+        assert np.all(np.abs(R[b] - Ro) <= (64 + 4) * U32 * np.outer(d, d))
+
+
+# ---------------------------------------------------------------- spectrum ---
+@pytest.mark.parametrize("M,nc,grid", [(2, 1, (-90.0, 1.0, 181)), (7, 3, (-90.0, 0.37, 487)),
+                                       (64, 3, (-90.0, 0.1, 1801)), (200, 13, (-60.0, 0.05, 2401)),
+                                       (512, 8, (-75.0, 0.01, 15001)), (1000, 16, (-90.0, 0.9, 201))])
+def test_spectrum_parity(ctx, M, nc, grid):
+    rng = np.random.default_rng(M + nc)
+    A = rng.standard_normal((M, nc)) + 1j * rng.standard_normal((M, nc))
+    U = np.linalg.qr(A)[0].astype(np.complex64)
+    th0, st, L = grid
+    P = ctx.spectrum(dev(U), th0, st, L)[0].cpu().numpy().astype(np.float64)
+    Po = oracle.spectrum(U.astype(np.complex128), th0, st, L)
+    # den = M - sum_k |c_k|^2 with c_k an M-term FP32 sum of unit-modulus products:
+    # |d den| <= 2 sum_k |c_k| |d c_k| + ... <= 8 u M max(nc, 1) (steering error incl.)
+    dd = np.abs(1.0 / P - 1.0 / Po)
+    assert np.max(dd) <= 8 * U32 * M * max(nc, 1), np.max(dd)
+
+
+# ------------------------------------------------------------------- peaks ---
+@pytest.mark.parametrize("L,K", [(1, 1), (2, 3), (3, 1), (100, 5), (1025, 16), (15001, 8), (65536, 4)])
+def test_peaks_bit_exact(ctx, L, K):
+    rng = np.random.default_rng(L * 31 + K)
+    for trial in range(3):
+        if trial == 0:
+            P = rng.integers(0, 7, L).astype(np.float32)          # ties and plateaus
+        elif trial == 1:
+            P = rng.standard_normal(L).astype(np.float32)
+        else:
+            P = np.full(L, 2.5, np.float32)
+            P[::7] = np.inf
+        idx, deg, n = ctx.peaks(dev(P), K, -90.0, 0.25)
+        io, no = oracle.peaks(P.astype(np.float64), K)
+        assert int(n[0]) == no
+        assert np.array_equal(idx[0].cpu().numpy(), io)
+        got = deg[0].cpu().numpy()[:no]
+        assert np.array_equal(got, (-90.0 + 0.25 * io[:no]).astype(np.float32))
+
+
+# ---------------------------------------------------------------- subspace ---
+SUB_CASES = [
+    # (frame factory, K, l, t, method)
+    ("small", 3, 13, 0, 2), ("small", 3, 13, 1, 2), ("small", 3, 13, 2, 2), ("small", 3, 13, 0, 1),
+    ("small", 3, 3, 2, 2), ("small", 3, 64, 1, 1), ("mid", 5, 7, 1, 2), ("mid", 5, 7, 0, 1), ("mid", 5, 5, 1, 1),
+    ("big", 8, 24, 1, 2), ("big", 8, 24, 0, 1), ("big", 8, 24, 1, 1),
+]
+
+
+def _frame(kind):
+    if kind == "small":
+        return synth.small_frame().X
+    if kind == "mid":
+        return synth.massive_mimo_frames(1, seed=4, M=100, T=150, K=5, extra=2).frames[0].X
+    return synth.massive_mimo_frames(1, seed=1).frames[0].X
+
+
+@pytest.mark.parametrize("kind,K,l,t,method", SUB_CASES)
+def test_subspace_parity(ctx, kind, K, l, t, method):
+    X = _frame(kind)
+    R32 = oracle.covariance(X).astype(np.complex64)   # both sides start from the same complex64 R
+    U, status = ctx.subspace(dev(R32), K, l, t, method, seed=11, frame_id0=5)
+    Ug = U[0].cpu().numpy().astype(np.complex128)
+    Uo, _, _ = oracle.fast_music(R32.astype(np.complex128), K, l, t, method, seed=11, frame_id=5)
+    assert int(status[0]) == 0
+    err = np.linalg.norm(proj(Ug) - proj(Uo))
+    assert err <= 1e-5, err
+    assert np.linalg.norm(Ug.conj().T @ Ug - np.eye(K)) < 1e-5
+
+
+# -------------------------------------------------------------- end to end ---
+def _run(ctx, frames, methods):
+    from paper_1911_07434_gb300 import binding
+    outs, fs = [], []
+    for fr, m in zip(frames, methods):
+        X = dev(fr.X)
+        P = torch.empty(fr.L, dtype=torch.float32, device="cuda")
+        idx = torch.empty(fr.K, dtype=torch.int32, device="cuda")
+        deg = torch.empty(fr.K, dtype=torch.float32, device="cuda")
+        n = torch.empty(1, dtype=torch.int32, device="cuda")
+        st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        fs.append(ctx.frame(X, fr.K, fr.l, fr.t, m, fr.theta0, fr.step, fr.L, P, idx, deg, n, seed=3,
+                            frame_id=fr.frame_id, status=st))
+        outs.append((X, P, idx, deg, n, st))
+    ctx.run(fs)
+    torch.cuda.synchronize()
+    return outs
+
+
+def _check_frame(fr, m, out, db_tol=0.01):
+    X, P, idx, deg, n, st = out
+    Po, io, no = oracle.frame(fr.X, fr.K, fr.l, fr.t, m, 3, fr.frame_id, fr.theta0, fr.step, fr.L)
+    Pg = P.cpu().numpy().astype(np.float64)
+    assert int(st[0]) == 0
+    assert int(n[0]) == no
+    th = fr.theta0 + fr.step * np.arange(fr.L)
+    bw = np.rad2deg(2.0 / fr.M)
+    far = np.min(np.abs(th[:, None] - fr.angles_deg[None, :]), axis=1) > 2 * bw
+    ddb = np.abs(10 * np.log10(Pg) - 10 * np.log10(Po))
+    assert np.max(ddb[far]) < db_tol, np.max(ddb[far])
+    assert np.sort(idx.cpu().numpy()).tolist() == np.sort(io).tolist()
+
+
+def test_run_small_frame(ctx):
+    fr = synth.small_frame()
+    for m in (2, 1):
+        out = _run(ctx, [fr], [m])
+        _check_frame(fr, m, out[0])
+
+
+def test_run_uneven_batch(ctx):
+    """Frames of different M, T, K, l, t, method and grid in one fm_run call."""
+    frames = synth.uneven_frames(6, seed=2).frames
+    frames[0].t = 0
+    frames[1].t = 2
+    methods = [2, 1, 2, 1, 2, 2]
+    outs = _run(ctx, frames, methods)
+    for fr, m, o in zip(frames, methods, outs):
+        _check_frame(fr, m, o, db_tol=0.05)
+
+
+def test_run_full_size_sampled(ctx):
+    """The benchmark's launch configuration (64 frames, M=512, T=1024, K=8, l=24,
+    t=1, 15001-point grid); the oracle recomputes two sampled frames, all frames
+    are checked for their K peaks at the true angles."""
+    wl = synth.massive_mimo_frames(64, seed=0)
+    outs = _run(ctx, wl.frames, [2] * 64)
+    for b in (0, 37):
+        _check_frame(wl.frames[b], 2, outs[b], db_tol=0.01)
+    for fr, o in zip(wl.frames, outs):
+        assert int(o[4][0]) == fr.K and int(o[5][0]) == 0
+        est = np.sort(o[3].cpu().numpy())
+        assert np.max(np.abs(est - fr.angles_deg)) < 0.05, (est, fr.angles_deg)
