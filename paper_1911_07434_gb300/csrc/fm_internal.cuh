@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/fastmusic.h"
+#include "fastmusic.h"
 
 namespace fm {
 

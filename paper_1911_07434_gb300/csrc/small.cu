@@ -49,6 +49,7 @@ struct Sm {
     int2* pairs;   // kLMax/2
     int* flags;    // 8
     double* dscal; // 8
+    double* dinv;  // kLMax
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -73,6 +74,7 @@ __host__ __device__ inline size_t smem_layout(int l, Sm* sm, char* base) {
     char* pairs = take((kLMax / 2 + 1) * sizeof(int2));
     char* flags = take(8 * sizeof(int));
     char* dscal = take(8 * sizeof(double));
+    char* dinv = take(kLMax * sizeof(double));
     if (sm) {
         sm->G64 = reinterpret_cast<double2*>(u0);
         sm->R64 = reinterpret_cast<double2*>(u0) + ll;
@@ -90,6 +92,7 @@ __host__ __device__ inline size_t smem_layout(int l, Sm* sm, char* base) {
         sm->pairs = reinterpret_cast<int2*>(pairs);
         sm->flags = reinterpret_cast<int*>(flags);
         sm->dscal = reinterpret_cast<double*>(dscal);
+        sm->dinv = reinterpret_cast<double*>(dinv);
     }
     return off;
 }
@@ -235,22 +238,23 @@ __device__ void gram_df64(const float2* A, const FrameDesc& d, int M, int l, con
 // In place: G (Hermitian) -> upper R with G = R^H R.  Returns false on a
 // non-positive pivot (the pivot is then clamped so the factor stays finite).
 template <typename T2, typename T>
-__device__ bool cholesky_upper(T2* G, int l, int* flag) {
+__device__ bool cholesky_upper(T2* G, int l, int* flag, T* scratch) {
     if (threadIdx.x == 0) flag[0] = 0;
     __syncthreads();
     for (int k = 0; k < l; ++k) {
         if (threadIdx.x == 0) {
             T dkk = G[k * l + k].x;
-            T floor_v = (T)1e-30;
             if (!(dkk > (T)0)) {
                 flag[0] = 1;
-                dkk = floor_v;
+                dkk = (T)1e-30;
             }
-            G[k * l + k].x = sqrt(dkk);
+            const T r = sqrt(dkk);
+            G[k * l + k].x = r;
             G[k * l + k].y = (T)0;
+            scratch[0] = (T)1 / r;
         }
         __syncthreads();
-        const T inv = (T)1 / G[k * l + k].x;
+        const T inv = scratch[0];
         for (int j = k + 1 + threadIdx.x; j < l; j += kThreads) {
             G[k * l + j].x *= inv;
             G[k * l + j].y *= inv;
@@ -279,29 +283,39 @@ __device__ bool cholesky_upper(T2* G, int l, int* flag) {
     return flag[0] == 0;
 }
 
-// Ri = R^{-1} for upper triangular R with real positive diagonal (column-wise
-// back substitution, one thread per column).
+// X = R^{-1} for upper triangular R with real positive diagonal, by right-looking
+// back substitution: row i of X is finalised as X_ij = (delta_ij - S_ij) / R_ii
+// (S_ij = sum_{m>i} R_im X_mj, accumulated in X itself), then its contribution
+// R_ki X_ij is added to the partial sums of all rows k < i in parallel.
+// dinv: scratch for the l reciprocals of the diagonal.
 template <typename T2, typename T>
-__device__ void tri_inv_upper(const T2* R, T2* Ri, int l) {
-    for (int j = threadIdx.x; j < l; j += kThreads) {
-        for (int i = 0; i < l; ++i) {
-            Ri[i * l + j].x = (T)0;
-            Ri[i * l + j].y = (T)0;
-        }
-        Ri[j * l + j].x = (T)1 / R[j * l + j].x;
-        for (int i = j - 1; i >= 0; --i) {
-            T sx = 0, sy = 0;
-            for (int k = i + 1; k <= j; ++k) {
-                const T2 a = R[i * l + k], b = Ri[k * l + j];
-                sx += a.x * b.x - a.y * b.y;
-                sy += a.x * b.y + a.y * b.x;
-            }
-            const T inv = (T)1 / R[i * l + i].x;
-            Ri[i * l + j].x = -sx * inv;
-            Ri[i * l + j].y = -sy * inv;
-        }
+__device__ void tri_inv_upper(const T2* R, T2* X, int l, T* dinv) {
+    for (int e = threadIdx.x; e < l * l; e += kThreads) {
+        X[e].x = (T)0;
+        X[e].y = (T)0;
     }
+    for (int i = threadIdx.x; i < l; i += kThreads) dinv[i] = (T)1 / R[i * l + i].x;
     __syncthreads();
+    for (int i = l - 1; i >= 0; --i) {
+        const T inv = dinv[i];
+        for (int j = i + threadIdx.x; j < l; j += kThreads) {
+            T2 x = X[i * l + j];
+            x.x = ((j == i) ? (T)1 : (T)0) - x.x;
+            x.y = -x.y;
+            x.x *= inv;
+            x.y *= inv;
+            X[i * l + j] = x;
+        }
+        __syncthreads();
+        const int w = l - i;
+        for (int e = threadIdx.x; e < i * w; e += kThreads) {
+            const int k = e / w, j = i + e % w;
+            const T2 a = R[k * l + i], b = X[i * l + j];
+            X[k * l + j].x += a.x * b.x - a.y * b.y;
+            X[k * l + j].y += a.x * b.y + a.y * b.x;
+        }
+        __syncthreads();
+    }
 }
 
 // dst (M x ld_dst) = src (M x l) * Tm (l x n_out, row stride ldt); columns
@@ -327,6 +341,36 @@ __device__ void apply_rows(const float2* src, float2* dst, const FrameDesc& d, i
     }
 }
 
+// dst (M x l) = src (M x l) * Ri with Ri upper triangular given as an
+// unevaluated sum Ri = hi + lo of two FP32 matrices; products with hi are split
+// exactly (FMA) and summed in double-float, so the result is the correctly
+// scaled combination up to one final rounding even when Ri is ill-conditioned.
+__device__ void apply_rows_df(const float2* src, float2* dst, const FrameDesc& d, int M, int l, const float2* Rhi,
+                              const float2* Rlo, const Sm& sm) {
+    for (int m0 = 0; m0 < M; m0 += kRowsChunk) {
+        load_chunk(src, kMem, d, M, l, m0, sm.ca);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kRowsChunk * l; e += kThreads) {
+            const int r = e / l, c = e % l;
+            const int m = m0 + r;
+            if (m >= M) continue;
+            df re{0.f, 0.f}, im{0.f, 0.f};
+            for (int k = 0; k <= c; ++k) {
+                const float2 a = sm.ca[r * l + k];
+                const float2 h = Rhi[k * l + c], w = Rlo[k * l + c];
+                df_add_prod(re, a.x, h.x);
+                df_add_prod(re, -a.y, h.y);
+                df_add_prod(im, a.x, h.y);
+                df_add_prod(im, a.y, h.x);
+                re.lo = fmaf(a.x, w.x, fmaf(-a.y, w.y, re.lo));
+                im.lo = fmaf(a.x, w.y, fmaf(a.y, w.x, im.lo));
+            }
+            dst[(int64_t)m * l + c] = make_float2(re.hi + re.lo, im.hi + im.lo);
+        }
+        __syncthreads();
+    }
+}
+
 // Rc <- Rk * Rc (both l x l upper triangular), using tmp as scratch.
 __device__ void upper_mul_inplace(const float2* Rk, float2* Rc, float2* tmp, int l) {
     for (int e = threadIdx.x; e < l * l; e += kThreads) {
@@ -346,35 +390,27 @@ __device__ void upper_mul_inplace(const float2* Rk, float2* Rc, float2* tmp, int
 __device__ bool cholqr2(const float2* src, float2* dst, const FrameDesc& d, int M, int l, const Sm& sm) {
     // pass 1: double-float Gram, FP64 Cholesky and inverse
     gram_df64(src, d, M, l, sm, sm.G64);
-    bool ok = cholesky_upper<double2, double>(sm.G64, l, sm.flags + 4);
-    tri_inv_upper<double2, double>(sm.G64, sm.R64, l);
-    // Rc = R1 (FP32 copy); the FP32 inverse goes to Y (Y aliases the upper half of R64,
-    // so convert through registers first)
+    bool ok = cholesky_upper<double2, double>(sm.G64, l, sm.flags + 4, sm.dinv);
+    tri_inv_upper<double2, double>(sm.G64, sm.R64, l, sm.dinv);
+    // Rc = R1 in FP32, then R1^{-1} (FP64, in R64) as hi + lo FP32 pairs in the
+    // slots of G64 (G = hi, Ri = lo), which are free once Rc is taken.
     for (int e = threadIdx.x; e < l * l; e += kThreads) {
         const double2 r = sm.G64[e];
         sm.Rc[e] = make_float2((float)r.x, (float)r.y);
     }
-    float2 tmpv[(kLMax * kLMax + kThreads - 1) / kThreads];
-#pragma unroll
-    for (int q = 0; q < (kLMax * kLMax + kThreads - 1) / kThreads; ++q) {
-        const int e = threadIdx.x + q * kThreads;
-        if (e < l * l) {
-            const double2 r = sm.R64[e];
-            tmpv[q] = make_float2((float)r.x, (float)r.y);
-        }
+    __syncthreads();
+    for (int e = threadIdx.x; e < l * l; e += kThreads) {
+        const double2 r = sm.R64[e];
+        const float hx = (float)r.x, hy = (float)r.y;
+        sm.G[e] = make_float2(hx, hy);
+        sm.Ri[e] = make_float2((float)(r.x - (double)hx), (float)(r.y - (double)hy));
     }
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < (kLMax * kLMax + kThreads - 1) / kThreads; ++q) {
-        const int e = threadIdx.x + q * kThreads;
-        if (e < l * l) sm.Y[e] = tmpv[q];
-    }
-    __syncthreads();
-    apply_rows(src, dst, d, M, l, sm.Y, l, l, l, l, true, sm);
+    apply_rows_df(src, dst, d, M, l, sm.G, sm.Ri, sm);
     // pass 2 in FP32 (cond ~ 1)
     gram_fp32(dst, kMem, nullptr, d, M, l, sm, sm.G);
-    ok = cholesky_upper<float2, float>(sm.G, l, sm.flags + 4) && ok;
-    tri_inv_upper<float2, float>(sm.G, sm.Ri, l);
+    ok = cholesky_upper<float2, float>(sm.G, l, sm.flags + 4, reinterpret_cast<float*>(sm.dinv)) && ok;
+    tri_inv_upper<float2, float>(sm.G, sm.Ri, l, reinterpret_cast<float*>(sm.dinv));
     apply_rows(dst, dst, d, M, l, sm.Ri, l, l, l, l, true, sm);
     upper_mul_inplace(sm.G, sm.Rc, sm.Y, l);
     return ok;
