@@ -86,7 +86,7 @@ typedef struct {
 } fm_grid;
 
 /* Estimator parameters.  K = number of sources, l = sketch size (the paper's p,
- * K <= l <= min(M, 64)), t = power iterations (Eq. 11; 0..8).  rank_restrict:
+ * K <= l <= min(M, 48)), t = power iterations (Eq. 11; 0..8).  rank_restrict:
  * number of columns of U_s used by the scan, K (0 means K) or l.  refine and
  * prec other than FP32 are reserved and must be 0.  seed keys the Philox
  * stream of Pi / the sampled index set. */
@@ -186,6 +186,19 @@ fm_status fm_set_timing(fm_ctx* ctx, int enable);
 fm_status fm_stage_times(fm_ctx* ctx, double* total_ms, int* launches, int reset);
 /* Number of kernel launches issued by this context since creation. */
 uint64_t fm_launch_count(const fm_ctx* ctx);
+
+/* ---- covariance kernel selection ----------------------------------------------
+ * FM_COV_AUTO (default): the tensor-core kernel (tcgen05 MMAs with TMEM
+ * accumulators, TMA-staged tiles, FP32-level accuracy from three TF32 products
+ * per FP32 product) whenever every frame's X is 16-byte aligned with an even
+ * ldx, else the FP32 CUDA-core kernel.  FM_COV_SIMT / FM_COV_TC force one path
+ * (FM_COV_TC fails with FM_ERR_INVALID_ARG for frames it cannot take).
+ * fm_last_cov_path returns the path the latest covariance launch used. */
+#define FM_COV_AUTO 0
+#define FM_COV_SIMT 1
+#define FM_COV_TC 2
+fm_status fm_set_cov_path(fm_ctx* ctx, int path);
+int fm_last_cov_path(const fm_ctx* ctx);
 
 /* ---- serving (continuous batching) ------------------------------------------
  * fm_serve_submit: enqueue one frame; the library admits queued frames into

@@ -29,6 +29,9 @@ FM_RAND_SAMPLING = 1
 FM_RAND_PROJECTION = 2
 
 FM_PREC_FP32 = 0
+FM_COV_AUTO = 0
+FM_COV_SIMT = 1
+FM_COV_TC = 2
 FM_N_STAGES = 7
 STAGES = ("grid", "covariance", "sketch", "orth", "final", "scan", "peaks")
 
@@ -71,6 +74,8 @@ _SIGS = {
     "fm_set_timing": (c_int, [c_void_p, c_int]),
     "fm_stage_times": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int), c_int]),
     "fm_launch_count": (c_uint64, [c_void_p]),
+    "fm_set_cov_path": (c_int, [c_void_p, c_int]),
+    "fm_last_cov_path": (c_int, [c_void_p]),
     "fm_serve_submit": (c_int, [c_void_p, POINTER(FmFrame), POINTER(c_uint64)]),
     "fm_serve_poll": (c_int, [c_void_p, c_uint64, POINTER(c_int)]),
 }
@@ -166,6 +171,14 @@ def fm_stage_times(ctx, reset=False):
 
 def fm_launch_count(ctx) -> int:
     return load().fm_launch_count(ctx)
+
+
+def fm_set_cov_path(ctx, path) -> int:
+    return load().fm_set_cov_path(ctx, path)
+
+
+def fm_last_cov_path(ctx) -> int:
+    return load().fm_last_cov_path(ctx)
 
 
 def fm_serve_submit(ctx, frame: FmFrame):
@@ -307,6 +320,12 @@ class Context:
 
     def launch_count(self) -> int:
         return fm_launch_count(self.h)
+
+    def set_cov_path(self, path: int):
+        self._check(fm_set_cov_path(self.h, path), "fm_set_cov_path")
+
+    def last_cov_path(self) -> int:
+        return fm_last_cov_path(self.h)
 
     def serve_submit(self, frame: FmFrame) -> int:
         st, t = fm_serve_submit(self.h, frame)

@@ -39,7 +39,6 @@ __global__ void __launch_bounds__(kThreads, 2) cov_fp32_kernel(const FrameDesc* 
     const float2* __restrict__ X = dp->X;
     float2* __restrict__ R = dp->R;
     const int nt = (M + kTile - 1) / kTile;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && dp->status) *dp->status = 0;  // fresh per-frame status
     if ((int)blockIdx.x >= nt * (nt + 1) / 2) return;
     int ti, tj;
     tile_coords(blockIdx.x, nt, ti, tj);

@@ -1,0 +1,340 @@
+// cov_tc.cu -- R = X X^H / T (Sec. II-B, Eq. 2) on the 5th-generation tensor
+// cores: TMA loads of X tiles, tcgen05.mma (kind::tf32) into TMEM accumulators,
+// tcgen05.ld epilogue.
+//
+// Real formulation.  With X = Xr + j Xi, one 128 x 128 output tile (I, J) of
+// the upper block triangle is
+//   Re R_IJ = (Xr_I Xr_J^T + Xi_I Xi_J^T) / T,  Im R_IJ = (Xi_I Xr_J^T - Xr_I Xi_J^T) / T.
+// Two accumulators of 128 x 256 FP32 each (all 512 TMEM columns) hold
+//   D_top = Xr_I [Xr_J; Xi_J]^T = [rr | ri],  D_bot = Xi_I [Xr_J; Xi_J]^T = [ir | ii].
+// FP32 accuracy from TF32 tensor cores ("3xTF32"): every operand x is split into
+// hi = rn_tf32(x) and lo = rn_tf32(x - hi), and each product is formed as
+// hi*hi + hi*lo + lo*hi (the dropped lo*lo term is below 2^-22 |x y|).
+//
+// Warp roles (192 threads): warp 0 issues the TMA loads of the raw interleaved
+// complex64 tiles (128 rows x 16 snapshots = one 128-byte swizzled box per
+// operand and stage); warp 1 allocates TMEM and issues the MMAs (one thread);
+// warps 2-5 split each raw stage into planar hi/lo operand tiles in the
+// 128-byte-swizzled K-major layout the MMA descriptors expect, and finally run
+// the epilogue (TMEM -> registers -> R tile and its conjugate mirror).  Raw and
+// converted stages are double-buffered and handed over with mbarriers; every
+// wait is bounded and records FM_ERR_TIMEOUT in the frame status on expiry.
+#include <cuda.h>
+
+#include "fm_internal.cuh"
+
+namespace fm {
+namespace {
+
+constexpr int kTile = 128;                         // complex rows per tile side
+constexpr int kRawBox = kTile * 32 * 4;            // 16 KB: 128 rows x 32 floats (16 complex)
+constexpr int kConvA = kTile * 128;                // 16 KB: 128 rows x [hi 16 | lo 16] tf32
+constexpr int kConvB = 2 * kTile * 128;            // 32 KB: 256 rows ([Xr_J; Xi_J]) x [hi | lo]
+constexpr int kRawStage = 2 * kRawBox;             // A and B boxes
+constexpr int kConvStage = 2 * kConvA + kConvB;    // Ar, Ai, B
+constexpr int kNRaw = 2, kNConv = 2;
+constexpr int kThreads = 192;
+constexpr int kTiles = kNRaw * kRawStage + kNConv * kConvStage;   // 192 KB
+constexpr int kSmemBytes = kTiles + 1024 + 256;                   // + 1024-B alignment slack + barriers
+constexpr uint32_t kTmemCols = 512;
+constexpr long long kWaitCycles = 4000000000LL;                   // ~2 s at 2 GHz
+
+// ------------------------------------------------------------- PTX helpers --
+__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(sa(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false (and *abort set) if the phase did not complete in time.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
+    if (mbar_test(b, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_test(b, parity)) return true;
+        if (*abort) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *abort = 1;
+            return false;
+        }
+        __nanosleep(64);
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(sa(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(sa(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t tf32_rn(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// K-major, 128-byte-swizzled shared-memory matrix descriptor (tcgen05):
+// start address >> 4 in [0,14), leading-dim offset (unused for this layout) = 1,
+// stride-dim offset = 1024 B (one 8-row x 128-B swizzle atom) in [32,46),
+// version 1 in [46,48), layout SWIZZLE_128B (2) in [61,64).
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
+// (bits 7-9 = bits 10-12 = 2), both K-major, N >> 3 in bits 17-22, M >> 4 in 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// byte offset of 16-byte chunk c of row r in a 128-byte-swizzled tile
+__device__ __forceinline__ uint32_t swz(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+
+__device__ __forceinline__ void tile_coords(int b, int nt, int& ti, int& tj) {
+    ti = 0;
+    while (b >= nt - ti) {
+        b -= nt - ti;
+        ++ti;
+    }
+    tj = ti + b;
+}
+
+// Split 4 raw floats (2 complex) pairs into planar hi/lo (TF32-rounded) values.
+__device__ __forceinline__ void split4(float a, float b, float c, float d, uint4& hi, uint4& lo) {
+    hi.x = tf32_rn(a);
+    hi.y = tf32_rn(b);
+    hi.z = tf32_rn(c);
+    hi.w = tf32_rn(d);
+    lo.x = tf32_rn(a - __uint_as_float(hi.x));
+    lo.y = tf32_rn(b - __uint_as_float(hi.y));
+    lo.z = tf32_rn(c - __uint_as_float(hi.z));
+    lo.w = tf32_rn(d - __uint_as_float(hi.w));
+}
+
+// Convert one 128-row raw box (interleaved complex, 16 per row) into the planar
+// hi/lo rows of two destination tiles (re -> dre row rr, im -> dim row ri).
+__device__ __forceinline__ void convert_row(const char* raw, int r, char* dre, int rr, char* dim, int ri) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {  // output chunk q: complex 4q .. 4q+3
+        const float4 v0 = *reinterpret_cast<const float4*>(raw + swz(r, 2 * q));
+        const float4 v1 = *reinterpret_cast<const float4*>(raw + swz(r, 2 * q + 1));
+        uint4 rh, rl, ih, il;
+        split4(v0.x, v0.z, v1.x, v1.z, rh, rl);
+        split4(v0.y, v0.w, v1.y, v1.w, ih, il);
+        *reinterpret_cast<uint4*>(dre + swz(rr, q)) = rh;
+        *reinterpret_cast<uint4*>(dre + swz(rr, 4 + q)) = rl;
+        *reinterpret_cast<uint4*>(dim + swz(ri, q)) = ih;
+        *reinterpret_cast<uint4*>(dim + swz(ri, 4 + q)) = il;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    cov_tc_kernel(const FrameDesc* __restrict__ descs, const CUtensorMap* __restrict__ tmaps) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* raw = base;                              // kNRaw x {A, B}
+    unsigned char* conv = base + kNRaw * kRawStage;         // kNConv x {Ar, Ai, B}
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + kTiles);
+    uint64_t* raw_full = bars;                 // [kNRaw]
+    uint64_t* raw_empty = bars + 2;            // [kNRaw]
+    uint64_t* conv_full = bars + 4;            // [kNConv]
+    uint64_t* conv_empty = bars + 6;           // [kNConv]
+    uint64_t* acc_full = bars + 8;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 9);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 10);
+
+    const FrameDesc* dp = descs + blockIdx.y;
+    const int M = dp->M, T = dp->T;
+    const int nt = (M + kTile - 1) / kTile;
+    if ((int)blockIdx.x >= nt * (nt + 1) / 2) return;
+    int ti, tj;
+    tile_coords(blockIdx.x, nt, ti, tj);
+    const bool diag = (ti == tj);
+    const int i0 = ti * kTile, j0 = tj * kTile;
+    const int nstages = (T + 15) / 16;
+    const CUtensorMap* tm = tmaps + blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kNRaw; ++s) {
+            mbar_init(&raw_full[s], 1);
+            mbar_init(&raw_empty[s], 128);
+        }
+        for (int s = 0; s < kNConv; ++s) {
+            mbar_init(&conv_full[s], 128);
+            mbar_init(&conv_empty[s], 1);
+        }
+        mbar_init(acc_full, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tm)) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------ TMA producer --
+        if (lane == 0) {
+            const uint32_t bytes = diag ? kRawBox : 2 * kRawBox;
+            for (int s = 0; s < nstages; ++s) {
+                const int slot = s % kNRaw;
+                const uint32_t ph = (uint32_t)(s / kNRaw) & 1u;
+                if (!mbar_wait(&raw_empty[slot], ph ^ 1u, abort_flag)) break;
+                unsigned char* dst = raw + slot * kRawStage;
+                mbar_expect_tx(&raw_full[slot], bytes);
+                tma_load_2d(dst, tm, s * 32, i0, &raw_full[slot]);
+                if (!diag) tma_load_2d(dst + kRawBox, tm, s * 32, j0, &raw_full[slot]);
+            }
+            // drain: the last loads must land before the CTA may exit
+            for (int s = max(0, nstages - kNRaw); s < nstages; ++s)
+                mbar_wait(&raw_full[s % kNRaw], (uint32_t)(s / kNRaw) & 1u, abort_flag);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------- MMA issuer --
+        if (lane == 0) {
+            const uint32_t d_top = tmem, d_bot = tmem + 256;
+            for (int s = 0; s < nstages; ++s) {
+                const int slot = s % kNConv;
+                const uint32_t ph = (uint32_t)(s / kNConv) & 1u;
+                if (!mbar_wait(&conv_full[slot], ph, abort_flag)) break;
+                tc_fence_after();
+                unsigned char* cv = conv + slot * kConvStage;
+                const uint32_t ar = sa(cv), ai = sa(cv + kConvA), bb = sa(cv + 2 * kConvA);
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                    const uint32_t acc0 = (s > 0 || kk > 0) ? 1u : 0u;
+                    const uint64_t b_hi = desc_sw128(bb + 32 * kk), b_lo = desc_sw128(bb + 64 + 32 * kk);
+                    const uint64_t r_hi = desc_sw128(ar + 32 * kk), r_lo = desc_sw128(ar + 64 + 32 * kk);
+                    const uint64_t i_hi = desc_sw128(ai + 32 * kk), i_lo = desc_sw128(ai + 64 + 32 * kk);
+                    mma_tf32(d_top, r_hi, b_hi, acc0);
+                    mma_tf32(d_top, r_hi, b_lo, 1u);
+                    mma_tf32(d_top, r_lo, b_hi, 1u);
+                    mma_tf32(d_bot, i_hi, b_hi, acc0);
+                    mma_tf32(d_bot, i_hi, b_lo, 1u);
+                    mma_tf32(d_bot, i_lo, b_hi, 1u);
+                }
+                mma_commit(&conv_empty[slot]);  // frees the converted stage once these MMAs finish
+            }
+            mma_commit(acc_full);
+            mbar_wait(acc_full, 0u, abort_flag);  // all MMAs retired before the epilogue / dealloc
+        }
+    } else {
+        // ------------------------------------------- converters, then epilogue --
+        const int r = threadIdx.x - 64;  // 0..127: one row of each tile
+        for (int s = 0; s < nstages; ++s) {
+            const int rs = s % kNRaw, cs = s % kNConv;
+            if (!mbar_wait(&raw_full[rs], (uint32_t)(s / kNRaw) & 1u, abort_flag)) break;
+            if (!mbar_wait(&conv_empty[cs], ((uint32_t)(s / kNConv) & 1u) ^ 1u, abort_flag)) break;
+            const char* rawA = reinterpret_cast<const char*>(raw + rs * kRawStage);
+            const char* rawB = diag ? rawA : rawA + kRawBox;
+            char* cv = reinterpret_cast<char*>(conv + cs * kConvStage);
+            convert_row(rawA, r, cv, r, cv + kConvA, r);                        // Ar, Ai
+            convert_row(rawB, r, cv + 2 * kConvA, r, cv + 2 * kConvA, 128 + r);  // B = [Br; Bi]
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&conv_full[cs]);
+            mbar_arrive(&raw_empty[rs]);
+        }
+        // epilogue: rows 32 * (warp % 4) + lane of the tile
+        const bool ok = mbar_wait(acc_full, 0u, abort_flag);
+        tc_fence_after();
+        if (ok) {
+            const int q = warp & 3;
+            const int row = 32 * q + lane;
+            const int gi = i0 + row;
+            const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+            const float invT = (float)(1.0 / (double)T);
+            float2* __restrict__ R = dp->R;
+            for (int c0 = 0; c0 < kTile; c0 += 16) {
+                uint32_t rr[16], ri[16], ir[16], ii[16];
+                tmem_ld16(tl + c0, rr);
+                tmem_ld16(tl + 128 + c0, ri);
+                tmem_ld16(tl + 256 + c0, ir);
+                tmem_ld16(tl + 384 + c0, ii);
+                tmem_wait_ld();
+                if (gi >= M) continue;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int gj = j0 + c0 + c;
+                    if (gj >= M || (diag && gj < gi)) continue;
+                    float re = (__uint_as_float(rr[c]) + __uint_as_float(ii[c])) * invT;
+                    float im = (__uint_as_float(ir[c]) - __uint_as_float(ri[c])) * invT;
+                    if (gj == gi) im = 0.f;
+                    R[(int64_t)gi * M + gj] = make_float2(re, im);
+                    if (gj != gi) R[(int64_t)gj * M + gi] = make_float2(re, -im);
+                }
+            }
+        }
+        tc_fence_before();
+    }
+    __syncthreads();
+    if (*abort_flag && threadIdx.x == 0) set_status(dp->status, FM_ERR_TIMEOUT);
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+}  // namespace
+
+size_t cov_tc_smem_bytes() { return kSmemBytes; }
+
+cudaError_t launch_covariance_tc(const FrameDesc* d, const void* tmaps, int n_frames, int max_M, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(cov_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    const int nt = (max_M + kTile - 1) / kTile;
+    dim3 grid(nt * (nt + 1) / 2, n_frames);
+    cov_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(d, reinterpret_cast<const CUtensorMap*>(tmaps));
+    return cudaGetLastError();
+}
+
+}  // namespace fm

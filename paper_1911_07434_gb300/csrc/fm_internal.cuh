@@ -8,7 +8,7 @@
 
 namespace fm {
 
-constexpr int kLMax = 64;      // largest sketch size l handled by the small solver
+constexpr int kLMax = 48;      // largest sketch size l handled by the small solver
 constexpr int kMMax = 1024;    // largest array size M (scan keeps e^{j pi 64 m1 q}, m1 < 16, in registers)
 constexpr int kKPadMax = 32;   // largest padded K in the scan
 
@@ -147,16 +147,19 @@ __device__ __forceinline__ void set_status(int* status, int code) {
 
 // ---------------------------------------------------------- launch wrappers --
 // Implemented in the .cu files; each returns cudaGetLastError() after launching.
-cudaError_t launch_grid_table(const GridDesc* g, int n_grids, int max_L, cudaStream_t s);
+cudaError_t launch_grid_table(const GridDesc* g, int n_grids, int max_L, const FrameDesc* d, int n_frames,
+                              cudaStream_t s);
+cudaError_t launch_covariance_tc(const FrameDesc* d, const void* tmaps, int n_frames, int max_M, cudaStream_t s);
+size_t cov_tc_smem_bytes();
 cudaError_t launch_covariance(const FrameDesc* d, int n_frames, int max_M, cudaStream_t s);
 cudaError_t launch_sketch(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, bool any_gather,
                           bool any_dense, cudaStream_t s);
-cudaError_t launch_orth(const FrameDesc* d, int n_frames, int max_l, int pass, cudaStream_t s);
-cudaError_t launch_final(const FrameDesc* d, int n_frames, int max_l, cudaStream_t s);
+cudaError_t launch_orth(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, cudaStream_t s);
+cudaError_t launch_final(const FrameDesc* d, int n_frames, int max_M, int max_l, cudaStream_t s);
 cudaError_t launch_scan(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s);
 cudaError_t launch_peaks(const FrameDesc* d, int n_frames, int max_K, cudaStream_t s);
 cudaError_t launch_test_matrix(uint64_t seed, uint64_t frame_id, int M, int l, float2* out, cudaStream_t s);
 cudaError_t launch_sample_indices(uint64_t seed, uint64_t frame_id, int M, int l, int* out, cudaStream_t s);
-size_t small_smem_bytes(int l);
+size_t small_smem_bytes(int max_M, int l);
 
 }  // namespace fm

@@ -1,5 +1,7 @@
 // host.cu -- C ABI of the library: context, validation, workspace planning,
 // launch sequencing, per-stage timing and the continuous-batching server.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,6 +53,8 @@ struct fm_ctx {
     double stage_ms[FM_N_STAGES] = {};
     int stage_n[FM_N_STAGES] = {};
     uint64_t launches = 0;
+    int cov_path = FM_COV_AUTO;
+    int last_cov_path = 0;
     // serving state
     struct Slot;
     std::vector<Slot*> slots;
@@ -188,7 +192,7 @@ const char* check_frame(const fm_frame& f) {
     if (!std::isfinite(f.grid.theta0_deg) || !std::isfinite(f.grid.step_deg)) return "grid is not finite";
     if (p.method != FM_RAND_SAMPLING && p.method != FM_RAND_PROJECTION) return "method must be 1 or 2";
     if (p.K < 1 || p.K > p.l) return "need 1 <= K <= l";
-    if (p.l > M || p.l > fm::kLMax) return "need l <= min(M, 64)";
+    if (p.l > M || p.l > fm::kLMax) return "need l <= min(M, 48)";
     if (p.t < 0 || p.t > 8) return "t must be in [0, 8]";
     if (p.prec != FM_PREC_FP32) return "only FM_PREC_FP32 is available";
     if (p.refine != 0) return "refine is reserved";
@@ -201,7 +205,7 @@ const char* check_frame(const fm_frame& f) {
 }
 
 struct Plan {
-    size_t desc_off, grid_off, total;
+    size_t desc_off, tmap_off, grid_off, total;
     std::vector<size_t> R, C, V, Us, idx;  // per-frame offsets (R == SIZE_MAX: caller-owned)
     std::vector<int> grid_of;
     std::vector<GridDesc> grids;
@@ -216,6 +220,8 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
     size_t off = 0;
     pl.desc_off = off;
     off = aup(off + sizeof(FrameDesc) * (size_t)n);
+    pl.tmap_off = off;  // TMA tensor maps of the frames' X (tensor-core covariance)
+    if (need_R) off = aup(off + sizeof(CUtensorMap) * (size_t)n);
     std::map<GridKey, int> gmap;
     pl.grid_of.assign(n, -1);
     if (need_grid) {
@@ -310,14 +316,75 @@ Maxes maxes_of(const std::vector<FrameDesc>& ds) {
     return m;
 }
 
+// ---- TMA tensor maps for the tensor-core covariance ----------------------
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// A frame can take the tensor-core path if its rows can be described to TMA:
+// 16-byte aligned base and an even leading dimension (row stride multiple of 16 B).
+bool tc_eligible(const FrameDesc& d) {
+    return (reinterpret_cast<uintptr_t>(d.X) % 16 == 0) && (d.ldx % 2 == 0) && d.M >= 1 && d.T >= 1 &&
+           (int64_t)2 * d.T < ((int64_t)1 << 32);
+}
+
+// X viewed as an M x 2T FP32 matrix, boxes of 128 rows x 32 floats, 128-byte swizzle.
+bool encode_tmap(const FrameDesc& d, CUtensorMap* out) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)(2 * (int64_t)d.T), (cuuint64_t)d.M};
+    cuuint64_t strides[1] = {(cuuint64_t)(d.ldx * 8)};
+    cuuint32_t box[2] = {32, 128};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(d.X), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// Decide the covariance path for these frames and, for the tensor-core path,
+// encode one tensor map per frame.  Fails only if the context forces the
+// tensor-core path and a frame cannot take it.
+fm_status choose_cov_path(fm_ctx* c, const std::vector<FrameDesc>& ds, std::vector<CUtensorMap>& maps, bool* tc_out) {
+    bool tc = (c->cov_path != FM_COV_SIMT);
+    for (size_t b = 0; tc && b < ds.size(); ++b) tc = tc_eligible(ds[b]);
+    if (tc) {
+        maps.resize(ds.size());
+        for (size_t b = 0; tc && b < ds.size(); ++b) tc = encode_tmap(ds[b], &maps[b]);
+    }
+    if (!tc) maps.clear();
+    if (!tc && c->cov_path == FM_COV_TC)
+        return fail(c, FM_ERR_INVALID_ARG, "tensor-core covariance needs 16-byte aligned X with an even ldx");
+    c->last_cov_path = tc ? FM_COV_TC : FM_COV_SIMT;
+    *tc_out = tc;
+    return FM_OK;
+}
+
+fm_status launch_cov(fm_ctx* c, bool tc, FrameDesc* dd, const char* tm_dev, int n, int max_M, cudaStream_t s) {
+    if (tc) return stage(c, 1, s, [&] { return fm::launch_covariance_tc(dd, tm_dev, n, max_M, s); });
+    return stage(c, 1, s, [&] { return fm::launch_covariance(dd, n, max_M, s); });
+}
+
 // Uploads descriptors (+ grids) and returns device pointers.
-fm_status upload_descs(fm_ctx* c, const Plan& pl, std::vector<FrameDesc>& ds, cudaStream_t s, FrameDesc** dd,
-                       GridDesc** dg) {
+fm_status upload_descs(fm_ctx* c, const Plan& pl, std::vector<FrameDesc>& ds, const std::vector<CUtensorMap>& maps,
+                       cudaStream_t s, FrameDesc** dd, GridDesc** dg) {
     const size_t bytes = pl.grid_off + sizeof(GridDesc) * pl.grids.size();
     char* host = nullptr;
     fm_status st = staging(c, bytes, &host);
     if (st != FM_OK) return st;
     memcpy(host + pl.desc_off, ds.data(), sizeof(FrameDesc) * ds.size());
+    if (!maps.empty()) memcpy(host + pl.tmap_off, maps.data(), sizeof(CUtensorMap) * maps.size());
     std::vector<GridDesc> g = pl.grids;
     for (size_t i = 0; i < g.size(); ++i) g[i].qtab = reinterpret_cast<float2*>(c->arena + pl.qtab[i]);
     if (!g.empty()) memcpy(host + pl.grid_off, g.data(), sizeof(GridDesc) * g.size());
@@ -335,12 +402,12 @@ fm_status run_subspace_chain(fm_ctx* c, FrameDesc* dd, int n, const Maxes& mx, c
     });
     if (st != FM_OK) return st;
     for (int p = 1; p <= mx.t; ++p) {
-        st = stage(c, kStOrth, s, [&] { return fm::launch_orth(dd, n, mx.l, p, s); });
+        st = stage(c, kStOrth, s, [&] { return fm::launch_orth(dd, n, mx.M, mx.l, p, s); });
         if (st != FM_OK) return st;
         st = stage(c, kStSketch, s, [&] { return fm::launch_sketch(dd, n, mx.M, mx.l, p, false, true, s); });
         if (st != FM_OK) return st;
     }
-    return stage(c, kStFinal, s, [&] { return fm::launch_final(dd, n, mx.l, s); });
+    return stage(c, kStFinal, s, [&] { return fm::launch_final(dd, n, mx.M, mx.l, s); });
 }
 
 }  // namespace
@@ -426,15 +493,19 @@ fm_status fm_run(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream) {
         d.qtab = reinterpret_cast<float2*>(c->arena + pl.qtab[pl.grid_of[b]]);
         ds[b] = d;
     }
+    std::vector<CUtensorMap> maps;
+    bool tc = false;
+    st = choose_cov_path(c, ds, maps, &tc);
+    if (st != FM_OK) return st;
     FrameDesc* dd;
     GridDesc* dg;
-    st = upload_descs(c, pl, ds, s, &dd, &dg);
+    st = upload_descs(c, pl, ds, maps, s, &dd, &dg);
     if (st != FM_OK) return st;
     const Maxes mx = maxes_of(ds);
     const int ng = (int)pl.grids.size();
-    st = stage(c, kStGrid, s, [&] { return fm::launch_grid_table(dg, ng, mx.L, s); });
+    st = stage(c, kStGrid, s, [&] { return fm::launch_grid_table(dg, ng, mx.L, dd, n, s); });
     if (st != FM_OK) return st;
-    st = stage(c, kStCov, s, [&] { return fm::launch_covariance(dd, n, mx.M, s); });
+    st = launch_cov(c, tc, dd, c->arena + pl.tmap_off, n, mx.M, s);
     if (st != FM_OK) return st;
     st = run_subspace_chain(c, dd, n, mx, s);
     if (st != FM_OK) return st;
@@ -452,7 +523,8 @@ fm_status fm_covariance(fm_ctx* c, const void* X, int n, int M, int T, int64_t l
     fm_status st = set_device(c);
     if (st != FM_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const size_t bytes = aup(sizeof(FrameDesc) * (size_t)n);
+    const size_t tmap_off = aup(sizeof(FrameDesc) * (size_t)n);
+    const size_t bytes = tmap_off + sizeof(CUtensorMap) * (size_t)n;
     st = ensure_arena(c, bytes);
     if (st != FM_OK) return st;
     std::vector<FrameDesc> ds(n);
@@ -465,14 +537,19 @@ fm_status fm_covariance(fm_ctx* c, const void* X, int n, int M, int T, int64_t l
         d.R = reinterpret_cast<float2*>(R) + (int64_t)b * M * M;
         ds[b] = d;
     }
+    std::vector<CUtensorMap> maps;
+    bool tc = false;
+    st = choose_cov_path(c, ds, maps, &tc);
+    if (st != FM_OK) return st;
     char* host = nullptr;
     st = staging(c, bytes, &host);
     if (st != FM_OK) return st;
     memcpy(host, ds.data(), sizeof(FrameDesc) * n);
-    st = upload(c, host, c->arena, sizeof(FrameDesc) * n, s);
+    if (tc) memcpy(host + tmap_off, maps.data(), sizeof(CUtensorMap) * n);
+    st = upload(c, host, c->arena, bytes, s);
     if (st != FM_OK) return st;
     FrameDesc* dd = reinterpret_cast<FrameDesc*>(c->arena);
-    return stage(c, kStCov, s, [&] { return fm::launch_covariance(dd, n, M, s); });
+    return launch_cov(c, tc, dd, c->arena + tmap_off, n, M, s);
 }
 
 fm_status fm_subspace(fm_ctx* c, const void* R, int n, int M, const fm_params* p, uint64_t frame_id0, void* U,
@@ -528,7 +605,7 @@ fm_status fm_subspace(fm_ctx* c, const void* R, int n, int M, const fm_params* p
     }
     FrameDesc* dd;
     GridDesc* dg;
-    st = upload_descs(c, pl, ds, s, &dd, &dg);
+    st = upload_descs(c, pl, ds, {}, s, &dd, &dg);
     if (st != FM_OK) return st;
     return run_subspace_chain(c, dd, n, maxes_of(ds), s);
 }
@@ -567,10 +644,10 @@ fm_status fm_spectrum(fm_ctx* c, const void* U, int n, int M, int ncols, double 
     }
     FrameDesc* dd;
     GridDesc* dg;
-    st = upload_descs(c, pl, ds, s, &dd, &dg);
+    st = upload_descs(c, pl, ds, {}, s, &dd, &dg);
     if (st != FM_OK) return st;
     const Maxes mx = maxes_of(ds);
-    st = stage(c, kStGrid, s, [&] { return fm::launch_grid_table(dg, (int)pl.grids.size(), mx.L, s); });
+    st = stage(c, kStGrid, s, [&] { return fm::launch_grid_table(dg, (int)pl.grids.size(), mx.L, nullptr, 0, s); });
     if (st != FM_OK) return st;
     return stage(c, kStScan, s, [&] { return fm::launch_scan(dd, n, mx.L, mx.M, mx.kpad, s); });
 }
@@ -665,6 +742,16 @@ fm_status fm_stage_times(fm_ctx* c, double* total_ms, int* launches, int reset) 
     }
     return FM_OK;
 }
+
+fm_status fm_set_cov_path(fm_ctx* c, int path) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (path != FM_COV_AUTO && path != FM_COV_SIMT && path != FM_COV_TC)
+        return fail(c, FM_ERR_INVALID_ARG, "unknown covariance path %d", path);
+    c->cov_path = path;
+    return FM_OK;
+}
+
+int fm_last_cov_path(const fm_ctx* c) { return c ? c->last_cov_path : 0; }
 
 uint64_t fm_launch_count(const fm_ctx* c) { return c ? c->launches + c->serve_launches : 0; }
 

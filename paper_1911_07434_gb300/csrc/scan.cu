@@ -19,9 +19,16 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__global__ void grid_table_kernel(const GridDesc* __restrict__ grids) {
-    const GridDesc g = grids[blockIdx.y];
+// blockIdx.y < n_grids: fill the (q_hi, q_lo) table of grid blockIdx.y;
+// blockIdx.y == n_grids: clear the per-frame status words (first kernel of a run).
+__global__ void grid_table_kernel(const GridDesc* __restrict__ grids, int n_grids, const FrameDesc* __restrict__ descs,
+                                  int n_frames) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if ((int)blockIdx.y == n_grids) {
+        if (descs && i < n_frames && descs[i].status) *descs[i].status = 0;
+        return;
+    }
+    const GridDesc g = grids[blockIdx.y];
     if (i >= g.L) return;
     const double th = (g.theta0 + (double)i * g.step) * (3.14159265358979323846 / 180.0);
     const double q = 2.0 * g.d_wl * sin(th);
@@ -118,9 +125,11 @@ cudaError_t launch_nb(const FrameDesc* d, int n_frames, int max_L, int max_M, in
 
 }  // namespace
 
-cudaError_t launch_grid_table(const GridDesc* g, int n_grids, int max_L, cudaStream_t s) {
-    dim3 grid((max_L + 255) / 256, n_grids);
-    grid_table_kernel<<<grid, 256, 0, s>>>(g);
+cudaError_t launch_grid_table(const GridDesc* g, int n_grids, int max_L, const FrameDesc* d, int n_frames,
+                              cudaStream_t s) {
+    const int gx = (max(max_L, d ? n_frames : 0) + 255) / 256;
+    dim3 grid(gx, n_grids + 1);
+    grid_table_kernel<<<grid, 256, 0, s>>>(g, n_grids, d, n_frames);
     return cudaGetLastError();
 }
 

@@ -1,91 +1,148 @@
 // sketch.cu -- the range sketch C = R Pi of Algorithms 1 and 2 and the power
 // step C = R V of Eq. 11 (Sec. III).
 //
-//   pass 0, projection : C = R Omega, Omega (M x l complex Gaussian) generated
-//                        from Philox into shared memory, never stored.
+//   pass 0, projection : Omega (M x l complex Gaussian, Philox) is generated once
+//                        per frame into the basis buffer V, then C = R V.
 //   pass 0, sampling   : C = R(:, I) = conj(R(I, :))^T (R is exactly Hermitian
 //                        as written by the covariance kernel), I the sorted
 //                        Fisher-Yates index set; rows of R are read coalesced.
 //   pass p >= 1        : C = R V with V the basis from the previous orth step.
 //
-// The dense form is HBM-bound (R is read once per pass: 8 M^2 bytes for
-// 8 M^2 l flops); each CTA owns 64 rows of R and all l columns of C.
+// Dense form: each CTA owns 64 rows of R and all l columns of C.  Threads hold a
+// 4-row x ceil(l/8)-column register tile; R and V stream through shared memory
+// in 32-column chunks with the next chunk prefetched into registers while the
+// current one is consumed.  FP32 products, two-level accumulation (per chunk,
+// then into the running sum).  R is read from HBM exactly once per pass.
 #include "fm_internal.cuh"
 
 namespace fm {
 namespace {
 
-constexpr int kRows = 64;     // rows of R per CTA
-constexpr int kKc = 64;       // reduction chunk (columns of R / rows of Pi)
-constexpr int kThreads = 256;
-constexpr int kColGroups = kThreads / kRows;  // 4 threads share a row
-constexpr int kMaxQ = kLMax / kColGroups;     // accumulators per thread
+constexpr int kRows = 64;      // rows of R per CTA
+constexpr int kKc = 32;        // reduction chunk
+constexpr int kThreads = 128;  // 16 row groups x 8 column groups
+constexpr int kRowT = 4;       // rows per thread (rg + 16 r)
+constexpr int kColG = 8;       // column groups (cg + 8 q)
+constexpr int kMaxQ = kLMax / kColG;
+constexpr int kALoads = kRows * kKc / kThreads;  // 16 complex per thread per chunk
 
-// dynamic smem: As[kRows][kKc+1] + Bs[kKc][l]
+template <int NQ>
 __global__ void __launch_bounds__(kThreads) sketch_dense_kernel(const FrameDesc* __restrict__ descs, int pass) {
     extern __shared__ float4 smem_raw[];
-    float2* As = reinterpret_cast<float2*>(smem_raw);
+    float2(*As)[kRows][kKc + 1] = reinterpret_cast<float2(*)[kRows][kKc + 1]>(smem_raw);
+    float2* Bbase = reinterpret_cast<float2*>(smem_raw) + 2 * kRows * (kKc + 1);
     const FrameDesc* dp = descs + blockIdx.y;
     const int M = dp->M, l = dp->l;
     if (pass > dp->t) return;
     if (pass == 0 && dp->method != FM_RAND_PROJECTION) return;
     const int r0 = blockIdx.x * kRows;
     if (r0 >= M) return;
-    float2* Bs = As + kRows * (kKc + 1);
     const float2* __restrict__ R = dp->R;
     const float2* __restrict__ V = dp->V;
     float2* __restrict__ C = dp->C;
-    const uint64_t seed = dp->seed, fid = dp->frame_id;
 
     const int tid = threadIdx.x;
-    const int row = tid / kColGroups, cg = tid % kColGroups;
-    const int nq = (l - cg + kColGroups - 1) / kColGroups;  // columns cg, cg+4, ...
+    const int rg = tid >> 3, cg = tid & 7;
 
-    float2 acc[kMaxQ], tmp[kMaxQ];
+    float2 acc[kRowT][NQ], tmp[kRowT][NQ];
 #pragma unroll
-    for (int q = 0; q < kMaxQ; ++q) {
-        acc[q] = make_float2(0.f, 0.f);
-        tmp[q] = make_float2(0.f, 0.f);
-    }
+    for (int r = 0; r < kRowT; ++r)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[r][q] = tmp[r][q] = make_float2(0.f, 0.f);
 
-    for (int k0 = 0; k0 < M; k0 += kKc) {
-        // A chunk: rows r0.., cols k0.. of R (coalesced: 64 consecutive complex per row)
-        for (int e = tid; e < kRows * kKc; e += kThreads) {
-            const int rr = e / kKc, kk = e % kKc;
+    // prefetch registers: A chunk (64 x 32) = 16 per thread; B chunk (32 x l) <= 16 per thread
+    float2 pa[kALoads], pb[kALoads];
+    const int nb = kKc * l;
+    auto gload = [&](int k0) {
+#pragma unroll
+        for (int u = 0; u < kALoads; ++u) {
+            const int e = tid + u * kThreads;
+            const int rr = e >> 5, kk = e & 31;  // kKc == 32
             const int gr = r0 + rr, gk = k0 + kk;
-            As[rr * (kKc + 1) + kk] = (gr < M && gk < M) ? R[(int64_t)gr * M + gk] : make_float2(0.f, 0.f);
+            pa[u] = (gr < M && gk < M) ? R[(int64_t)gr * M + gk] : make_float2(0.f, 0.f);
         }
-        // B chunk: rows k0.. of Omega (generated) or V
-        for (int e = tid; e < kKc * l; e += kThreads) {
-            const int kk = e / l, j = e % l;
-            const int gk = k0 + kk;
+#pragma unroll
+        for (int u = 0; u < kALoads; ++u) {
+            const int e = tid + u * kThreads;
             float2 v = make_float2(0.f, 0.f);
-            if (gk < M) v = (pass == 0) ? gaussian_entry(seed, fid, gk, j) : V[(int64_t)gk * l + j];
-            Bs[kk * l + j] = v;
+            if (e < nb) {
+                const int kk = e / l, j = e - kk * l;
+                const int gk = k0 + kk;
+                if (gk < M) v = V[(int64_t)gk * l + j];
+            }
+            pb[u] = v;
         }
-        __syncthreads();
-        const float2* arow = As + row * (kKc + 1);
-#pragma unroll 4
+    };
+    auto sstore = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < kALoads; ++u) {
+            const int e = tid + u * kThreads;
+            As[buf][e >> 5][e & 31] = pa[u];
+        }
+#pragma unroll
+        for (int u = 0; u < kALoads; ++u) {
+            const int e = tid + u * kThreads;
+            if (e < nb) {
+                const int kk = e / l, j = e - kk * l;
+                Bbase[(buf * kKc + kk) * l + j] = pb[u];
+            }
+        }
+    };
+
+    const int nchunks = (M + kKc - 1) / kKc;
+    gload(0);
+    sstore(0);
+    __syncthreads();
+    for (int c = 0; c < nchunks; ++c) {
+        const int buf = c & 1;
+        if (c + 1 < nchunks) gload((c + 1) * kKc);
+#pragma unroll 8
         for (int kk = 0; kk < kKc; ++kk) {
-            const float2 a = arow[kk];
-            const float2* brow = Bs + kk * l + cg;
+            float2 a[kRowT], b[NQ];
 #pragma unroll
-            for (int q = 0; q < kMaxQ; ++q)
-                if (q < nq) cfma(tmp[q], a, brow[q * kColGroups]);
-        }
+            for (int r = 0; r < kRowT; ++r) a[r] = As[buf][rg + 16 * r][kk];
 #pragma unroll
-        for (int q = 0; q < kMaxQ; ++q) {
-            acc[q] = cadd(acc[q], tmp[q]);
-            tmp[q] = make_float2(0.f, 0.f);
+            for (int q = 0; q < NQ; ++q) {
+                const int j = cg + kColG * q;
+                b[q] = (j < l) ? Bbase[(buf * kKc + kk) * l + j] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int r = 0; r < kRowT; ++r)
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) cfma(tmp[r][q], a[r], b[q]);
         }
+        if ((c & 3) == 3 || c + 1 == nchunks) {
+#pragma unroll
+            for (int r = 0; r < kRowT; ++r)
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    acc[r][q] = cadd(acc[r][q], tmp[r][q]);
+                    tmp[r][q] = make_float2(0.f, 0.f);
+                }
+        }
+        if (c + 1 < nchunks) sstore(buf ^ 1);
         __syncthreads();
     }
-    const int gr = r0 + row;
-    if (gr < M) {
 #pragma unroll
-        for (int q = 0; q < kMaxQ; ++q)
-            if (q < nq) C[(int64_t)gr * l + cg + q * kColGroups] = acc[q];
+    for (int r = 0; r < kRowT; ++r) {
+        const int gr = r0 + rg + 16 * r;
+        if (gr >= M) continue;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int j = cg + kColG * q;
+            if (j < l) C[(int64_t)gr * l + j] = acc[r][q];
+        }
     }
+}
+
+// Omega -> V for projection frames (pass 0), one thread per entry.
+__global__ void omega_kernel(const FrameDesc* __restrict__ descs) {
+    const FrameDesc* dp = descs + blockIdx.y;
+    if (dp->method != FM_RAND_PROJECTION) return;
+    const int M = dp->M, l = dp->l;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= M * l) return;
+    dp->V[e] = gaussian_entry(dp->seed, dp->frame_id, e / l, e % l);
 }
 
 // pass 0, sampling: C[i][j] = conj(R[I[j]][i])
@@ -125,6 +182,18 @@ __global__ void sample_indices_kernel(uint64_t seed, uint64_t fid, int M, int l,
     }
 }
 
+template <int NQ>
+cudaError_t launch_dense(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, cudaStream_t s) {
+    const size_t smem = sizeof(float2) * (2 * (size_t)kRows * (kKc + 1) + 2 * (size_t)kKc * max_l);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(sketch_dense_kernel<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    sketch_dense_kernel<NQ><<<dim3((max_M + kRows - 1) / kRows, n_frames), kThreads, smem, s>>>(d, pass);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_sketch(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, bool any_gather,
@@ -136,14 +205,18 @@ cudaError_t launch_sketch(const FrameDesc* d, int n_frames, int max_M, int max_l
         if (e != cudaSuccess) return e;
     }
     if (!any_dense) return cudaSuccess;
-    const size_t smem = sizeof(float2) * ((size_t)kRows * (kKc + 1) + (size_t)kKc * max_l);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(sketch_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    if (pass == 0) {
+        omega_kernel<<<dim3((max_M * max_l + 255) / 256, n_frames), 256, 0, s>>>(d);
+        cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    sketch_dense_kernel<<<dim3((max_M + kRows - 1) / kRows, n_frames), kThreads, smem, s>>>(d, pass);
-    return cudaGetLastError();
+    const int nq = (max_l + kColG - 1) / kColG;
+    if (nq <= 1) return launch_dense<1>(d, n_frames, max_M, max_l, pass, s);
+    if (nq <= 2) return launch_dense<2>(d, n_frames, max_M, max_l, pass, s);
+    if (nq <= 3) return launch_dense<3>(d, n_frames, max_M, max_l, pass, s);
+    if (nq <= 4) return launch_dense<4>(d, n_frames, max_M, max_l, pass, s);
+    if (nq <= 6) return launch_dense<6>(d, n_frames, max_M, max_l, pass, s);
+    return launch_dense<kMaxQ>(d, n_frames, max_M, max_l, pass, s);
 }
 
 cudaError_t launch_test_matrix(uint64_t seed, uint64_t frame_id, int M, int l, float2* out, cudaStream_t s) {

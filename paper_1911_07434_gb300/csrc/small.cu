@@ -1,383 +1,487 @@
-// small.cu -- per-frame l x l work of Algorithms 1 and 2 (Sec. III), one CTA per frame.
+// small.cu -- per-frame l x l work of Algorithms 1 and 2 (Sec. III).
 //
 //   ORTH  (power step, Eq. 11):  V = orth(C)
 //   FINAL (Alg. 1 lines 5-9 / Alg. 2 lines 7-10):
-//         H = P^H C  with P = V (t >= 1), the index selection (sampling, t = 0)
-//                    or the Gaussian Pi regenerated from Philox (projection, t = 0)
-//         W = pinv(H)                                    (Eq. 8)
-//         C = Q R_c                                      (QR in place of SVD(C); same subspace)
-//         B = R_c W R_c^H, eig(B) = U_B L_B U_B^H        (rank restriction)
-//         U_s = Q U_B[:, :ncols]
+//         H = P^H C   with P = V (t >= 1; for projection with t = 0, V holds Pi)
+//                     or H = C(I, :) = R(I, I) (sampling, t = 0)       (Eq. 8)
+//         C = Q R_c                         (QR in place of SVD(C): Q = U_c Z, Z unitary)
+//         B = R_c W R_c^H, W = H^+          (rank restriction)
+//         eig(B) = U_B L_B U_B^H, U_s = Q U_B[:, :ncols]
 //
-// orth / QR use CholeskyQR2 with a mixed-precision first pass: the Gram matrix
-// C^H C is accumulated in double-float arithmetic (each FP32 product split
-// exactly with an FMA, sums carried as unevaluated (hi, lo) pairs) and factored
-// in FP64, so the first pass survives cond(C) up to ~1/u_fp32; the second pass
-// (cond ~ 1) runs in FP32.  The two Hermitian l x l eigenproblems use a
-// parallel-ordered (round-robin) two-sided complex Jacobi method in FP32 with
-// the relative stopping test |a_pq| <= tol sqrt(|a_pp a_qq|).
+// One thread-block cluster per frame: CTA r of the cluster keeps rows
+// [r*Mr, (r+1)*Mr) of C (and V) in shared memory for the whole kernel, so
+// every M-long operation is a row-local pass over shared memory; l x l Gram
+// matrices are formed as per-CTA partials and summed over the cluster through
+// distributed shared memory in rank order (deterministic), after which every
+// CTA holds the same l x l matrix and runs the same l x l algorithms.
+//
+// Precision (no FP64 -- its rate on GB300 is a small fraction of FP32):
+//   - QR: CholeskyQR2.  Pass 1 accumulates C^H C in double-float arithmetic
+//     (FP32 products split exactly with an FMA, sums kept as hi + lo pairs),
+//     factors and inverts it in double-float, and applies the inverse with
+//     double-float accumulation, so the pass survives cond(C) up to ~1/u_fp32
+//     without amplifying rounding into the range of Q; pass 2 (cond ~ 1) is FP32.
+//   - W: H is Hermitian positive definite in exact arithmetic, so
+//     B = R_c H^{-1} R_c^H = F F^H with F = R_c R_h^{-1}, H = R_h^H R_h (FP32
+//     Cholesky).  If the Cholesky breaks down, W is the eigenvalue pseudo-inverse
+//     of H (pivots with |lambda| <= l eps max|lambda| dropped).
+//   - eig(B): two-sided complex Jacobi in FP32, round-robin parallel ordering,
+//     relative stopping test |b_pq| <= tol sqrt(|b_pp b_qq|), followed by one
+//     Rayleigh-Ritz correction of the leading eigenspace with double-float sums
+//     (see refine_subspace).
+#include <cooperative_groups.h>
 #include <float.h>
 
 #include "fm_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace fm {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kRowsChunk = 16;     // rows of an M x l operand staged per step
-constexpr int kMaxItems = (kLMax * kLMax + kThreads - 1) / kThreads;  // Gram items per thread
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxRows = 128;   // rows of C / V held by one CTA
 constexpr int kMaxSweeps = 30;
 constexpr float kJacobiTol = 1e-6f;
 
 enum Mode { kOrth = 0, kFinal = 1 };
-enum Src { kMem = 0, kOmega = 1 };
 
+// ------------------------------------------------------------ double-float --
+// Error-free transformations.  Every product and sum here uses the _rn
+// intrinsics, which the compiler never contracts into an FMA: a contraction of
+// p = a*b into the following add would change p's rounding and void the exact
+// (hi, lo) splits.
+struct df {
+    float hi, lo;
+};
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return df{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ df quick_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return df{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df dd_add(df x, df y) {
+    const df s = two_sum(x.hi, y.hi);
+    return quick_two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, x.lo), y.lo));
+}
+__device__ __forceinline__ df dd_neg(df x) { return df{-x.hi, -x.lo}; }
+__device__ __forceinline__ df dd_mul(df x, df y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return quick_two_sum(p, e);
+}
+__device__ __forceinline__ df dd_div(df x, df y) {
+    const float q1 = __fdiv_rn(x.hi, y.hi);
+    const df r = dd_add(x, dd_neg(dd_mul(df{q1, 0.f}, y)));
+    return quick_two_sum(q1, __fdiv_rn(r.hi, y.hi));
+}
+__device__ __forceinline__ df dd_sqrt(df x) {
+    if (!(x.hi > 0.f)) return df{0.f, 0.f};
+    const float s = __fsqrt_rn(x.hi);
+    const float p = __fmul_rn(s, s);
+    const float e = __fmaf_rn(s, s, -p);
+    const float num = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p), e), x.lo);
+    return quick_two_sum(s, __fdiv_rn(num, __fmul_rn(2.f, s)));
+}
+// s += a * b with the product split exactly (its error kept in lo)
+__device__ __forceinline__ void dd_acc(df& s, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);
+    const df t = two_sum(s.hi, p);
+    s.hi = t.hi;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(t.lo, pe));
+}
+// complex double-float, stored as float4 (re.hi, re.lo, im.hi, im.lo)
+struct zd {
+    df re, im;
+};
+__device__ __forceinline__ zd zload(const float4& v) { return zd{df{v.x, v.y}, df{v.z, v.w}}; }
+__device__ __forceinline__ float4 zpack(const zd& z) { return make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo); }
+__device__ __forceinline__ zd zadd(zd a, zd b) { return zd{dd_add(a.re, b.re), dd_add(a.im, b.im)}; }
+// conj(a) * b
+__device__ __forceinline__ zd zmulc(zd a, zd b) {
+    return zd{dd_add(dd_mul(a.re, b.re), dd_mul(a.im, b.im)), dd_add(dd_mul(a.re, b.im), dd_neg(dd_mul(a.im, b.re)))};
+}
+__device__ __forceinline__ zd zmul(zd a, zd b) {
+    return zd{dd_add(dd_mul(a.re, b.re), dd_neg(dd_mul(a.im, b.im))), dd_add(dd_mul(a.re, b.im), dd_mul(a.im, b.re))};
+}
+__device__ __forceinline__ zd zscale(zd a, df s) { return zd{dd_mul(a.re, s), dd_mul(a.im, s)}; }
+__device__ __forceinline__ zd zneg(zd a) { return zd{dd_neg(a.re), dd_neg(a.im)}; }
+
+// ------------------------------------------------------------------ layout --
 struct Sm {
-    double2* G64;  // l*l   (pass-1 Gram / factor)
-    double2* R64;  // l*l   (pass-1 inverse)
-    float2* G;     // l*l   (FP32 Gram / factor)
-    float2* Ri;    // l*l   (triangular inverse, FP32)
-    float2* Rc;    // l*l   (accumulated R factor of the QR)
-    float2* H;     // l*l   (core matrix, then B)
-    float2* Z;     // l*l   (eigenvectors)
-    float2* Y;     // l*l   (temp)
-    float2* ca;    // kRowsChunk*l
-    float2* cb;    // kRowsChunk*l
+    float2* Cs;    // Mr x l   rows of C (Q after the QR)
+    float2* Vs;    // Mr x l   rows of V (FINAL, until H is formed)
+    float4* Gd;    // l x l    double-float Gram / Cholesky factor   (aliases Vs)
+    float4* Xd;    // l x l    double-float inverse                  (aliases Vs)
+    float2* Gf;    // l x l    FP32 Gram / Cholesky factor           (aliases Vs)
+    float2* Xf;    // l x l    FP32 inverse                          (aliases Vs)
+    float4* part;  // l x l    per-CTA partial Gram (float4 or float2 view)
+    float2* T;     // l x l    temp                                  (aliases part)
+    float2* Rc;    // l x l    R factor of C = Q R_c
+    float2* H;     // l x l    core matrix, then B
+    float2* Z;     // l x l    eigenvectors
     float* w;      // l
     int* perm;     // l
-    float4* rot;   // kLMax/2
-    int2* pairs;   // kLMax/2
-    int* flags;    // 8
-    double* dscal; // 8
-    double* dinv;  // kLMax
+    float4* rot;   // l/2+1
+    int2* pairs;   // l/2+1
+    int* act;      // l/2+1
+    int* items;    // phase-B item table
+    int* flags;    // kMaxSweeps + 8
+    float* scal;   // 8
+    float4* dscal; // 4
 };
 
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline size_t smem_layout(int l, Sm* sm, char* base) {
+__host__ __device__ inline size_t smem_layout(int Mr, int l, Sm* sm, char* base) {
     size_t off = 0;
     auto take = [&](size_t bytes) {
-        size_t o = off;
-        off = align16(off + bytes);
+        const size_t o = off;
+        off = a16(off + bytes);
         return base ? base + o : nullptr;
     };
-    const size_t ll = (size_t)l * l;
-    // G64 and R64 are only live in the first CholQR pass; they alias G/Ri/Y/Z
-    char* u0 = take(2 * ll * sizeof(double2));
+    const size_t ll = (size_t)l * l, rows = (size_t)Mr * l;
+    const int np = (l + 1) / 2 + 1;
+    char* Cs = take(rows * sizeof(float2));
+    const size_t u1 = rows * sizeof(float2) > 2 * ll * sizeof(float4) ? rows * sizeof(float2) : 2 * ll * sizeof(float4);
+    char* U1 = take(u1);
+    char* part = take(ll * sizeof(float4));
     char* Rc = take(ll * sizeof(float2));
     char* H = take(ll * sizeof(float2));
-    char* ca = take(kRowsChunk * (size_t)l * sizeof(float2));
-    char* cb = take(kRowsChunk * (size_t)l * sizeof(float2));
+    char* Z = take(ll * sizeof(float2));
     char* w = take(l * sizeof(float));
     char* perm = take(l * sizeof(int));
-    char* rot = take((kLMax / 2 + 1) * sizeof(float4));
-    char* pairs = take((kLMax / 2 + 1) * sizeof(int2));
-    char* flags = take(8 * sizeof(int));
-    char* dscal = take(8 * sizeof(double));
-    char* dinv = take(kLMax * sizeof(double));
+    char* rot = take(np * sizeof(float4));
+    char* pairs = take(np * sizeof(int2));
+    char* act = take(np * sizeof(int));
+    char* items = take((size_t)(np * (np + 1) / 2 + np * l) * sizeof(int));
+    char* flags = take((kMaxSweeps + 8) * sizeof(int));
+    char* scal = take(8 * sizeof(float));
+    char* dscal = take(4 * sizeof(float4));
     if (sm) {
-        sm->G64 = reinterpret_cast<double2*>(u0);
-        sm->R64 = reinterpret_cast<double2*>(u0) + ll;
-        sm->G = reinterpret_cast<float2*>(u0);
-        sm->Ri = reinterpret_cast<float2*>(u0) + ll;
-        sm->Y = reinterpret_cast<float2*>(u0) + 2 * ll;
-        sm->Z = reinterpret_cast<float2*>(u0) + 3 * ll;
+        sm->Cs = reinterpret_cast<float2*>(Cs);
+        sm->Vs = reinterpret_cast<float2*>(U1);
+        sm->Gd = reinterpret_cast<float4*>(U1);
+        sm->Xd = reinterpret_cast<float4*>(U1) + ll;
+        sm->Gf = reinterpret_cast<float2*>(U1);
+        sm->Xf = reinterpret_cast<float2*>(U1) + ll;
+        sm->part = reinterpret_cast<float4*>(part);
+        sm->T = reinterpret_cast<float2*>(part);
         sm->Rc = reinterpret_cast<float2*>(Rc);
         sm->H = reinterpret_cast<float2*>(H);
-        sm->ca = reinterpret_cast<float2*>(ca);
-        sm->cb = reinterpret_cast<float2*>(cb);
+        sm->Z = reinterpret_cast<float2*>(Z);
         sm->w = reinterpret_cast<float*>(w);
         sm->perm = reinterpret_cast<int*>(perm);
         sm->rot = reinterpret_cast<float4*>(rot);
         sm->pairs = reinterpret_cast<int2*>(pairs);
+        sm->act = reinterpret_cast<int*>(act);
+        sm->items = reinterpret_cast<int*>(items);
         sm->flags = reinterpret_cast<int*>(flags);
-        sm->dscal = reinterpret_cast<double*>(dscal);
-        sm->dinv = reinterpret_cast<double*>(dinv);
+        sm->scal = reinterpret_cast<float*>(scal);
+        sm->dscal = reinterpret_cast<float4*>(dscal);
     }
     return off;
 }
 
-// ------------------------------------------------------------ double-float --
-struct df {
-    float hi, lo;
-};
-__device__ __forceinline__ void df_add_prod(df& s, float a, float b) {
-    const float p = a * b;
-    const float pe = fmaf(a, b, -p);  // exact: a*b = p + pe
-    const float t = s.hi + p;         // TwoSum(s.hi, p) = t + e
-    const float bp = t - s.hi;
-    const float e = (s.hi - (t - bp)) + (p - bp);
-    s.hi = t;
-    s.lo += e + pe;
-}
-__device__ __forceinline__ df df_add(df a, df b) {
-    const float t = a.hi + b.hi;
-    const float bp = t - a.hi;
-    const float e = (a.hi - (t - bp)) + (b.hi - bp);
-    df r;
-    r.hi = t;
-    r.lo = e + a.lo + b.lo;
-    return r;
-}
-
-// --------------------------------------------------------------- staging ---
-// dst[r*l + j] = row (m0 + r) of an M x l operand (zeros past M).
-__device__ __forceinline__ void load_chunk(const float2* __restrict__ src, int src_kind, const FrameDesc& d,
-                                           int M, int l, int m0, float2* dst) {
-    for (int e = threadIdx.x; e < kRowsChunk * l; e += kThreads) {
-        const int r = e / l, j = e % l;
-        const int m = m0 + r;
-        float2 v = make_float2(0.f, 0.f);
-        if (m < M) v = (src_kind == kOmega) ? gaussian_entry(d.seed, d.frame_id, m, j) : src[(int64_t)m * l + j];
-        dst[e] = v;
-    }
-}
-
-__device__ __forceinline__ void item_coords(int e, int l, bool herm, int& i, int& j) {
-    if (!herm) {
-        i = e / l;
-        j = e % l;
-        return;
-    }
+// --------------------------------------------------------------- helpers ---
+__device__ __forceinline__ void tri_coords(int e, int n, int& i, int& j) {
     i = 0;
-    while (e >= l - i) {
-        e -= l - i;
+    while (e >= n - i) {
+        e -= n - i;
         ++i;
     }
     j = i + e;
 }
 
-// G = A^H B (l x l) in FP32 with per-chunk two-level accumulation.  B == nullptr
-// means B = A (Hermitian: upper triangle computed, mirrored).
-__device__ void gram_fp32(const float2* A, int a_kind, const float2* B, const FrameDesc& d, int M, int l,
-                          const Sm& sm, float2* G) {
-    const bool herm = (B == nullptr);
-    const int nitems = herm ? l * (l + 1) / 2 : l * l;
-    int ii[kMaxItems], jj[kMaxItems];
-    float2 acc[kMaxItems];
-#pragma unroll
-    for (int q = 0; q < kMaxItems; ++q) {
-        const int e = threadIdx.x + q * kThreads;
-        ii[q] = jj[q] = 0;
-        if (e < nitems) item_coords(e, l, herm, ii[q], jj[q]);
-        acc[q] = make_float2(0.f, 0.f);
+__device__ void load_rows(const float2* __restrict__ src, float2* dst, int r0, int rows, int l) {
+    const float2* s = src + (int64_t)r0 * l;
+    const int n = rows * l;
+    if (((reinterpret_cast<uintptr_t>(s) & 15) == 0) && (n % 2 == 0)) {
+        const float4* s4 = reinterpret_cast<const float4*>(s);
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        for (int e = threadIdx.x; e < n / 2; e += kThreads) d4[e] = s4[e];
+    } else {
+        for (int e = threadIdx.x; e < n; e += kThreads) dst[e] = s[e];
     }
-    for (int m0 = 0; m0 < M; m0 += kRowsChunk) {
-        load_chunk(A, a_kind, d, M, l, m0, sm.ca);
-        if (!herm) load_chunk(B, kMem, d, M, l, m0, sm.cb);
-        __syncthreads();
-        const float2* bb = herm ? sm.ca : sm.cb;
-#pragma unroll
-        for (int q = 0; q < kMaxItems; ++q) {
-            if (threadIdx.x + q * kThreads < nitems) {
-                float2 t = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int r = 0; r < kRowsChunk; ++r) cfmac(t, sm.ca[r * l + ii[q]], bb[r * l + jj[q]]);
-                acc[q] = cadd(acc[q], t);
-            }
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int q = 0; q < kMaxItems; ++q) {
-        if (threadIdx.x + q * kThreads < nitems) {
-            float2 v = acc[q];
-            if (herm && ii[q] == jj[q]) v.y = 0.f;
-            G[ii[q] * l + jj[q]] = v;
-            if (herm && ii[q] != jj[q]) G[jj[q] * l + ii[q]] = cconj(v);
-        }
-    }
-    __syncthreads();
 }
 
-// G = A^H A in double-float accumulation, result in FP64.
-__device__ void gram_df64(const float2* A, const FrameDesc& d, int M, int l, const Sm& sm, double2* G) {
-    const int nitems = l * (l + 1) / 2;
-    int ii[kMaxItems], jj[kMaxItems];
-    df sre[kMaxItems], sim[kMaxItems];
-#pragma unroll
-    for (int q = 0; q < kMaxItems; ++q) {
-        const int e = threadIdx.x + q * kThreads;
-        ii[q] = jj[q] = 0;
-        if (e < nitems) item_coords(e, l, true, ii[q], jj[q]);
-        sre[q] = df{0.f, 0.f};
-        sim[q] = df{0.f, 0.f};
-    }
-    for (int m0 = 0; m0 < M; m0 += kRowsChunk) {
-        load_chunk(A, kMem, d, M, l, m0, sm.ca);
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < kMaxItems; ++q) {
-            if (threadIdx.x + q * kThreads < nitems) {
-                for (int r = 0; r < kRowsChunk; ++r) {
-                    const float2 a = sm.ca[r * l + ii[q]], b = sm.ca[r * l + jj[q]];
-                    // conj(a) * b = (ar br + ai bi) + j (ar bi - ai br)
-                    df_add_prod(sre[q], a.x, b.x);
-                    df_add_prod(sre[q], a.y, b.y);
-                    df_add_prod(sim[q], a.x, b.y);
-                    df_add_prod(sim[q], -a.y, b.x);
-                }
-            }
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int q = 0; q < kMaxItems; ++q) {
-        if (threadIdx.x + q * kThreads < nitems) {
-            const int i = ii[q], j = jj[q];
-            double2 v = make_double2((double)sre[q].hi + (double)sre[q].lo, (double)sim[q].hi + (double)sim[q].lo);
-            if (i == j) v.y = 0.0;
-            G[i * l + j] = v;
-            if (i != j) G[j * l + i] = make_double2(v.x, -v.y);
-        }
-    }
-    __syncthreads();
+__device__ void store_rows(const float2* src, float2* __restrict__ dst, int r0, int rows, int l) {
+    for (int e = threadIdx.x; e < rows * l; e += kThreads) dst[(int64_t)r0 * l + e] = src[e];
 }
 
-// -------------------------------------------------------------- Cholesky ----
-// In place: G (Hermitian) -> upper R with G = R^H R.  Returns false on a
-// non-positive pivot (the pivot is then clamped so the factor stays finite).
-template <typename T2, typename T>
-__device__ bool cholesky_upper(T2* G, int l, int* flag, T* scratch) {
-    if (threadIdx.x == 0) flag[0] = 0;
+// part <- A^H B over this CTA's rows, FP32 (float2 view of part).  herm: B == A,
+// upper triangle only (the reduction mirrors it).
+__device__ void gram_part_f(const float2* A, const float2* B, int rows, int l, bool herm, float2* part) {
+    const int n = herm ? l * (l + 1) / 2 : l * l;
+    for (int e = threadIdx.x; e < n; e += kThreads) {
+        int i, j;
+        if (herm) {
+            tri_coords(e, l, i, j);
+        } else {
+            i = e / l;
+            j = e - i * l;
+        }
+        float2 acc = make_float2(0.f, 0.f), t = make_float2(0.f, 0.f);
+        for (int r = 0; r < rows; ++r) {
+            cfmac(t, A[r * l + i], B[r * l + j]);
+            if ((r & 15) == 15) {
+                acc = cadd(acc, t);
+                t = make_float2(0.f, 0.f);
+            }
+        }
+        part[e] = cadd(acc, t);
+    }
+}
+
+// part <- A^H A over this CTA's rows in double-float (upper triangle, float4 entries).
+__device__ void gram_part_d(const float2* A, int rows, int l, float4* part) {
+    const int n = l * (l + 1) / 2;
+    for (int e = threadIdx.x; e < n; e += kThreads) {
+        int i, j;
+        tri_coords(e, l, i, j);
+        df re{0.f, 0.f}, im{0.f, 0.f};
+        for (int r = 0; r < rows; ++r) {
+            const float2 a = A[r * l + i], b = A[r * l + j];
+            dd_acc(re, a.x, b.x);
+            dd_acc(re, a.y, b.y);
+            dd_acc(im, a.x, b.y);
+            dd_acc(im, -a.y, b.x);
+        }
+        part[e] = zpack(zd{quick_two_sum(re.hi, re.lo), quick_two_sum(im.hi, im.lo)});
+    }
+}
+
+// Sum the cluster's partials (rank order) into out (l x l, full).  herm: the
+// partials hold the upper triangle and out receives the Hermitian matrix.
+__device__ void reduce_f(cg::cluster_group& cl, float2* part, float2* out, int l, bool herm) {
+    const int n = herm ? l * (l + 1) / 2 : l * l;
+    const unsigned nc = cl.num_blocks();
+    cl.sync();
+    for (int e = threadIdx.x; e < n; e += kThreads) {
+        float2 s = make_float2(0.f, 0.f);
+        for (unsigned r = 0; r < nc; ++r) s = cadd(s, cl.map_shared_rank(part, r)[e]);
+        if (herm) {
+            int i, j;
+            tri_coords(e, l, i, j);
+            if (i == j) s.y = 0.f;
+            out[i * l + j] = s;
+            if (i != j) out[j * l + i] = cconj(s);
+        } else {
+            out[e] = s;
+        }
+    }
+    cl.sync();
+}
+
+__device__ void reduce_d(cg::cluster_group& cl, float4* part, float4* out, int l) {
+    const int n = l * (l + 1) / 2;
+    const unsigned nc = cl.num_blocks();
+    cl.sync();
+    for (int e = threadIdx.x; e < n; e += kThreads) {
+        zd s = zload(cl.map_shared_rank(part, 0u)[e]);
+        for (unsigned r = 1; r < nc; ++r) s = zadd(s, zload(cl.map_shared_rank(part, r)[e]));
+        int i, j;
+        tri_coords(e, l, i, j);
+        if (i == j) s.im = df{0.f, 0.f};
+        out[i * l + j] = zpack(s);
+        if (i != j) out[j * l + i] = zpack(zd{s.re, dd_neg(s.im)});
+    }
+    cl.sync();
+}
+
+// ------------------------------------------------------ Cholesky / inverse --
+// In place, G = R^H R with R upper (FP32).  Returns false on a non-positive pivot.
+__device__ bool chol_f(float2* G, int l, const Sm& sm) {
+    if (threadIdx.x == 0) sm.flags[kMaxSweeps + 4] = 0;
     __syncthreads();
     for (int k = 0; k < l; ++k) {
         if (threadIdx.x == 0) {
-            T dkk = G[k * l + k].x;
-            if (!(dkk > (T)0)) {
-                flag[0] = 1;
-                dkk = (T)1e-30;
+            float d = G[k * l + k].x;
+            if (!(d > 0.f)) {
+                sm.flags[kMaxSweeps + 4] = 1;
+                d = 1e-30f;
             }
-            const T r = sqrt(dkk);
-            G[k * l + k].x = r;
-            G[k * l + k].y = (T)0;
-            scratch[0] = (T)1 / r;
+            const float r = sqrtf(d);
+            G[k * l + k] = make_float2(r, 0.f);
+            sm.scal[0] = 1.f / r;
         }
         __syncthreads();
-        const T inv = scratch[0];
-        for (int j = k + 1 + threadIdx.x; j < l; j += kThreads) {
-            G[k * l + j].x *= inv;
-            G[k * l + j].y *= inv;
-        }
+        const float inv = sm.scal[0];
+        for (int j = k + 1 + threadIdx.x; j < l; j += kThreads) G[k * l + j] = cscale(G[k * l + j], inv);
         __syncthreads();
         const int n = l - k - 1;
         for (int e = threadIdx.x; e < n * n; e += kThreads) {
             const int i = k + 1 + e / n, j = k + 1 + e % n;
             if (i <= j) {
-                const T2 a = G[k * l + i], b = G[k * l + j];
-                // G_ij -= conj(R_ki) R_kj
-                G[i * l + j].x -= a.x * b.x + a.y * b.y;
-                G[i * l + j].y -= a.x * b.y - a.y * b.x;
+                const float2 a = G[k * l + i], b = G[k * l + j];
+                G[i * l + j] = csub(G[i * l + j], cmulc(a, b));
             }
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < l * l; e += kThreads) {
-        const int i = e / l, j = e % l;
-        if (i > j) {
-            G[e].x = (T)0;
-            G[e].y = (T)0;
-        }
-    }
+    for (int e = threadIdx.x; e < l * l; e += kThreads)
+        if (e / l > e % l) G[e] = make_float2(0.f, 0.f);
     __syncthreads();
-    return flag[0] == 0;
+    return sm.flags[kMaxSweeps + 4] == 0;
 }
 
-// X = R^{-1} for upper triangular R with real positive diagonal, by right-looking
-// back substitution: row i of X is finalised as X_ij = (delta_ij - S_ij) / R_ii
-// (S_ij = sum_{m>i} R_im X_mj, accumulated in X itself), then its contribution
-// R_ki X_ij is added to the partial sums of all rows k < i in parallel.
-// dinv: scratch for the l reciprocals of the diagonal.
-template <typename T2, typename T>
-__device__ void tri_inv_upper(const T2* R, T2* X, int l, T* dinv) {
-    for (int e = threadIdx.x; e < l * l; e += kThreads) {
-        X[e].x = (T)0;
-        X[e].y = (T)0;
+__device__ bool chol_d(float4* G, int l, const Sm& sm) {
+    if (threadIdx.x == 0) sm.flags[kMaxSweeps + 4] = 0;
+    __syncthreads();
+    for (int k = 0; k < l; ++k) {
+        if (threadIdx.x == 0) {
+            df d = zload(G[k * l + k]).re;
+            if (!(d.hi > 0.f)) {
+                sm.flags[kMaxSweeps + 4] = 1;
+                d = df{1e-30f, 0.f};
+            }
+            const df r = dd_sqrt(d);
+            G[k * l + k] = make_float4(r.hi, r.lo, 0.f, 0.f);
+            const df inv = dd_div(df{1.f, 0.f}, r);
+            sm.dscal[0] = make_float4(inv.hi, inv.lo, 0.f, 0.f);
+        }
+        __syncthreads();
+        const df inv = df{sm.dscal[0].x, sm.dscal[0].y};
+        for (int j = k + 1 + threadIdx.x; j < l; j += kThreads) G[k * l + j] = zpack(zscale(zload(G[k * l + j]), inv));
+        __syncthreads();
+        const int n = l - k - 1;
+        for (int e = threadIdx.x; e < n * n; e += kThreads) {
+            const int i = k + 1 + e / n, j = k + 1 + e % n;
+            if (i <= j)
+                G[i * l + j] = zpack(zadd(zload(G[i * l + j]), zneg(zmulc(zload(G[k * l + i]), zload(G[k * l + j])))));
+        }
+        __syncthreads();
     }
-    for (int i = threadIdx.x; i < l; i += kThreads) dinv[i] = (T)1 / R[i * l + i].x;
+    for (int e = threadIdx.x; e < l * l; e += kThreads)
+        if (e / l > e % l) G[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    return sm.flags[kMaxSweeps + 4] == 0;
+}
+
+// X = R^{-1}, R upper with real positive diagonal; right-looking back
+// substitution (row i finalised as (delta_ij - S_ij)/R_ii, then R_ki X_ij added to
+// the partial sums S_kj of all rows k < i in parallel).
+__device__ void trinv_f(const float2* R, float2* X, int l) {
+    for (int e = threadIdx.x; e < l * l; e += kThreads) X[e] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int i = l - 1; i >= 0; --i) {
-        const T inv = dinv[i];
+        const float inv = 1.f / R[i * l + i].x;
         for (int j = i + threadIdx.x; j < l; j += kThreads) {
-            T2 x = X[i * l + j];
-            x.x = ((j == i) ? (T)1 : (T)0) - x.x;
-            x.y = -x.y;
-            x.x *= inv;
-            x.y *= inv;
-            X[i * l + j] = x;
+            const float2 s = X[i * l + j];
+            X[i * l + j] = make_float2((((j == i) ? 1.f : 0.f) - s.x) * inv, -s.y * inv);
         }
         __syncthreads();
         const int w = l - i;
         for (int e = threadIdx.x; e < i * w; e += kThreads) {
             const int k = e / w, j = i + e % w;
-            const T2 a = R[k * l + i], b = X[i * l + j];
-            X[k * l + j].x += a.x * b.x - a.y * b.y;
-            X[k * l + j].y += a.x * b.y + a.y * b.x;
+            cfma(X[k * l + j], R[k * l + i], X[i * l + j]);
         }
         __syncthreads();
     }
 }
 
-// dst (M x ld_dst) = src (M x l) * Tm (l x n_out, row stride ldt); columns
-// n_out..n_pad-1 of dst are zero-filled.  upper: Tm is upper triangular.
-// src may equal dst (rows are staged before they are overwritten).
-__device__ void apply_rows(const float2* src, float2* dst, const FrameDesc& d, int M, int l, const float2* Tm,
-                           int ldt, int n_out, int ld_dst, int n_pad, bool upper, const Sm& sm) {
-    for (int m0 = 0; m0 < M; m0 += kRowsChunk) {
-        load_chunk(src, kMem, d, M, l, m0, sm.ca);
+__device__ void trinv_d(const float4* R, float4* X, int l, const Sm& sm) {
+    for (int e = threadIdx.x; e < l * l; e += kThreads) X[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    for (int i = l - 1; i >= 0; --i) {
+        if (threadIdx.x == 0) {
+            const df inv = dd_div(df{1.f, 0.f}, zload(R[i * l + i]).re);
+            sm.dscal[1] = make_float4(inv.hi, inv.lo, 0.f, 0.f);
+        }
         __syncthreads();
-        for (int e = threadIdx.x; e < kRowsChunk * n_pad; e += kThreads) {
-            const int r = e / n_pad, c = e % n_pad;
-            const int m = m0 + r;
-            if (m >= M) continue;
-            float2 out = make_float2(0.f, 0.f);
-            if (c < n_out) {
-                const int kend = upper ? c : l - 1;
-                for (int k = 0; k <= kend; ++k) cfma(out, sm.ca[r * l + k], Tm[k * ldt + c]);
-            }
-            dst[(int64_t)m * ld_dst + c] = out;
+        const df inv = df{sm.dscal[1].x, sm.dscal[1].y};
+        for (int j = i + threadIdx.x; j < l; j += kThreads) {
+            zd s = zneg(zload(X[i * l + j]));
+            if (j == i) s.re = dd_add(s.re, df{1.f, 0.f});
+            X[i * l + j] = zpack(zscale(s, inv));
+        }
+        __syncthreads();
+        const int w = l - i;
+        for (int e = threadIdx.x; e < i * w; e += kThreads) {
+            const int k = e / w, j = i + e % w;
+            X[k * l + j] = zpack(zadd(zload(X[k * l + j]), zmul(zload(R[k * l + i]), zload(X[i * l + j]))));
         }
         __syncthreads();
     }
 }
 
-// dst (M x l) = src (M x l) * Ri with Ri upper triangular given as an
-// unevaluated sum Ri = hi + lo of two FP32 matrices; products with hi are split
-// exactly (FMA) and summed in double-float, so the result is the correctly
-// scaled combination up to one final rounding even when Ri is ill-conditioned.
-__device__ void apply_rows_df(const float2* src, float2* dst, const FrameDesc& d, int M, int l, const float2* Rhi,
-                              const float2* Rlo, const Sm& sm) {
-    for (int m0 = 0; m0 < M; m0 += kRowsChunk) {
-        load_chunk(src, kMem, d, M, l, m0, sm.ca);
-        __syncthreads();
-        for (int e = threadIdx.x; e < kRowsChunk * l; e += kThreads) {
-            const int r = e / l, c = e % l;
-            const int m = m0 + r;
-            if (m >= M) continue;
+// In place, row-local: rows of A (rows x l) <- A * X for X upper triangular given
+// in double-float (hi, lo) pairs.  Warp w owns rows w, w + 8, ...; a row is
+// overwritten only after the whole warp has read it.
+__device__ void apply_upper_d(float2* A, int rows, int l, const float4* X) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = warp; r < rows; r += kWarps) {
+        float2 out[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            out[h] = make_float2(0.f, 0.f);
+            if (c >= l) continue;
             df re{0.f, 0.f}, im{0.f, 0.f};
             for (int k = 0; k <= c; ++k) {
-                const float2 a = sm.ca[r * l + k];
-                const float2 h = Rhi[k * l + c], w = Rlo[k * l + c];
-                df_add_prod(re, a.x, h.x);
-                df_add_prod(re, -a.y, h.y);
-                df_add_prod(im, a.x, h.y);
-                df_add_prod(im, a.y, h.x);
-                re.lo = fmaf(a.x, w.x, fmaf(-a.y, w.y, re.lo));
-                im.lo = fmaf(a.x, w.y, fmaf(a.y, w.x, im.lo));
+                const float2 a = A[r * l + k];
+                const float4 x = X[k * l + c];  // (re.hi, re.lo, im.hi, im.lo)
+                dd_acc(re, a.x, x.x);
+                dd_acc(re, -a.y, x.z);
+                dd_acc(im, a.x, x.z);
+                dd_acc(im, a.y, x.x);
+                re.lo = fmaf(a.x, x.y, fmaf(-a.y, x.w, re.lo));
+                im.lo = fmaf(a.x, x.w, fmaf(a.y, x.y, im.lo));
             }
-            dst[(int64_t)m * l + c] = make_float2(re.hi + re.lo, im.hi + im.lo);
+            out[h] = make_float2(re.hi + re.lo, im.hi + im.lo);
         }
-        __syncthreads();
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            if (c < l) A[r * l + c] = out[h];
+        }
+        __syncwarp();
     }
+    __syncthreads();
 }
 
-// Rc <- Rk * Rc (both l x l upper triangular), using tmp as scratch.
-__device__ void upper_mul_inplace(const float2* Rk, float2* Rc, float2* tmp, int l) {
+// dst rows (rows x ncols, row stride ld) = A rows (rows x l) * T (l x ncols, row
+// stride ldt), FP32; upper: T upper triangular.  dst may equal A (row-local).
+__device__ void apply_f(const float2* A, float2* dst, int rows, int l, const float2* T, int ldt, int ncols, int ld,
+                        bool upper) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = warp; r < rows; r += kWarps) {
+        float2 out[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            out[h] = make_float2(0.f, 0.f);
+            if (c >= ncols) continue;
+            const int kend = upper ? c : l - 1;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int k = 0; k <= kend; ++k) cfma(acc, A[r * l + k], T[k * ldt + c]);
+            out[h] = acc;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            if (c < ncols) dst[(int64_t)r * ld + c] = out[h];
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
+// Rc <- R * Rc for upper triangular R, Rc (tmp: scratch).
+__device__ void upper_mul(const float2* R, float2* Rc, float2* tmp, int l) {
     for (int e = threadIdx.x; e < l * l; e += kThreads) {
         const int i = e / l, j = e % l;
         float2 s = make_float2(0.f, 0.f);
-        if (i <= j)
-            for (int k = i; k <= j; ++k) cfma(s, Rk[i * l + k], Rc[k * l + j]);
+        for (int k = i; k <= j; ++k) cfma(s, R[i * l + k], Rc[k * l + j]);
         tmp[e] = s;
     }
     __syncthreads();
@@ -385,130 +489,156 @@ __device__ void upper_mul_inplace(const float2* Rk, float2* Rc, float2* tmp, int
     __syncthreads();
 }
 
-// CholeskyQR2: src (M x l) = Q * Rc, Q written to dst (may be src).  Returns
-// false if a Cholesky pivot failed.
-__device__ bool cholqr2(const float2* src, float2* dst, const FrameDesc& d, int M, int l, const Sm& sm) {
-    // pass 1: double-float Gram, FP64 Cholesky and inverse
-    gram_df64(src, d, M, l, sm, sm.G64);
-    bool ok = cholesky_upper<double2, double>(sm.G64, l, sm.flags + 4, sm.dinv);
-    tri_inv_upper<double2, double>(sm.G64, sm.R64, l, sm.dinv);
-    // Rc = R1 in FP32, then R1^{-1} (FP64, in R64) as hi + lo FP32 pairs in the
-    // slots of G64 (G = hi, Ri = lo), which are free once Rc is taken.
+// CholeskyQR2 of the cluster-distributed rows A (rows x l, in place -> Q).
+// Rc receives the R factor (the same on every CTA).  Returns false on a breakdown.
+__device__ bool cholqr2(cg::cluster_group& cl, float2* A, int rows, int l, const Sm& sm) {
+    gram_part_d(A, rows, l, sm.part);
+    reduce_d(cl, sm.part, sm.Gd, l);
+    bool ok = chol_d(sm.Gd, l, sm);
+    trinv_d(sm.Gd, sm.Xd, l, sm);
     for (int e = threadIdx.x; e < l * l; e += kThreads) {
-        const double2 r = sm.G64[e];
-        sm.Rc[e] = make_float2((float)r.x, (float)r.y);
+        const float4 g = sm.Gd[e];
+        sm.Rc[e] = make_float2(g.x + g.y, g.z + g.w);
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < l * l; e += kThreads) {
-        const double2 r = sm.R64[e];
-        const float hx = (float)r.x, hy = (float)r.y;
-        sm.G[e] = make_float2(hx, hy);
-        sm.Ri[e] = make_float2((float)(r.x - (double)hx), (float)(r.y - (double)hy));
-    }
-    __syncthreads();
-    apply_rows_df(src, dst, d, M, l, sm.G, sm.Ri, sm);
-    // pass 2 in FP32 (cond ~ 1)
-    gram_fp32(dst, kMem, nullptr, d, M, l, sm, sm.G);
-    ok = cholesky_upper<float2, float>(sm.G, l, sm.flags + 4, reinterpret_cast<float*>(sm.dinv)) && ok;
-    tri_inv_upper<float2, float>(sm.G, sm.Ri, l, reinterpret_cast<float*>(sm.dinv));
-    apply_rows(dst, dst, d, M, l, sm.Ri, l, l, l, l, true, sm);
-    upper_mul_inplace(sm.G, sm.Rc, sm.Y, l);
+    apply_upper_d(A, rows, l, sm.Xd);
+    // pass 2 (FP32); Gf / Xf reuse the double-float slots
+    gram_part_f(A, A, rows, l, true, reinterpret_cast<float2*>(sm.part));
+    reduce_f(cl, reinterpret_cast<float2*>(sm.part), sm.Gf, l, true);
+    ok = chol_f(sm.Gf, l, sm) && ok;
+    trinv_f(sm.Gf, sm.Xf, l);
+    apply_f(A, A, rows, l, sm.Xf, l, l, l, true);
+    upper_mul(sm.Gf, sm.Rc, sm.T, l);
     return ok;
 }
 
 // ---------------------------------------------------------------- Jacobi ----
-// Eigendecomposition of the Hermitian n x n matrix A (destroyed; its diagonal
-// ends up holding the eigenvalues).  Z receives the eigenvectors (columns), w
-// the eigenvalues, perm the column order by eigenvalue descending (ties: lower
-// index).  Returns the number of sweeps, or -1 if the sweep cap was hit.
-__device__ int jacobi_herm(float2* A, float2* Z, float* w, int* perm, int n, const Sm& sm) {
+// Hermitian eigendecomposition of A (n x n, destroyed: its diagonal ends as the
+// eigenvalues), eigenvectors in the columns of Z, w the eigenvalues, perm the
+// column order by eigenvalue descending (ties: lower index).  One round = one
+// set of disjoint rotations: phase A computes them, phase B applies U^H A U as
+// independent 2x2 blocks (k, k') and rotates the columns of Z.  Returns the
+// number of sweeps or -1 if the sweep cap was hit.
+__device__ int jacobi(float2* A, float2* Z, float* w, int* perm, int n, const Sm& sm) {
+    const int ne = n + (n & 1), np = ne / 2, nr = ne - 1;
+    const int nblk = np * (np + 1) / 2, nitems = nblk + np * n;
     for (int e = threadIdx.x; e < n * n; e += kThreads)
         Z[e] = (e / n == e % n) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
-    const int ne = n + (n & 1), npairs = ne / 2, nr = ne - 1;
-    int sweeps = -1;
+    for (int e = threadIdx.x; e < nitems; e += kThreads) {
+        int a, b;
+        if (e < nblk) {
+            tri_coords(e, np, a, b);
+        } else {
+            a = (e - nblk) / n;
+            b = (e - nblk) % n;
+        }
+        sm.items[e] = (a << 16) | b;
+    }
+    for (int e = threadIdx.x; e < kMaxSweeps; e += kThreads) sm.flags[e] = 0;
     __syncthreads();
-    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-        if (threadIdx.x == 0) sm.flags[0] = 0;
-        __syncthreads();
+    int sweeps = -1;
+    for (int sweep = 0; sweep < kMaxSweeps && nr > 0; ++sweep) {
         for (int r = 0; r < nr; ++r) {
-            if (threadIdx.x < npairs) {
+            if (threadIdx.x < np) {
                 const int k = threadIdx.x;
-                const int pa = (k == 0) ? 0 : 1 + ((k - 1 + r) % nr);
-                const int pb = 1 + ((ne - 2 - k + r) % nr);
+                const int pa = (k == 0) ? 0 : 1 + (k - 1 + r) % nr;
+                const int pb = 1 + (ne - 2 - k + r) % nr;
                 const int p = min(pa, pb), q = max(pa, pb);
-                int2 pr = make_int2(-1, -1);
                 float4 rt = make_float4(1.f, 0.f, 1.f, 0.f);
-                if (q < n && nr > 0) {
+                int on = 0;
+                if (q < n) {
                     const float2 apq = A[p * n + q];
                     const float mag = sqrtf(cabs2(apq));
                     const float app = A[p * n + p].x, aqq = A[q * n + q].x;
                     if (mag > 1e-30f && mag > kJacobiTol * sqrtf(fabsf(app * aqq))) {
-                        const float phr = apq.x / mag, phi = apq.y / mag;
                         const float tau = (aqq - app) / (2.f * mag);
-                        float t;
-                        if (fabsf(tau) > 1e18f)
-                            t = 0.5f / tau;
-                        else
-                            t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+                        const float t = (fabsf(tau) > 1e18f)
+                                            ? 0.5f / tau
+                                            : (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
                         const float c = rsqrtf(fmaf(t, t, 1.f));
-                        rt = make_float4(c, t * c, phr, phi);
-                        pr = make_int2(p, q);
-                        sm.flags[0] = 1;
+                        rt = make_float4(c, t * c, apq.x / mag, apq.y / mag);
+                        on = 1;
+                        sm.flags[sweep] = 1;
                     }
                 }
-                sm.pairs[k] = pr;
+                sm.pairs[k] = make_int2(p, q < n ? q : -1);
                 sm.rot[k] = rt;
+                sm.act[k] = on;
             }
             __syncthreads();
-            // A <- A U and Z <- Z U, U = [[c, s], [-s conj(ph), c conj(ph)]]
-            for (int e = threadIdx.x; e < npairs * n; e += kThreads) {
-                const int k = e / n, i = e % n;
-                const int2 pr = sm.pairs[k];
-                if (pr.x < 0) continue;
-                const float4 rt = sm.rot[k];
-                const float c = rt.x, s = rt.y;
-                const float2 phc = make_float2(rt.z, -rt.w);
-                const float2 uqp = cscale(phc, -s), uqq = cscale(phc, c);
-                float2 x = A[i * n + pr.x], y = A[i * n + pr.y];
-                A[i * n + pr.x] = cadd(cscale(x, c), cmul(y, uqp));
-                A[i * n + pr.y] = cadd(cscale(x, s), cmul(y, uqq));
-                x = Z[i * n + pr.x];
-                y = Z[i * n + pr.y];
-                Z[i * n + pr.x] = cadd(cscale(x, c), cmul(y, uqp));
-                Z[i * n + pr.y] = cadd(cscale(x, s), cmul(y, uqq));
-            }
-            __syncthreads();
-            // A <- U^H A: row p = c row_p - s ph row_q, row q = s row_p + c ph row_q
-            for (int e = threadIdx.x; e < npairs * n; e += kThreads) {
-                const int k = e / n, j = e % n;
-                const int2 pr = sm.pairs[k];
-                if (pr.x < 0) continue;
-                const float4 rt = sm.rot[k];
-                const float c = rt.x, s = rt.y;
-                const float2 ph = make_float2(rt.z, rt.w);
-                const float2 x = A[pr.x * n + j], y = A[pr.y * n + j];
-                float2 np = cadd(cscale(x, c), cmul(y, cscale(ph, -s)));
-                float2 nq = cadd(cscale(x, s), cmul(y, cscale(ph, c)));
-                if (j == pr.y) {
-                    np = make_float2(0.f, 0.f);
-                    nq.y = 0.f;
+            for (int e = threadIdx.x; e < nitems; e += kThreads) {
+                const int it = sm.items[e];
+                const int a = it >> 16, b = it & 0xffff;
+                if (e < nblk) {
+                    // block (a, b), a <= b: rows (p_a, q_a), cols (p_b, q_b)
+                    if (!sm.act[a] && !sm.act[b]) continue;
+                    const int2 ra = sm.pairs[a], rb = sm.pairs[b];
+                    const float4 ua = sm.rot[a], ub = sm.rot[b];
+                    const bool qa = ra.y >= 0, qb = rb.y >= 0;
+                    float2 x00 = A[ra.x * n + rb.x];
+                    float2 x01 = qb ? A[ra.x * n + rb.y] : make_float2(0.f, 0.f);
+                    float2 x10 = qa ? A[ra.y * n + rb.x] : make_float2(0.f, 0.f);
+                    float2 x11 = (qa && qb) ? A[ra.y * n + rb.y] : make_float2(0.f, 0.f);
+                    {  // X <- X U_b, U = [[c, s], [-s conj(ph), c conj(ph)]]
+                        const float c = ub.x, s = ub.y;
+                        const float2 phc = make_float2(ub.z, -ub.w);
+                        const float2 u10 = cscale(phc, -s), u11 = cscale(phc, c);
+                        const float2 y00 = cadd(cscale(x00, c), cmul(x01, u10));
+                        const float2 y01 = cadd(cscale(x00, s), cmul(x01, u11));
+                        const float2 y10 = cadd(cscale(x10, c), cmul(x11, u10));
+                        const float2 y11 = cadd(cscale(x10, s), cmul(x11, u11));
+                        x00 = y00;
+                        x01 = y01;
+                        x10 = y10;
+                        x11 = y11;
+                    }
+                    {  // X <- U_a^H X: row p = c row_p - s ph row_q, row q = s row_p + c ph row_q
+                        const float c = ua.x, s = ua.y;
+                        const float2 ph = make_float2(ua.z, ua.w);
+                        const float2 m01 = cscale(ph, -s), m11 = cscale(ph, c);
+                        const float2 y00 = cadd(cscale(x00, c), cmul(m01, x10));
+                        const float2 y01 = cadd(cscale(x01, c), cmul(m01, x11));
+                        const float2 y10 = cadd(cscale(x00, s), cmul(m11, x10));
+                        const float2 y11 = cadd(cscale(x01, s), cmul(m11, x11));
+                        x00 = y00;
+                        x01 = y01;
+                        x10 = y10;
+                        x11 = y11;
+                    }
+                    if (a == b) {
+                        x00.y = 0.f;
+                        x11.y = 0.f;
+                        if (sm.act[a]) x01 = x10 = make_float2(0.f, 0.f);
+                    }
+                    A[ra.x * n + rb.x] = x00;
+                    if (qb) A[ra.x * n + rb.y] = x01;
+                    if (qa) A[ra.y * n + rb.x] = x10;
+                    if (qa && qb) A[ra.y * n + rb.y] = x11;
+                    if (a != b) {
+                        A[rb.x * n + ra.x] = cconj(x00);
+                        if (qb) A[rb.y * n + ra.x] = cconj(x01);
+                        if (qa) A[rb.x * n + ra.y] = cconj(x10);
+                        if (qa && qb) A[rb.y * n + ra.y] = cconj(x11);
+                    }
+                } else {
+                    // Z <- Z U_a on row b
+                    if (!sm.act[a]) continue;
+                    const int2 ra = sm.pairs[a];
+                    const float4 ua = sm.rot[a];
+                    const float c = ua.x, s = ua.y;
+                    const float2 phc = make_float2(ua.z, -ua.w);
+                    const float2 x = Z[b * n + ra.x], y = Z[b * n + ra.y];
+                    Z[b * n + ra.x] = cadd(cscale(x, c), cmul(y, cscale(phc, -s)));
+                    Z[b * n + ra.y] = cadd(cscale(x, s), cmul(y, cscale(phc, c)));
                 }
-                if (j == pr.x) {
-                    np.y = 0.f;
-                    nq = make_float2(0.f, 0.f);
-                }
-                A[pr.x * n + j] = np;
-                A[pr.y * n + j] = nq;
             }
             __syncthreads();
         }
-        const int any = sm.flags[0];
-        __syncthreads();
-        if (!any) {
+        if (!sm.flags[sweep]) {
             sweeps = sweep;
             break;
         }
     }
+    if (nr == 0) sweeps = 0;
     for (int i = threadIdx.x; i < n; i += kThreads) w[i] = A[i * n + i].x;
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += kThreads) {
@@ -521,33 +651,102 @@ __device__ int jacobi_herm(float2* A, float2* Z, float* w, int* perm, int n, con
     return sweeps;
 }
 
-// ---------------------------------------------------------------- kernel ----
-__global__ void __launch_bounds__(kThreads) small_kernel(const FrameDesc* __restrict__ descs, int mode, int pass) {
-    extern __shared__ float4 smem_raw[];
-    const FrameDesc d = descs[blockIdx.x];
-    if (mode == kOrth && d.t < pass) return;
-    const int M = d.M, l = d.l;
-    Sm sm;
-    smem_layout(l, &sm, reinterpret_cast<char*>(smem_raw));
-    bool ok = true;
+// One Rayleigh-Ritz correction of the leading ncols-dimensional eigenspace of B
+// (in T) after the FP32 Jacobi: with Z0 the FP32 eigenvectors (columns ordered by
+// perm), B' = Z0^H B Z0 is formed for the (other x leading) block with products
+// split exactly and double-float sums, and the leading columns are corrected to
+// first order, z_k <- z_k + sum_n z_n B'_nk / (lambda_k - lambda_n).  This removes
+// the u ||B|| / gap error of the FP32 eigenvectors without an eigensolve in higher
+// precision.  Result (l x ncols) in Rc.  Pairs with a vanishing gap are skipped.
+__device__ void refine_subspace(const Sm& sm, int l, int nc) {
+    float4* Y = sm.Gd;  // l x nc double-float: B Z0[:, lead]
+    for (int e = threadIdx.x; e < l * nc; e += kThreads) {
+        const int i = e / nc, k = e % nc;
+        const int zk = sm.perm[k];
+        df re{0.f, 0.f}, im{0.f, 0.f};
+        for (int j = 0; j < l; ++j) {
+            const float2 b = sm.T[i * l + j], z = sm.Z[j * l + zk];
+            dd_acc(re, b.x, z.x);
+            dd_acc(re, -b.y, z.y);
+            dd_acc(im, b.x, z.y);
+            dd_acc(im, b.y, z.x);
+        }
+        Y[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+    __syncthreads();
+    // E[n][k] = (Z0[:, n]^H Y[:, k]) / (lambda_k - lambda_n), n = nc..l-1 (into H, free after the Jacobi)
+    float2* E = sm.H;
+    const int no = l - nc;
+    float lmax = 0.f;
+    for (int i = 0; i < l; ++i) lmax = fmaxf(lmax, fabsf(sm.w[i]));
+    for (int e = threadIdx.x; e < no * nc; e += kThreads) {
+        const int n = nc + e / nc, k = e % nc;
+        const int zn = sm.perm[n], zk = sm.perm[k];
+        df re{0.f, 0.f}, im{0.f, 0.f};
+        for (int i = 0; i < l; ++i) {
+            const float2 z = sm.Z[i * l + zn];
+            const float4 y = Y[i * nc + k];
+            // conj(z) * y with y = (y.x + y.y) + j (y.z + y.w)
+            dd_acc(re, z.x, y.x);
+            dd_acc(re, z.y, y.z);
+            dd_acc(im, z.x, y.z);
+            dd_acc(im, -z.y, y.x);
+            re.lo = fmaf(z.x, y.y, fmaf(z.y, y.w, re.lo));
+            im.lo = fmaf(z.x, y.w, fmaf(-z.y, y.y, im.lo));
+        }
+        const float gap = sm.w[zk] - sm.w[zn];
+        float2 v = make_float2(0.f, 0.f);
+        if (fabsf(gap) > 1e-4f * lmax) v = make_float2((re.hi + re.lo) / gap, (im.hi + im.lo) / gap);
+        E[(n - nc) * nc + k] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < l * nc; e += kThreads) {
+        const int m = e / nc, k = e % nc;
+        float2 z = sm.Z[m * l + sm.perm[k]];
+        for (int n = 0; n < no; ++n) cfma(z, sm.Z[m * l + sm.perm[nc + n]], E[n * nc + k]);
+        sm.Rc[e] = z;
+    }
+    __syncthreads();
+}
 
+// ---------------------------------------------------------------- kernel ----
+__global__ void __launch_bounds__(kThreads) small_cluster_kernel(const FrameDesc* __restrict__ descs, int mode,
+                                                                 int pass) {
+    extern __shared__ float4 smem_raw[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int nc = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const FrameDesc* dp = descs + blockIdx.x / nc;
+    if (mode == kOrth && dp->t < pass) return;  // uniform over the cluster
+    const int M = dp->M, l = dp->l;
+    const int Mr = (M + nc - 1) / nc;
+    const int r0 = min(M, rank * Mr);
+    const int rows = min(Mr, M - r0);
+    Sm sm;
+    smem_layout(Mr, l, &sm, reinterpret_cast<char*>(smem_raw));
+
+    load_rows(dp->C, sm.Cs, r0, rows, l);
     if (mode == kOrth) {
-        ok = cholqr2(d.C, d.V, d, M, l, sm);
-        if (!ok && threadIdx.x == 0) set_status(d.status, FM_ERR_NO_CONVERGENCE);
+        __syncthreads();
+        const bool ok = cholqr2(cl, sm.Cs, rows, l, sm);
+        store_rows(sm.Cs, dp->V, r0, rows, l);
+        if (!ok && rank == 0 && threadIdx.x == 0) set_status(dp->status, FM_ERR_NO_CONVERGENCE);
         return;
     }
 
-    // H = P^H C  (core matrix of Eq. 8 / Alg. 2 line 7)
-    if (d.t >= 1) {
-        gram_fp32(d.V, kMem, d.C, d, M, l, sm, sm.H);
-    } else if (d.method == FM_RAND_SAMPLING) {
+    // H = P^H C  (core matrix, Eq. 8 / Alg. 2 line 7)
+    const bool sampled0 = (dp->method == FM_RAND_SAMPLING && dp->t == 0);
+    if (!sampled0) {
+        load_rows(dp->V, sm.Vs, r0, rows, l);
+        __syncthreads();
+        gram_part_f(sm.Vs, sm.Cs, rows, l, false, reinterpret_cast<float2*>(sm.part));
+        reduce_f(cl, reinterpret_cast<float2*>(sm.part), sm.H, l, false);
+    } else {
         for (int e = threadIdx.x; e < l * l; e += kThreads) {
             const int i = e / l, j = e % l;
-            sm.H[e] = d.C[(int64_t)d.idx[i] * l + j];
+            sm.H[e] = dp->C[(int64_t)dp->idx[i] * l + j];
         }
         __syncthreads();
-    } else {
-        gram_fp32(nullptr, kOmega, d.C, d, M, l, sm, sm.H);
     }
     // exact Hermitian part
     for (int e = threadIdx.x; e < l * l; e += kThreads) {
@@ -563,72 +762,117 @@ __global__ void __launch_bounds__(kThreads) small_kernel(const FrameDesc* __rest
     }
     __syncthreads();
 
-    // C = Q R_c ; Q -> V (V is no longer needed once H is formed)
-    ok = cholqr2(d.C, d.V, d, M, l, sm) && ok;
+    // C = Q R_c (Q in place of the C rows); V rows are dead from here on
+    bool ok = cholqr2(cl, sm.Cs, rows, l, sm);
 
-    // W = pinv(H) via H = Z diag(w) Z^H
-    const int s1 = jacobi_herm(sm.H, sm.Z, sm.w, sm.perm, l, sm);
-    if (threadIdx.x == 0) {
-        float amax = 0.f;
-        for (int i = 0; i < l; ++i) amax = fmaxf(amax, fabsf(sm.w[i]));
-        sm.dscal[0] = (double)((float)l * FLT_EPSILON * amax);
+    // B = R_c H^+ R_c^H
+    for (int e = threadIdx.x; e < l * l; e += kThreads) sm.Gf[e] = sm.H[e];
+    __syncthreads();
+    const bool pd = chol_f(sm.Gf, l, sm);
+    if (pd) {
+        trinv_f(sm.Gf, sm.Xf, l);
+        // F = R_c R_h^{-1} (upper) into T, B = F F^H into H
+        for (int e = threadIdx.x; e < l * l; e += kThreads) {
+            const int i = e / l, j = e % l;
+            float2 s = make_float2(0.f, 0.f);
+            for (int k = i; k <= j; ++k) cfma(s, sm.Rc[i * l + k], sm.Xf[k * l + j]);
+            sm.T[e] = s;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < l * l; e += kThreads) {
+            const int i = e / l, j = e % l;
+            if (i > j) continue;
+            float2 s = make_float2(0.f, 0.f);
+            for (int k = j; k < l; ++k) cfmaconj(s, sm.T[i * l + k], sm.T[j * l + k]);
+            if (i == j) s.y = 0.f;
+            sm.H[i * l + j] = s;
+            sm.H[j * l + i] = cconj(s);
+        }
+        __syncthreads();
+    } else {
+        // eigenvalue pseudo-inverse: H = Z diag(w) Z^H, B = (R_c Z) diag(w+) (R_c Z)^H
+        const int s0 = jacobi(sm.H, sm.Z, sm.w, sm.perm, l, sm);
+        if (s0 < 0) ok = false;
+        if (threadIdx.x == 0) {
+            float amax = 0.f;
+            for (int i = 0; i < l; ++i) amax = fmaxf(amax, fabsf(sm.w[i]));
+            sm.scal[1] = (float)l * FLT_EPSILON * amax;
+        }
+        __syncthreads();
+        const float thr = sm.scal[1];
+        for (int e = threadIdx.x; e < l * l; e += kThreads) {
+            const int i = e / l, k = e % l;
+            float2 s = make_float2(0.f, 0.f);
+            for (int m = i; m < l; ++m) cfma(s, sm.Rc[i * l + m], sm.Z[m * l + k]);
+            sm.T[e] = s;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < l; k += kThreads) sm.w[k] = (fabsf(sm.w[k]) > thr) ? 1.f / sm.w[k] : 0.f;
+        __syncthreads();
+        for (int e = threadIdx.x; e < l * l; e += kThreads) {
+            const int i = e / l, j = e % l;
+            if (i > j) continue;
+            float2 s = make_float2(0.f, 0.f);
+            for (int k = 0; k < l; ++k) cfmaconj(s, cscale(sm.T[i * l + k], sm.w[k]), sm.T[j * l + k]);
+            if (i == j) s.y = 0.f;
+            sm.H[i * l + j] = s;
+            sm.H[j * l + i] = cconj(s);
+        }
+        __syncthreads();
     }
+    // eig(B) = U_B L_B U_B^H in FP32 (B kept in T for the refinement below)
+    for (int e = threadIdx.x; e < l * l; e += kThreads) sm.T[e] = sm.H[e];
     __syncthreads();
-    const float thr = (float)sm.dscal[0];
-    // Y = R_c Z
-    for (int e = threadIdx.x; e < l * l; e += kThreads) {
-        const int i = e / l, k = e % l;
-        float2 s = make_float2(0.f, 0.f);
-        for (int m = i; m < l; ++m) cfma(s, sm.Rc[i * l + m], sm.Z[m * l + k]);
-        sm.Y[e] = s;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < l; k += kThreads) sm.w[k] = (fabsf(sm.w[k]) > thr) ? 1.f / sm.w[k] : 0.f;
-    __syncthreads();
-    // B = Y diag(w+) Y^H -> H
-    for (int e = threadIdx.x; e < l * l; e += kThreads) {
-        const int i = e / l, j = e % l;
-        if (i > j) continue;
-        float2 s = make_float2(0.f, 0.f);
-        for (int k = 0; k < l; ++k) cfmaconj(s, cscale(sm.Y[i * l + k], sm.w[k]), sm.Y[j * l + k]);
-        if (i == j) s.y = 0.f;
-        sm.H[i * l + j] = s;
-        sm.H[j * l + i] = cconj(s);
-    }
-    __syncthreads();
-    // eig(B): U_B
-    const int s2 = jacobi_herm(sm.H, sm.Z, sm.w, sm.perm, l, sm);
-    // U_s = Q U_B[:, perm[0..ncols-1]]  (Tp in Ri: l x ncols)
-    const int nc = d.ncols;
-    for (int e = threadIdx.x; e < l * nc; e += kThreads) {
-        const int k = e / nc, c = e % nc;
-        sm.Ri[e] = sm.Z[k * l + sm.perm[c]];
-    }
-    __syncthreads();
-    apply_rows(d.V, d.Us, d, M, l, sm.Ri, nc, nc, d.kpad, d.kpad, false, sm);
-    if (threadIdx.x == 0 && (s1 < 0 || s2 < 0 || !ok)) set_status(d.status, FM_ERR_NO_CONVERGENCE);
+    const int s2 = jacobi(sm.H, sm.Z, sm.w, sm.perm, l, sm);
+    const int nc_out = dp->ncols;
+    refine_subspace(sm, l, nc_out);
+    // U_s rows = Q rows * U_B[:, :ncols] (refined, in Rc: l x ncols)
+    apply_f(sm.Cs, dp->Us + (int64_t)r0 * dp->kpad, rows, l, sm.Rc, nc_out, nc_out, dp->kpad, false);
+    if (rank == 0 && threadIdx.x == 0 && (s2 < 0 || !ok)) set_status(dp->status, FM_ERR_NO_CONVERGENCE);
+}
+
+int cluster_size_for(int max_M) {
+    int nc = 1;
+    while (nc < 8 && (max_M + nc - 1) / nc > kMaxRows) nc *= 2;
+    return nc;
+}
+
+cudaError_t launch_small(const FrameDesc* d, int n_frames, int max_M, int max_l, int mode, int pass, cudaStream_t s) {
+    const int nc = cluster_size_for(max_M);
+    const int Mr = (max_M + nc - 1) / nc;
+    const size_t smem = smem_layout(Mr, max_l, nullptr, nullptr);
+    cudaError_t e = cudaFuncSetAttribute(small_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nc * n_frames), 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)nc;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, small_cluster_kernel, d, mode, pass);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t small_smem_bytes(int l) { return smem_layout(l, nullptr, nullptr); }
-
-static cudaError_t launch_small(const FrameDesc* d, int n_frames, int max_l, int mode, int pass, cudaStream_t s) {
-    const size_t smem = small_smem_bytes(max_l);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    small_kernel<<<n_frames, kThreads, smem, s>>>(d, mode, pass);
-    return cudaGetLastError();
+size_t small_smem_bytes(int max_M, int l) {
+    const int nc = cluster_size_for(max_M);
+    return smem_layout((max_M + nc - 1) / nc, l, nullptr, nullptr);
 }
 
-cudaError_t launch_orth(const FrameDesc* d, int n_frames, int max_l, int pass, cudaStream_t s) {
-    return launch_small(d, n_frames, max_l, kOrth, pass, s);
+cudaError_t launch_orth(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, cudaStream_t s) {
+    return launch_small(d, n_frames, max_M, max_l, kOrth, pass, s);
 }
 
-cudaError_t launch_final(const FrameDesc* d, int n_frames, int max_l, cudaStream_t s) {
-    return launch_small(d, n_frames, max_l, kFinal, 0, s);
+cudaError_t launch_final(const FrameDesc* d, int n_frames, int max_M, int max_l, cudaStream_t s) {
+    return launch_small(d, n_frames, max_M, max_l, kFinal, 0, s);
 }
 
 }  // namespace fm

@@ -56,7 +56,12 @@ def test_covariance_parity(ctx, M, T):
     rng = np.random.default_rng(M * 1000 + T)
     X = ((rng.standard_normal((M, T)) + 1j * rng.standard_normal((M, T))) * rng.uniform(0.1, 10, (M, 1)))
     X = X.astype(np.complex64)
-    R = ctx.covariance(dev(X))[0].cpu().numpy()
+    from paper_1911_07434_gb300 import binding
+    ctx.set_cov_path(binding.FM_COV_SIMT)
+    try:
+        R = ctx.covariance(dev(X))[0].cpu().numpy()
+    finally:
+        ctx.set_cov_path(binding.FM_COV_AUTO)
     Ro = oracle.covariance(X)
     # two-level FP32 sum: |error| <= (64 + ceil(T/64) + 2) u sum_t |x_it x_jt| / T <= that * sqrt(R_ii R_jj)
     d = np.sqrt(np.real(np.diag(Ro)))
@@ -66,12 +71,47 @@ def test_covariance_parity(ctx, M, T):
     assert np.all(np.diag(R).imag == 0)
 
 
+@pytest.mark.parametrize("M,T,ld", [(1, 2, 2), (3, 16, 16), (65, 17, 18), (127, 64, 64), (128, 200, 200),
+                                     (129, 100, 100), (130, 334, 334), (256, 1000, 1000), (300, 34, 40)])
+def test_covariance_tensor_core_parity(ctx, M, T, ld):
+    """tcgen05 path (3xTF32): each product is formed as hi*hi + hi*lo + lo*hi with
+    hi = rn_tf32(x), lo = rn_tf32(x - hi), so its relative error is below 3 * 2^-22;
+    the FP32 accumulator takes 6 MMAs per 16 snapshots (+ the in-MMA sum of 8), so
+    |error| <= (3 * 2^-22 + (6 T / 16 + 16) u) sum_t |x_it x_jt| / T (worst case),
+    and the mean relative error must stay at the FP32 level."""
+    from paper_1911_07434_gb300 import binding
+    rng = np.random.default_rng(M * 7 + T)
+    buf = ((rng.standard_normal((M, ld)) + 1j * rng.standard_normal((M, ld))) * rng.uniform(0.1, 10, (M, 1)))
+    buf = buf.astype(np.complex64)
+    X = dev(buf)[:, :T]
+    ctx.set_cov_path(binding.FM_COV_TC)
+    try:
+        R = ctx.covariance(X)[0].cpu().numpy()
+        assert ctx.last_cov_path() == binding.FM_COV_TC
+    finally:
+        ctx.set_cov_path(binding.FM_COV_AUTO)
+    Ro = oracle.covariance(buf[:, :T])
+    d = np.sqrt(np.real(np.diag(Ro)))
+    scale = np.outer(d, d)
+    bound = (3 * 2.0 ** -22 + (6 * T / 16 + 16) * U32) * scale
+    err = np.abs(R - Ro)
+    assert np.all(err <= bound), np.max(err / scale)
+    assert np.mean(err / scale) < 1e-6, np.mean(err / scale)
+    assert np.array_equal(R, R.conj().T)
+    assert np.all(np.diag(R).imag == 0)
+
+
 def test_covariance_batch_and_stride(ctx):
     rng = np.random.default_rng(3)
     B, M, T, ld = 3, 70, 90, 96
     buf = (rng.standard_normal((B, M, ld)) + 1j * rng.standard_normal((B, M, ld))).astype(np.complex64)
     Xt = dev(buf)[:, :, :T]
-    R = ctx.covariance(Xt).cpu().numpy()
+    from paper_1911_07434_gb300 import binding
+    ctx.set_cov_path(binding.FM_COV_SIMT)
+    try:
+        R = ctx.covariance(Xt).cpu().numpy()
+    finally:
+        ctx.set_cov_path(binding.FM_COV_AUTO)
     for b in range(B):
         Ro = oracle.covariance(buf[b, :, :T])
         d = np.sqrt(np.real(np.diag(Ro)))
@@ -119,7 +159,7 @@ def test_peaks_bit_exact(ctx, L, K):
 SUB_CASES = [
     # (frame factory, K, l, t, method)
     ("small", 3, 13, 0, 2), ("small", 3, 13, 1, 2), ("small", 3, 13, 2, 2), ("small", 3, 13, 0, 1),
-    ("small", 3, 3, 2, 2), ("small", 3, 64, 1, 1), ("mid", 5, 7, 1, 2), ("mid", 5, 7, 0, 1), ("mid", 5, 5, 1, 1),
+    ("small", 3, 3, 2, 2), ("small", 3, 48, 1, 1), ("mid", 5, 7, 1, 2), ("mid", 5, 7, 0, 1), ("mid", 5, 5, 1, 1),
     ("big", 8, 24, 1, 2), ("big", 8, 24, 0, 1), ("big", 8, 24, 1, 1),
 ]
 
@@ -135,7 +175,11 @@ def _frame(kind):
 @pytest.mark.parametrize("kind,K,l,t,method", SUB_CASES)
 def test_subspace_parity(ctx, kind, K, l, t, method):
     X = _frame(kind)
-    R32 = oracle.covariance(X).astype(np.complex64)   # both sides start from the same complex64 R
+    # both sides start from the same, exactly Hermitian complex64 R (as the covariance kernels write it:
+    # the sampling sketch reads rows of R as conjugated columns)
+    R32 = oracle.covariance(X).astype(np.complex64)
+    R32 = np.triu(R32) + np.triu(R32, 1).conj().T
+    R32[np.diag_indices_from(R32)] = R32.diagonal().real
     U, status = ctx.subspace(dev(R32), K, l, t, method, seed=11, frame_id0=5)
     Ug = U[0].cpu().numpy().astype(np.complex128)
     Uo, _, _ = oracle.fast_music(R32.astype(np.complex128), K, l, t, method, seed=11, frame_id=5)
