@@ -152,6 +152,54 @@ def run_reference(args):
     return 0
 
 
+TF32_PER_BF16 = 1.1 / 2.25   # nominal dense TF32 / BF16 tensor rate on GB300 (profiling recipe)
+
+
+def profile_traffic(name):
+    """DRAM bytes per launch (read + write) recorded in the committed ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    rd = wr = None
+    for line in open(path):
+        cells = [c.strip() for c in line.split("|")]
+        if len(cells) > 3 and cells[1] == "dram__bytes_read.sum":
+            rd = float(cells[2]) * (1e6 if cells[3].lower().startswith("mbyte") else 1e9 if cells[3].lower().startswith("gbyte") else 1.0)
+        if len(cells) > 3 and cells[1] == "dram__bytes_write.sum":
+            wr = float(cells[2]) * (1e6 if cells[3].lower().startswith("mbyte") else 1e9 if cells[3].lower().startswith("gbyte") else 1.0)
+    return (rd + wr) if rd is not None and wr is not None else None
+
+
+def roofline(stages, ctx, pk, pk_kind, B, M, T, K, L):
+    """Roofline entry for the covariance (the dominant contraction of the step).
+
+    achieved = algorithmic FP32 flops per launch (4 M^2 T per frame: the Hermitian
+    half of X X^H) / average launch time from CUDA events on the launching stream.
+    Tensor-core path: every FP32 product costs three TF32 MMAs (3xTF32), so the
+    peak is the TF32 dense peak / 3, the TF32 peak being the measured BF16 burst
+    peak x the nominal TF32/BF16 ratio.  CUDA-core path: FP32 FFMA peak from the
+    SM count, lanes and the measured maximum SM clock."""
+    from paper_1911_07434_gb300 import binding
+    cov_ms, cov_n = stages["covariance"]
+    avg_s = cov_ms / max(cov_n, 1) / 1e3
+    flops = 4.0 * M * M * T * B
+    achieved = flops / avg_s / 1e12
+    if ctx.last_cov_path() == binding.FM_COV_TC:
+        tf32 = pk.get("bf16_tflops", 1895.2) * TF32_PER_BF16
+        peak = tf32 / 3.0
+        return {"kernel": "covariance (cov_tc_kernel, tcgen05 kind::tf32, 3xTF32)", "bound": "tensor",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "frac_of_tf32_peak": achieved / tf32,
+                "traffic": profile_traffic("cov_tc_kernel_ula_M512_T1024_B64.md"),
+                "algorithmic_bytes": 8.0 * M * T * B + 8.0 * M * M * B, "avg_launch_ms": avg_s * 1e3,
+                "peak_source": f"TF32 = bf16_tflops {pk.get('bf16_tflops')} ({pk_kind}) x {TF32_PER_BF16:.4f}; "
+                               f"/3 for three TF32 MMAs per FP32 product"}
+    fp32 = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    return {"kernel": "covariance (cov_fp32_kernel)", "bound": "alu", "achieved": achieved, "peak": fp32,
+            "unit": "TFLOP/s", "frac": achieved / fp32, "traffic": None, "avg_launch_ms": avg_s * 1e3,
+            "peak_source": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x sm_max_mhz ({pk_kind})"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -261,18 +309,27 @@ def main():
     pk, pk_kind = peaks_json()
     names = list(stages.keys())
     dom = max(names, key=lambda n: stages[n][0])
-    cov_ms, cov_n = stages["covariance"]
-    cov_avg_s = cov_ms / max(cov_n, 1) / 1e3
-    cov_flops = 4.0 * M * M * T * B                  # Hermitian half of X X^H, real flops per launch
-    fp32_peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # TFLOP/s, FFMA pipes
-    roof = {"kernel": "covariance (cov_fp32_kernel)", "bound": "alu", "achieved": cov_flops / cov_avg_s / 1e12,
-            "peak": fp32_peak, "unit": "TFLOP/s", "frac": (cov_flops / cov_avg_s / 1e12) / fp32_peak,
-            "traffic": None, "avg_launch_ms": cov_avg_s * 1e3,
-            "peak_source": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
-                           f"(sm_max_mhz from MEASURED_PEAKS.json, {pk_kind})"}
+    roof = roofline(stages, ctx, pk, pk_kind, B, M, T, K, L)
+    tot = max(1e-9, sum(v[0] for v in stages.values()))
     stage_summary = {n: {"ms_per_launch": (stages[n][0] / stages[n][1]) if stages[n][1] else 0.0,
-                         "launches": stages[n][1], "share": stages[n][0] / max(1e-9, sum(v[0] for v in stages.values()))}
-                     for n in names}
+                         "launches": stages[n][1], "share": stages[n][0] / tot} for n in names}
+
+    # ---- single-frame latency (one fm_run per frame, device-resident) ----------
+    lat = []
+    one = frames[:1]
+    for _ in range(5):
+        ctx.run(one)
+    torch.cuda.synchronize()
+    for _ in range(max(20, args.steps)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.run(one)
+        e1.record(stream)
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    lat.sort()
+    single = {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+              "frames_per_s": 1e3 / lat[len(lat) // 2]}
 
     # ---- full-eig MUSIC on the same GPU -----------------------------------------
     full = None
@@ -311,7 +368,10 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(args.method, B),
-        "latency_ms": {"p50_step": srt[len(srt) // 2], "p99_step": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
+        "latency_ms": {"p50_step": srt[len(srt) // 2], "p99_step": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
+                       "single_frame": single},
+        "kernel_paths": {"covariance": "tensor" if ctx.last_cov_path() == binding.FM_COV_TC else "cuda-core",
+                         "scan": "tensor" if ctx.last_scan_path() == binding.FM_COV_TC else "cuda-core"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": roof, "dominant_stage": dom, "stages": stage_summary,

@@ -200,6 +200,18 @@ uint64_t fm_launch_count(const fm_ctx* ctx);
 fm_status fm_set_cov_path(fm_ctx* ctx, int path);
 int fm_last_cov_path(const fm_ctx* ctx);
 
+/* ---- scan kernel selection (same constants) -------------------------------------
+ * FM_COV_AUTO (default): inside fm_run, frames that share M, the number of U_s
+ * columns and the angle grid are scanned by one batched tensor-core kernel (the
+ * steering tile generated in registers serves every frame; tcgen05 MMAs, 3 TF32
+ * products per FP32 product); the angles of the main lobes (||U_s^H a||^2 above
+ * 4 times the number of U_s columns, where M - ||U_s^H a||^2 cancels) are then
+ * recomputed by the FP32 CUDA-core scan.
+ * Other batches use the FP32 CUDA-core scan.  fm_spectrum always uses the
+ * CUDA-core scan. */
+fm_status fm_set_scan_path(fm_ctx* ctx, int path);
+int fm_last_scan_path(const fm_ctx* ctx);
+
 /* ---- serving (continuous batching) ------------------------------------------
  * fm_serve_submit: enqueue one frame; the library admits queued frames into
  * device work as workspace within the budget frees up, overlapping them on its

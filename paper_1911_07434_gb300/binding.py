@@ -76,6 +76,8 @@ _SIGS = {
     "fm_launch_count": (c_uint64, [c_void_p]),
     "fm_set_cov_path": (c_int, [c_void_p, c_int]),
     "fm_last_cov_path": (c_int, [c_void_p]),
+    "fm_set_scan_path": (c_int, [c_void_p, c_int]),
+    "fm_last_scan_path": (c_int, [c_void_p]),
     "fm_serve_submit": (c_int, [c_void_p, POINTER(FmFrame), POINTER(c_uint64)]),
     "fm_serve_poll": (c_int, [c_void_p, c_uint64, POINTER(c_int)]),
 }
@@ -179,6 +181,14 @@ def fm_set_cov_path(ctx, path) -> int:
 
 def fm_last_cov_path(ctx) -> int:
     return load().fm_last_cov_path(ctx)
+
+
+def fm_set_scan_path(ctx, path) -> int:
+    return load().fm_set_scan_path(ctx, path)
+
+
+def fm_last_scan_path(ctx) -> int:
+    return load().fm_last_scan_path(ctx)
 
 
 def fm_serve_submit(ctx, frame: FmFrame):
@@ -326,6 +336,12 @@ class Context:
 
     def last_cov_path(self) -> int:
         return fm_last_cov_path(self.h)
+
+    def set_scan_path(self, path: int):
+        self._check(fm_set_scan_path(self.h, path), "fm_set_scan_path")
+
+    def last_scan_path(self) -> int:
+        return fm_last_scan_path(self.h)
 
     def serve_submit(self, frame: FmFrame) -> int:
         st, t = fm_serve_submit(self.h, frame)

@@ -19,12 +19,12 @@
 // the epilogue (TMEM -> registers -> R tile and its conjugate mirror).  Raw and
 // converted stages are double-buffered and handed over with mbarriers; every
 // wait is bounded and records FM_ERR_TIMEOUT in the frame status on expiry.
-#include <cuda.h>
-
-#include "fm_internal.cuh"
+#include "tc_common.cuh"
 
 namespace fm {
 namespace {
+
+using namespace tc;
 
 constexpr int kTile = 128;                         // complex rows per tile side
 constexpr int kRawBox = kTile * 32 * 4;            // 16 KB: 128 rows x 32 floats (16 complex)
@@ -37,100 +37,7 @@ constexpr int kThreads = 192;
 constexpr int kTiles = kNRaw * kRawStage + kNConv * kConvStage;   // 192 KB
 constexpr int kSmemBytes = kTiles + 1024 + 256;                   // + 1024-B alignment slack + barriers
 constexpr uint32_t kTmemCols = 512;
-constexpr long long kWaitCycles = 4000000000LL;                   // ~2 s at 2 GHz
-
-// ------------------------------------------------------------- PTX helpers --
-__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(n) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(sa(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait: false (and *abort set) if the phase did not complete in time.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
-    if (mbar_test(b, parity)) return true;
-    const long long t0 = clock64();
-    while (true) {
-        if (mbar_test(b, parity)) return true;
-        if (*abort) return false;
-        if (clock64() - t0 > kWaitCycles) {
-            *abort = 1;
-            return false;
-        }
-        __nanosleep(64);
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-            "r"(sa(dst)),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(sa(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ uint32_t tf32_rn(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-// K-major, 128-byte-swizzled shared-memory matrix descriptor (tcgen05):
-// start address >> 4 in [0,14), leading-dim offset (unused for this layout) = 1,
-// stride-dim offset = 1024 B (one 8-row x 128-B swizzle atom) in [32,46),
-// version 1 in [46,48), layout SWIZZLE_128B (2) in [61,64).
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-// Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
-// (bits 7-9 = bits 10-12 = 2), both K-major, N >> 3 in bits 17-22, M >> 4 in 24-28.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
-
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// byte offset of 16-byte chunk c of row r in a 128-byte-swizzled tile
-__device__ __forceinline__ uint32_t swz(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+constexpr uint32_t kIdesc = idesc_tf32(128, 256);  // M = 128 rows of X_I, N = 256 rows of [Xr_J; Xi_J]
 
 __device__ __forceinline__ void tile_coords(int b, int nt, int& ti, int& tj) {
     ti = 0;
@@ -256,12 +163,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint64_t b_hi = desc_sw128(bb + 32 * kk), b_lo = desc_sw128(bb + 64 + 32 * kk);
                     const uint64_t r_hi = desc_sw128(ar + 32 * kk), r_lo = desc_sw128(ar + 64 + 32 * kk);
                     const uint64_t i_hi = desc_sw128(ai + 32 * kk), i_lo = desc_sw128(ai + 64 + 32 * kk);
-                    mma_tf32(d_top, r_hi, b_hi, acc0);
-                    mma_tf32(d_top, r_hi, b_lo, 1u);
-                    mma_tf32(d_top, r_lo, b_hi, 1u);
-                    mma_tf32(d_bot, i_hi, b_hi, acc0);
-                    mma_tf32(d_bot, i_hi, b_lo, 1u);
-                    mma_tf32(d_bot, i_lo, b_hi, 1u);
+                    mma_tf32(d_top, r_hi, b_hi, kIdesc, acc0);
+                    mma_tf32(d_top, r_hi, b_lo, kIdesc, 1u);
+                    mma_tf32(d_top, r_lo, b_hi, kIdesc, 1u);
+                    mma_tf32(d_bot, i_hi, b_hi, kIdesc, acc0);
+                    mma_tf32(d_bot, i_hi, b_lo, kIdesc, 1u);
+                    mma_tf32(d_bot, i_lo, b_hi, kIdesc, 1u);
                 }
                 mma_commit(&conv_empty[slot]);  // frees the converted stage once these MMAs finish
             }
@@ -285,7 +192,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_arrive(&raw_empty[rs]);
         }
         // epilogue: rows 32 * (warp % 4) + lane of the tile
-        const bool ok = mbar_wait(acc_full, 0u, abort_flag);
+        // warp-uniform: tcgen05.ld below is .sync.aligned
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full, 0u, abort_flag));
         tc_fence_after();
         if (ok) {
             const int q = warp & 3;

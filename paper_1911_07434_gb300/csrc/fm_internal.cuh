@@ -140,6 +140,18 @@ __device__ inline void sample_indices_serial(uint64_t seed, uint64_t frame_id, i
     }
 }
 
+// e^{j pi m q} for q = q_hi + q_lo, q_hi a multiple of 2^-11 (|q| <= 2) and m < 2^11:
+// m*q_hi is exact in FP32 and is reduced mod 2 without error, m*q_lo is added
+// after the reduction, then one sincospif.
+__device__ __forceinline__ float2 steer_exact(int m, float qh, float ql) {
+    const float x = (float)m * qh;               // exact
+    const float r = x - 2.0f * rintf(0.5f * x);  // exact, in [-1, 1]
+    const float ph = fmaf((float)m, ql, r);
+    float s, c;
+    sincospif(ph, &s, &c);
+    return make_float2(c, s);
+}
+
 // Per-frame status bits.
 __device__ __forceinline__ void set_status(int* status, int code) {
     if (status) atomicOr(status, 1 << code);
@@ -151,12 +163,16 @@ cudaError_t launch_grid_table(const GridDesc* g, int n_grids, int max_L, const F
                               cudaStream_t s);
 cudaError_t launch_covariance_tc(const FrameDesc* d, const void* tmaps, int n_frames, int max_M, cudaStream_t s);
 size_t cov_tc_smem_bytes();
+cudaError_t launch_scan_tc(const FrameDesc* d, int n_frames, int M, int ncols, int L, float* bprep, const void* tmB,
+                           cudaStream_t s);
+int scan_tc_ncp(int ncols);
 cudaError_t launch_covariance(const FrameDesc* d, int n_frames, int max_M, cudaStream_t s);
 cudaError_t launch_sketch(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, bool any_gather,
                           bool any_dense, cudaStream_t s);
 cudaError_t launch_orth(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, cudaStream_t s);
 cudaError_t launch_final(const FrameDesc* d, int n_frames, int max_M, int max_l, cudaStream_t s);
 cudaError_t launch_scan(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s);
+cudaError_t launch_scan_fixup(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s);
 cudaError_t launch_peaks(const FrameDesc* d, int n_frames, int max_K, cudaStream_t s);
 cudaError_t launch_test_matrix(uint64_t seed, uint64_t frame_id, int M, int l, float2* out, cudaStream_t s);
 cudaError_t launch_sample_indices(uint64_t seed, uint64_t frame_id, int M, int l, int* out, cudaStream_t s);

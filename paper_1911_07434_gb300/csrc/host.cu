@@ -55,6 +55,8 @@ struct fm_ctx {
     uint64_t launches = 0;
     int cov_path = FM_COV_AUTO;
     int last_cov_path = 0;
+    int scan_path = FM_COV_AUTO;
+    int last_scan_path = 0;
     // serving state
     struct Slot;
     std::vector<Slot*> slots;
@@ -206,6 +208,9 @@ const char* check_frame(const fm_frame& f) {
 
 struct Plan {
     size_t desc_off, tmap_off, grid_off, total;
+    bool scan_uniform = false;  // all frames share M, ncols and one grid: batched tensor-core scan possible
+    int scan_M = 0, scan_nc = 0, scan_L = 0;
+    size_t bprep_off = 0, bprep_rows = 0, bprep_rowlen = 0;
     std::vector<size_t> R, C, V, Us, idx;  // per-frame offsets (R == SIZE_MAX: caller-owned)
     std::vector<int> grid_of;
     std::vector<GridDesc> grids;
@@ -220,8 +225,8 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
     size_t off = 0;
     pl.desc_off = off;
     off = aup(off + sizeof(FrameDesc) * (size_t)n);
-    pl.tmap_off = off;  // TMA tensor maps of the frames' X (tensor-core covariance)
-    if (need_R) off = aup(off + sizeof(CUtensorMap) * (size_t)n);
+    pl.tmap_off = off;  // TMA tensor maps: one per frame's X (covariance), then one for the scan's B
+    if (need_R) off = aup(off + sizeof(CUtensorMap) * ((size_t)n + 1));
     std::map<GridKey, int> gmap;
     pl.grid_of.assign(n, -1);
     if (need_grid) {
@@ -263,6 +268,23 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
         const size_t nc = (size_t)ncols_of(f[b].p);
         pl.Us.push_back(need_Us ? off : SIZE_MAX);
         if (need_Us) off = aup(off + sizeof(float2) * M * nc);
+    }
+    if (need_R && need_Us && need_grid) {
+        // batched tensor-core scan: one B operand row pair per (frame, column of U_s)
+        bool uni = pl.grids.size() == 1;
+        const int M0 = f[0].arr.M, nc0 = ncols_of(f[0].p);
+        for (int b = 1; uni && b < n; ++b) uni = f[b].arr.M == M0 && ncols_of(f[b].p) == nc0;
+        if (uni) {
+            pl.scan_uniform = true;
+            pl.scan_M = M0;
+            pl.scan_nc = nc0;
+            pl.scan_L = pl.grids[0].L;
+            const int ncp = fm::scan_tc_ncp(nc0), Mp = (M0 + 7) / 8 * 8;
+            pl.bprep_rows = (size_t)n * 2 * ncp;
+            pl.bprep_rowlen = 4 * (size_t)Mp;
+            pl.bprep_off = off;
+            off = aup(off + sizeof(float) * pl.bprep_rows * pl.bprep_rowlen);
+        }
     }
     pl.total = off;
     return pl;
@@ -353,6 +375,20 @@ bool encode_tmap(const FrameDesc& d, CUtensorMap* out) {
     return r == CUDA_SUCCESS;
 }
 
+// The scan's B operand (rows x rowlen FP32, rowlen = 4 Mp), boxes of 256 rows x 32 floats.
+bool encode_bprep_tmap(const float* base, size_t rows, size_t rowlen, CUtensorMap* out) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)rowlen, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(rowlen * sizeof(float))};
+    cuuint32_t box[2] = {32, 256};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // Decide the covariance path for these frames and, for the tensor-core path,
 // encode one tensor map per frame.  Fails only if the context forces the
 // tensor-core path and a frame cannot take it.
@@ -378,13 +414,14 @@ fm_status launch_cov(fm_ctx* c, bool tc, FrameDesc* dd, const char* tm_dev, int 
 
 // Uploads descriptors (+ grids) and returns device pointers.
 fm_status upload_descs(fm_ctx* c, const Plan& pl, std::vector<FrameDesc>& ds, const std::vector<CUtensorMap>& maps,
-                       cudaStream_t s, FrameDesc** dd, GridDesc** dg) {
+                       cudaStream_t s, FrameDesc** dd, GridDesc** dg, const CUtensorMap* extra_map = nullptr) {
     const size_t bytes = pl.grid_off + sizeof(GridDesc) * pl.grids.size();
     char* host = nullptr;
     fm_status st = staging(c, bytes, &host);
     if (st != FM_OK) return st;
     memcpy(host + pl.desc_off, ds.data(), sizeof(FrameDesc) * ds.size());
     if (!maps.empty()) memcpy(host + pl.tmap_off, maps.data(), sizeof(CUtensorMap) * maps.size());
+    if (extra_map) memcpy(host + pl.tmap_off + sizeof(CUtensorMap) * ds.size(), extra_map, sizeof(CUtensorMap));
     std::vector<GridDesc> g = pl.grids;
     for (size_t i = 0; i < g.size(); ++i) g[i].qtab = reinterpret_cast<float2*>(c->arena + pl.qtab[i]);
     if (!g.empty()) memcpy(host + pl.grid_off, g.data(), sizeof(GridDesc) * g.size());
@@ -497,9 +534,17 @@ fm_status fm_run(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream) {
     bool tc = false;
     st = choose_cov_path(c, ds, maps, &tc);
     if (st != FM_OK) return st;
+    // scan: batched tensor-core kernel when the frames share M, ncols and the grid
+    CUtensorMap bmap;
+    bool scan_tc = pl.scan_uniform && c->scan_path != FM_COV_SIMT &&
+                   encode_bprep_tmap(reinterpret_cast<float*>(c->arena + pl.bprep_off), pl.bprep_rows,
+                                     pl.bprep_rowlen, &bmap);
+    if (!scan_tc && c->scan_path == FM_COV_TC)
+        return fail(c, FM_ERR_INVALID_ARG, "tensor-core scan needs frames sharing M, ncols and the grid");
+    c->last_scan_path = scan_tc ? FM_COV_TC : FM_COV_SIMT;
     FrameDesc* dd;
     GridDesc* dg;
-    st = upload_descs(c, pl, ds, maps, s, &dd, &dg);
+    st = upload_descs(c, pl, ds, maps, s, &dd, &dg, scan_tc ? &bmap : nullptr);
     if (st != FM_OK) return st;
     const Maxes mx = maxes_of(ds);
     const int ng = (int)pl.grids.size();
@@ -509,7 +554,18 @@ fm_status fm_run(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream) {
     if (st != FM_OK) return st;
     st = run_subspace_chain(c, dd, n, mx, s);
     if (st != FM_OK) return st;
-    st = stage(c, kStScan, s, [&] { return fm::launch_scan(dd, n, mx.L, mx.M, mx.kpad, s); });
+    if (scan_tc) {
+        float* bp = reinterpret_cast<float*>(c->arena + pl.bprep_off);
+        const char* bmap_dev = c->arena + pl.tmap_off + sizeof(CUtensorMap) * (size_t)n;
+        st = stage(c, kStScan, s, [&] {
+            cudaError_t e = fm::launch_scan_tc(dd, n, pl.scan_M, pl.scan_nc, pl.scan_L, bp, bmap_dev, s);
+            if (e != cudaSuccess) return e;
+            // main-lobe angles again on the FP32 CUDA cores (see scan_kernel<..., FIXUP>)
+            return fm::launch_scan_fixup(dd, n, mx.L, mx.M, mx.kpad, s);
+        });
+    } else {
+        st = stage(c, kStScan, s, [&] { return fm::launch_scan(dd, n, mx.L, mx.M, mx.kpad, s); });
+    }
     if (st != FM_OK) return st;
     return stage(c, kStPeaks, s, [&] { return fm::launch_peaks(dd, n, mx.K, s); });
 }
@@ -752,6 +808,16 @@ fm_status fm_set_cov_path(fm_ctx* c, int path) {
 }
 
 int fm_last_cov_path(const fm_ctx* c) { return c ? c->last_cov_path : 0; }
+
+fm_status fm_set_scan_path(fm_ctx* c, int path) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (path != FM_COV_AUTO && path != FM_COV_SIMT && path != FM_COV_TC)
+        return fail(c, FM_ERR_INVALID_ARG, "unknown scan path %d", path);
+    c->scan_path = path;
+    return FM_OK;
+}
+
+int fm_last_scan_path(const fm_ctx* c) { return c ? c->last_scan_path : 0; }
 
 uint64_t fm_launch_count(const fm_ctx* c) { return c ? c->launches + c->serve_launches : 0; }
 

@@ -36,43 +36,20 @@ __global__ void grid_table_kernel(const GridDesc* __restrict__ grids, int n_grid
     g.qtab[i] = make_float2((float)qh, (float)(q - qh));
 }
 
-// e^{j pi (m*q)} with the exact reduction described above.
-__device__ __forceinline__ float2 steer(int m, float qh, float ql) {
-    const float x = (float)m * qh;               // exact
-    const float r = x - 2.0f * rintf(0.5f * x);  // exact, in [-1, 1]
-    const float ph = fmaf((float)m, ql, r);
-    float s, c;
-    sincospif(ph, &s, &c);
-    return make_float2(c, s);
-}
-
+// c_k += sum over m = 64 b + m0 (m0 = m0_begin, m0_begin + m0_stride, ... < min(64, M))
+// of conj(U_s[m][k]) a_m(theta), with U_s in shared memory.
 template <int KP, int NB>
-__global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restrict__ descs) {
-    extern __shared__ float4 smem_raw[];
-    float2* Usm = reinterpret_cast<float2*>(smem_raw);  // [M][KP]
-    const FrameDesc* dp = descs + blockIdx.y;
-    const int M = dp->M, L = dp->L, kp = dp->kpad;
-    const int i0 = blockIdx.x * kThreads;
-    if (i0 >= L) return;
-    const float2* __restrict__ Us = dp->Us;
-    for (int e = threadIdx.x; e < M * KP; e += kThreads) {
-        const int m = e / KP, k = e % KP;
-        Usm[e] = (k < kp) ? Us[(int64_t)m * kp + k] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    const int i = i0 + threadIdx.x;
-    if (i >= L) return;
-    const float2 qq = dp->qtab[i];
+__device__ __forceinline__ void accumulate_angle(const float2* __restrict__ Usm, int M, float2 qq, int m0_begin,
+                                                 int m0_stride, float2 (&acc)[KP]) {
     const int nb = (M + 63) / 64;
     float2 cb[NB];
 #pragma unroll
-    for (int b = 0; b < NB; ++b) cb[b] = (b < nb) ? steer(64 * b, qq.x, qq.y) : make_float2(0.f, 0.f);
-    float2 acc[KP];
+    for (int b = 0; b < NB; ++b) cb[b] = (b < nb) ? steer_exact(64 * b, qq.x, qq.y) : make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < KP; ++k) acc[k] = make_float2(0.f, 0.f);
     const int m0_end = min(64, M);
-    for (int m0 = 0; m0 < m0_end; ++m0) {
-        const float2 bm = steer(m0, qq.x, qq.y);
+    for (int m0 = m0_begin; m0 < m0_end; m0 += m0_stride) {
+        const float2 bm = steer_exact(m0, qq.x, qq.y);
         float2 part[KP];
 #pragma unroll
         for (int k = 0; k < KP; ++k) part[k] = make_float2(0.f, 0.f);
@@ -93,6 +70,10 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restr
 #pragma unroll
         for (int k = 0; k < KP; ++k) acc[k] = cadd(acc[k], part[k]);
     }
+}
+
+template <int KP>
+__device__ __forceinline__ void store_spectrum(const FrameDesc* dp, int i, int M, const float2 (&acc)[KP]) {
     float cn = 0.f;
 #pragma unroll
     for (int k = 0; k < KP; ++k) cn += cabs2(acc[k]);
@@ -102,25 +83,133 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restr
     if (dp->Pdb) dp->Pdb[i] = 10.0f * log10f(fminf(P, FLT_MAX));
 }
 
-template <int KP, int NB>
+// FIXUP = false: one angle per thread over the whole grid.
+// FIXUP = true: runs after the tensor-core scan and recomputes only the angles
+// where ||U_s^H a||^2 = M - 1/P exceeds 4 ncols (main lobes; about ncols for an
+// angle away from every source).  The tensor-core accumulator's error grows like
+// u M ||U_s^H a||^2 and is biased, while the sums here stay far below that, so
+// near a peak, where M - ||U_s^H a||^2 cancels, the CUDA-core value is kept.
+// The flagged angles of a 256-angle chunk are compacted; each is shared by
+// fix_groups(KP) warps, warp g taking the m0 residue class g (all lanes of a warp
+// read the same U_s row: a shared-memory broadcast), and the partial c_k are
+// summed in shared memory in a fixed order.  Chunks with no flagged angle exit
+// before loading U_s.
+__host__ __device__ constexpr int fix_groups(int kp) { return kp <= 8 ? 8 : (kp == 16 ? 4 : 2); }
+
+template <int KP, int NB, bool FIXUP>
+__global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restrict__ descs) {
+    extern __shared__ float4 smem_raw[];
+    float2* Usm = reinterpret_cast<float2*>(smem_raw);  // [M][KP]
+    const FrameDesc* dp = descs + blockIdx.y;
+    const int M = dp->M, L = dp->L, kp = dp->kpad;
+    const int i0 = blockIdx.x * kThreads;
+    if (i0 >= L) return;
+    const float2* __restrict__ Us = dp->Us;
+    constexpr int kWarps = kThreads / 32;
+    __shared__ int s_list[FIXUP ? kThreads : 1];
+    __shared__ int s_wcount[kWarps];
+    __shared__ float2 s_red[FIXUP ? kThreads * 8 : 1];  // [warp][k % 8][lane]
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int n_fix = 0;
+    if (FIXUP) {
+        const int ii = i0 + threadIdx.x;
+        bool f = false;
+        if (ii < L) f = !(1.0f / dp->P[ii] >= (float)(M - 4 * dp->ncols));  // NaN is recomputed too
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) s_wcount[w] = __popc(bal);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kWarps; ++j) n_fix += s_wcount[j];
+        if (n_fix == 0) return;
+        if (f) {
+            int base = 0;
+            for (int j = 0; j < w; ++j) base += s_wcount[j];
+            s_list[base + __popc(bal & ((1u << lane) - 1u))] = ii;
+        }
+        // s_list is ordered by the __syncthreads after the U_s load
+    }
+    for (int e = threadIdx.x; e < M * KP; e += kThreads) {
+        const int m = e / KP, k = e % KP;
+        Usm[e] = (k < kp) ? Us[(int64_t)m * kp + k] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2 acc[KP];
+    if (!FIXUP) {
+        const int i = i0 + threadIdx.x;
+        if (i >= L) return;
+        accumulate_angle<KP, NB>(Usm, M, dp->qtab[i], 0, 1, acc);
+        store_spectrum<KP>(dp, i, M, acc);
+        return;
+    }
+    constexpr int G = fix_groups(KP);            // warps per angle
+    constexpr int kPerRound = kWarps / G * 32;   // angles per round
+    const int g = w % G, grp = w / G;
+    // uniform trip count: every thread reaches every __syncthreads
+    for (int base = 0; base < n_fix; base += kPerRound) {
+        const int a = base + grp * 32 + lane;
+        const bool act = a < n_fix;
+        const int i = act ? s_list[a] : 0;
+        if (act) {
+            accumulate_angle<KP, NB>(Usm, M, dp->qtab[i], g, G, acc);
+        } else {
+#pragma unroll
+            for (int k = 0; k < KP; ++k) acc[k] = make_float2(0.f, 0.f);
+        }
+        float cn = 0.f;
+#pragma unroll
+        for (int kc = 0; kc < KP; kc += 8) {
+#pragma unroll
+            for (int k = 0; k < 8 && kc + k < KP; ++k) s_red[(w * 8 + k) * 32 + lane] = acc[kc + k];
+            __syncthreads();
+            if (g == 0 && act) {
+#pragma unroll
+                for (int k = 0; k < 8 && kc + k < KP; ++k) {
+                    float2 c = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int h = 0; h < G; ++h) c = cadd(c, s_red[((w + h) * 8 + k) * 32 + lane]);
+                    cn += cabs2(c);
+                }
+            }
+            __syncthreads();
+        }
+        if (g == 0 && act) {
+            const float den = (float)M - cn;
+            const float P = (den > 0.f) ? 1.0f / den : INFINITY;
+            dp->P[i] = P;
+            if (dp->Pdb) dp->Pdb[i] = 10.0f * log10f(fminf(P, FLT_MAX));
+        }
+    }
+}
+
+template <int KP, int NB, bool FIXUP>
 cudaError_t launch_kp(const FrameDesc* d, int n_frames, int max_L, int max_M, cudaStream_t s) {
     const size_t smem = sizeof(float2) * (size_t)max_M * KP;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(scan_kernel<KP, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    const size_t static_smem = FIXUP ? sizeof(int) * (kThreads + kThreads / 32) + sizeof(float2) * kThreads * 8
+                                     : sizeof(int) * (1 + kThreads / 32) + sizeof(float2);
+    if (smem + static_smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(scan_kernel<KP, NB, FIXUP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((max_L + kThreads - 1) / kThreads, n_frames);
-    scan_kernel<KP, NB><<<grid, kThreads, smem, s>>>(d);
+    scan_kernel<KP, NB, FIXUP><<<grid, kThreads, smem, s>>>(d);
     return cudaGetLastError();
 }
 
-template <int NB>
+template <int NB, bool FIXUP>
 cudaError_t launch_nb(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s) {
-    if (max_kpad <= 4) return launch_kp<4, NB>(d, n_frames, max_L, max_M, s);
-    if (max_kpad <= 8) return launch_kp<8, NB>(d, n_frames, max_L, max_M, s);
-    if (max_kpad <= 16) return launch_kp<16, NB>(d, n_frames, max_L, max_M, s);
-    return launch_kp<32, NB>(d, n_frames, max_L, max_M, s);
+    if (max_kpad <= 4) return launch_kp<4, NB, FIXUP>(d, n_frames, max_L, max_M, s);
+    if (max_kpad <= 8) return launch_kp<8, NB, FIXUP>(d, n_frames, max_L, max_M, s);
+    if (max_kpad <= 16) return launch_kp<16, NB, FIXUP>(d, n_frames, max_L, max_M, s);
+    return launch_kp<32, NB, FIXUP>(d, n_frames, max_L, max_M, s);
+}
+
+template <bool FIXUP>
+cudaError_t launch_scan_t(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s) {
+    if (max_M <= 128) return launch_nb<2, FIXUP>(d, n_frames, max_L, max_M, max_kpad, s);
+    if (max_M <= 256) return launch_nb<4, FIXUP>(d, n_frames, max_L, max_M, max_kpad, s);
+    if (max_M <= 512) return launch_nb<8, FIXUP>(d, n_frames, max_L, max_M, max_kpad, s);
+    return launch_nb<16, FIXUP>(d, n_frames, max_L, max_M, max_kpad, s);
 }
 
 }  // namespace
@@ -134,10 +223,11 @@ cudaError_t launch_grid_table(const GridDesc* g, int n_grids, int max_L, const F
 }
 
 cudaError_t launch_scan(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s) {
-    if (max_M <= 128) return launch_nb<2>(d, n_frames, max_L, max_M, max_kpad, s);
-    if (max_M <= 256) return launch_nb<4>(d, n_frames, max_L, max_M, max_kpad, s);
-    if (max_M <= 512) return launch_nb<8>(d, n_frames, max_L, max_M, max_kpad, s);
-    return launch_nb<16>(d, n_frames, max_L, max_M, max_kpad, s);
+    return launch_scan_t<false>(d, n_frames, max_L, max_M, max_kpad, s);
+}
+
+cudaError_t launch_scan_fixup(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s) {
+    return launch_scan_t<true>(d, n_frames, max_L, max_M, max_kpad, s);
 }
 
 }  // namespace fm

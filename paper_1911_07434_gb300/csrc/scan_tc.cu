@@ -1,0 +1,305 @@
+// scan_tc.cu -- MUSIC pseudo-spectrum (Eq. 5 / Eq. 10) for a batch of frames on
+// the 5th-generation tensor cores.
+//
+// Frames that share M and the angle grid share their steering vectors, so the
+// scan of a batch is one real GEMM per 128-angle tile:
+//   D[i][n] = sum_k A[i][k] B[n][k],  A = steering rows [ar_0, ai_0, ar_1, ai_1, ...]
+//   (a_m = ar + j ai = e^{j pi m q_i}), B = two rows per (frame f, column k of U_s):
+//   [ur_m, ui_m]_m -> Re(u^H a),  [-ui_m, ur_m]_m -> Im(u^H a),
+// and P_f(i) = 1 / (M - sum_k (Re^2 + Im^2)).  A is generated in registers by
+// the CTA itself (the exact phase reduction of scan.cu, one sincospi per
+// element) and written to shared memory as TF32 hi/lo pairs; B (U_s of up to
+// 512 / (2 ncp) frames, already split into hi/lo by scan_bprep_kernel) arrives by
+// TMA.  Each FP32 product is formed as hi*hi + hi*lo + lo*hi (3xTF32).  Two
+// 128 x 256 FP32 accumulators fill the 512 TMEM columns.
+//
+// Warp roles (192 threads): warp 0 TMA producer, warp 1 TMEM allocation + MMA
+// issue, warps 2-5 steering generation (one angle row each) and the epilogue.
+#include "tc_common.cuh"
+
+namespace fm {
+namespace {
+
+using namespace tc;
+
+constexpr int kRowsA = 128;                // angles per tile
+constexpr int kRowsB = 512;                // rows of B per CTA (two accumulators of N = 256)
+constexpr int kStageA = kRowsA * 128;      // 16 KB: [hi 16 | lo 16] floats per angle row
+constexpr int kStageB = kRowsB * 128;      // 64 KB
+constexpr int kStage = kStageA + kStageB;
+constexpr int kNStages = 2;
+constexpr int kThreads = 192;
+constexpr int kTiles = kNStages * kStage;  // 160 KB
+constexpr int kSmemBytes = kTiles + 1024 + 256;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kIdesc = idesc_tf32(128, 256);
+
+__device__ __forceinline__ void split2(float a, float b, uint32_t* hi, uint32_t* lo) {
+    hi[0] = tf32_rn(a);
+    hi[1] = tf32_rn(b);
+    lo[0] = tf32_rn(a - __uint_as_float(hi[0]));
+    lo[1] = tf32_rn(b - __uint_as_float(hi[1]));
+}
+
+// B rows for the frames of one launch: row f*2ncp + 2k (Re) and + 1 (Im); along a
+// row, stage s (8 antennas) holds 32 floats [hi of 16 interleaved values | lo].
+__global__ void scan_bprep_kernel(const FrameDesc* __restrict__ descs, int n_frames, int M, int Mp, int ncp,
+                                  float* __restrict__ Bp) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (f, k, m)
+    const int64_t total = (int64_t)n_frames * ncp * Mp;
+    if (e >= total) return;
+    const int m = (int)(e % Mp);
+    const int k = (int)((e / Mp) % ncp);
+    const int f = (int)(e / ((int64_t)Mp * ncp));
+    const FrameDesc* dp = descs + f;
+    float2 u = make_float2(0.f, 0.f);
+    if (m < M && k < dp->ncols) u = dp->Us[(int64_t)m * dp->kpad + k];
+    const int64_t rowlen = 4 * (int64_t)Mp;
+    float* re_row = Bp + ((int64_t)f * 2 * ncp + 2 * k) * rowlen;
+    float* im_row = re_row + rowlen;
+    const int s = m >> 3, p = (2 * m) & 15;
+    uint32_t hi[2], lo[2];
+    split2(u.x, u.y, hi, lo);  // Re row: [ur, ui]
+    re_row[s * 32 + p] = __uint_as_float(hi[0]);
+    re_row[s * 32 + p + 1] = __uint_as_float(hi[1]);
+    re_row[s * 32 + 16 + p] = __uint_as_float(lo[0]);
+    re_row[s * 32 + 16 + p + 1] = __uint_as_float(lo[1]);
+    split2(-u.y, u.x, hi, lo);  // Im row: [-ui, ur]
+    im_row[s * 32 + p] = __uint_as_float(hi[0]);
+    im_row[s * 32 + p + 1] = __uint_as_float(hi[1]);
+    im_row[s * 32 + 16 + p] = __uint_as_float(lo[0]);
+    im_row[s * 32 + 16 + p + 1] = __uint_as_float(lo[1]);
+}
+
+template <int NCP>
+__global__ void __launch_bounds__(kThreads, 1)
+    scan_tc_kernel(const FrameDesc* __restrict__ descs, int n_frames, const CUtensorMap* __restrict__ tmB, int M,
+                   int Mp, int L) {
+    constexpr int kRowsPerFrame = 2 * NCP;
+    constexpr int kFramesPerCta = kRowsB / kRowsPerFrame;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + kTiles);
+    uint64_t* a_full = bars;      // [2] generators -> MMA
+    uint64_t* b_full = bars + 2;  // [2] TMA -> MMA
+    uint64_t* empty = bars + 4;   // [2] MMA -> TMA and generators
+    uint64_t* acc_full = bars + 6;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 7);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 8);
+
+    const int f0 = blockIdx.y * kFramesPerCta;
+    const int nf = min(kFramesPerCta, n_frames - f0);
+    if (nf <= 0) return;
+    const int nrows = nf * kRowsPerFrame;
+    const bool two = nrows > 256;
+    const int i0 = blockIdx.x * kRowsA;
+    const int nstages = Mp / 8;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kNStages; ++s) {
+            mbar_init(&a_full[s], 128);
+            mbar_init(&b_full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(acc_full, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmB)) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint32_t bytes = (two ? 2u : 1u) * 256u * 128u;
+            const int y0 = f0 * kRowsPerFrame;
+            for (int s = 0; s < nstages; ++s) {
+                const int slot = s % kNStages;
+                if (!mbar_wait(&empty[slot], ((uint32_t)(s / kNStages) & 1u) ^ 1u, abort_flag)) break;
+                unsigned char* bdst = base + slot * kStage + kStageA;
+                mbar_expect_tx(&b_full[slot], bytes);
+                tma_load_2d(bdst, tmB, s * 32, y0, &b_full[slot]);
+                if (two) tma_load_2d(bdst + 256 * 128, tmB, s * 32, y0 + 256, &b_full[slot]);
+            }
+            for (int s = max(0, nstages - kNStages); s < nstages; ++s)
+                mbar_wait(&b_full[s % kNStages], (uint32_t)(s / kNStages) & 1u, abort_flag);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            for (int s = 0; s < nstages; ++s) {
+                const int slot = s % kNStages;
+                const uint32_t ph = (uint32_t)(s / kNStages) & 1u;
+                if (!mbar_wait(&a_full[slot], ph, abort_flag)) break;
+                if (!mbar_wait(&b_full[slot], ph, abort_flag)) break;
+                tc_fence_after();
+                const uint32_t a = sa(base + slot * kStage), b = a + kStageA;
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                    const uint32_t acc0 = (s > 0 || kk > 0) ? 1u : 0u;
+                    const uint64_t a_hi = desc_sw128(a + 32 * kk), a_lo = desc_sw128(a + 64 + 32 * kk);
+                    const uint64_t b0_hi = desc_sw128(b + 32 * kk), b0_lo = desc_sw128(b + 64 + 32 * kk);
+                    mma_tf32(tmem, a_hi, b0_hi, kIdesc, acc0);
+                    mma_tf32(tmem, a_hi, b0_lo, kIdesc, 1u);
+                    mma_tf32(tmem, a_lo, b0_hi, kIdesc, 1u);
+                    if (two) {
+                        const uint32_t b1 = b + 256 * 128;
+                        const uint64_t b1_hi = desc_sw128(b1 + 32 * kk), b1_lo = desc_sw128(b1 + 64 + 32 * kk);
+                        mma_tf32(tmem + 256, a_hi, b1_hi, kIdesc, acc0);
+                        mma_tf32(tmem + 256, a_hi, b1_lo, kIdesc, 1u);
+                        mma_tf32(tmem + 256, a_lo, b1_hi, kIdesc, 1u);
+                    }
+                }
+                mma_commit(&empty[slot]);
+            }
+            mma_commit(acc_full);
+            mbar_wait(acc_full, 0u, abort_flag);
+        }
+    } else {
+        // ------------------------------------------ steering generation --------
+        const int r = threadIdx.x - 64;
+        const int i = i0 + r;
+        const float2 qq = (i < L) ? descs[0].qtab[i] : make_float2(0.f, 0.f);
+        for (int s = 0; s < nstages; ++s) {
+            const int slot = s % kNStages;
+            if (!mbar_wait(&empty[slot], ((uint32_t)(s / kNStages) & 1u) ^ 1u, abort_flag)) break;
+            char* arow = reinterpret_cast<char*>(base + slot * kStage);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {  // chunk c: antennas 8s + 2c, 8s + 2c + 1
+                uint4 hi, lo;
+                uint32_t h[2], w[2];
+                const int m0 = 8 * s + 2 * c;
+                float2 a0 = (i < L && m0 < M) ? steer_exact(m0, qq.x, qq.y) : make_float2(0.f, 0.f);
+                float2 a1 = (i < L && m0 + 1 < M) ? steer_exact(m0 + 1, qq.x, qq.y) : make_float2(0.f, 0.f);
+                split2(a0.x, a0.y, h, w);
+                hi.x = h[0];
+                hi.y = h[1];
+                lo.x = w[0];
+                lo.y = w[1];
+                split2(a1.x, a1.y, h, w);
+                hi.z = h[0];
+                hi.w = h[1];
+                lo.z = w[0];
+                lo.w = w[1];
+                *reinterpret_cast<uint4*>(arow + swz(r, c)) = hi;
+                *reinterpret_cast<uint4*>(arow + swz(r, 4 + c)) = lo;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&a_full[slot]);
+        }
+        // ---------------------------------------------------------- epilogue --
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full, 0u, abort_flag));
+        tc_fence_after();
+        if (ok) {
+            const int q = warp & 3;
+            const int row = 32 * q + lane;
+            const int ia = i0 + row;
+            const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+            const float Mf = (float)M;
+            if constexpr (kRowsPerFrame <= 16) {
+                const int nchunks = (nrows + 15) / 16;
+                for (int ch = 0; ch < nchunks; ++ch) {
+                    uint32_t v[16];
+                    tmem_ld16(tl + 16 * ch, v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; j += kRowsPerFrame) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int jj = 0; jj < kRowsPerFrame; ++jj) {
+                            const float x = __uint_as_float(v[j + jj]);
+                            acc = fmaf(x, x, acc);
+                        }
+                        const int f = (16 * ch + j) / kRowsPerFrame;
+                        if (f < nf && ia < L) {
+                            const FrameDesc* dp = descs + f0 + f;
+                            const float den = Mf - acc;
+                            const float P = (den > 0.f) ? 1.0f / den : INFINITY;
+                            dp->P[ia] = P;
+                            if (dp->Pdb) dp->Pdb[ia] = 10.0f * log10f(fminf(P, 3.402823466e38f));
+                        }
+                    }
+                }
+            } else {
+                for (int f = 0; f < nf; ++f) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int h = 0; h < kRowsPerFrame / 16; ++h) {
+                        uint32_t v[16];
+                        tmem_ld16(tl + f * kRowsPerFrame + 16 * h, v);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int jj = 0; jj < 16; ++jj) {
+                            const float x = __uint_as_float(v[jj]);
+                            acc = fmaf(x, x, acc);
+                        }
+                    }
+                    if (ia < L) {
+                        const FrameDesc* dp = descs + f0 + f;
+                        const float den = Mf - acc;
+                        const float P = (den > 0.f) ? 1.0f / den : INFINITY;
+                        dp->P[ia] = P;
+                        if (dp->Pdb) dp->Pdb[ia] = 10.0f * log10f(fminf(P, 3.402823466e38f));
+                    }
+                }
+            }
+        }
+        tc_fence_before();
+    }
+    __syncthreads();
+    if (*abort_flag && threadIdx.x == 0) {
+        for (int f = 0; f < nf; ++f) set_status(descs[f0 + f].status, FM_ERR_TIMEOUT);
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+template <int NCP>
+cudaError_t launch_ncp(const FrameDesc* d, int n_frames, const void* tmB, int M, int Mp, int L, cudaStream_t s) {
+    cudaError_t e =
+        cudaFuncSetAttribute(scan_tc_kernel<NCP>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    const int fpc = kRowsB / (2 * NCP);
+    dim3 grid((L + kRowsA - 1) / kRowsA, (n_frames + fpc - 1) / fpc);
+    scan_tc_kernel<NCP><<<grid, kThreads, kSmemBytes, s>>>(d, n_frames, reinterpret_cast<const CUtensorMap*>(tmB),
+                                                           M, Mp, L);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int scan_tc_ncp(int ncols) {
+    int p = 1;
+    while (p < ncols) p *= 2;
+    return p;
+}
+
+cudaError_t launch_scan_tc(const FrameDesc* d, int n_frames, int M, int ncols, int L, float* bprep, const void* tmB,
+                           cudaStream_t s) {
+    const int ncp = scan_tc_ncp(ncols);
+    const int Mp = (M + 7) / 8 * 8;
+    const int64_t total = (int64_t)n_frames * ncp * Mp;
+    scan_bprep_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(d, n_frames, M, Mp, ncp, bprep);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    switch (ncp) {
+        case 1: return launch_ncp<1>(d, n_frames, tmB, M, Mp, L, s);
+        case 2: return launch_ncp<2>(d, n_frames, tmB, M, Mp, L, s);
+        case 4: return launch_ncp<4>(d, n_frames, tmB, M, Mp, L, s);
+        case 8: return launch_ncp<8>(d, n_frames, tmB, M, Mp, L, s);
+        default: return launch_ncp<16>(d, n_frames, tmB, M, Mp, L, s);
+    }
+}
+
+}  // namespace fm

@@ -20,7 +20,9 @@
 //     (FP32 products split exactly with an FMA, sums kept as hi + lo pairs),
 //     factors and inverts it in double-float, and applies the inverse with
 //     double-float accumulation, so the pass survives cond(C) up to ~1/u_fp32
-//     without amplifying rounding into the range of Q; pass 2 (cond ~ 1) is FP32.
+//     without amplifying rounding into the range of Q.  Pass 2 (cond ~ 1) is
+//     double-float for the final Q (its orthonormality feeds U_s directly) and
+//     FP32 for the power-step basis V.
 //   - W: H is Hermitian positive definite in exact arithmetic, so
 //     B = R_c H^{-1} R_c^H = F F^H with F = R_c R_h^{-1}, H = R_h^H R_h (FP32
 //     Cholesky).  If the Cholesky breaks down, W is the eigenvalue pseudo-inverse
@@ -28,7 +30,8 @@
 //   - eig(B): two-sided complex Jacobi in FP32, round-robin parallel ordering,
 //     relative stopping test |b_pq| <= tol sqrt(|b_pp b_qq|), followed by one
 //     Rayleigh-Ritz correction of the leading eigenspace with double-float sums
-//     (see refine_subspace).
+//     (see refine_subspace) and a double-float re-orthonormalisation of the
+//     selected eigenvectors.
 #include <cooperative_groups.h>
 #include <float.h>
 
@@ -489,19 +492,35 @@ __device__ void upper_mul(const float2* R, float2* Rc, float2* tmp, int l) {
     __syncthreads();
 }
 
-// CholeskyQR2 of the cluster-distributed rows A (rows x l, in place -> Q).
-// Rc receives the R factor (the same on every CTA).  Returns false on a breakdown.
-__device__ bool cholqr2(cg::cluster_group& cl, float2* A, int rows, int l, const Sm& sm) {
+// One double-float CholeskyQR pass on the cluster-distributed rows A (in place):
+// G = A^H A (double-float sums), G = R^H R (double-float Cholesky),
+// A <- A R^{-1} (double-float accumulation).  Rk receives R rounded to FP32.
+__device__ bool cholqr_pass_d(cg::cluster_group& cl, float2* A, int rows, int l, const Sm& sm, float2* Rk) {
     gram_part_d(A, rows, l, sm.part);
     reduce_d(cl, sm.part, sm.Gd, l);
-    bool ok = chol_d(sm.Gd, l, sm);
+    const bool ok = chol_d(sm.Gd, l, sm);
     trinv_d(sm.Gd, sm.Xd, l, sm);
     for (int e = threadIdx.x; e < l * l; e += kThreads) {
         const float4 g = sm.Gd[e];
-        sm.Rc[e] = make_float2(g.x + g.y, g.z + g.w);
+        Rk[e] = make_float2(g.x + g.y, g.z + g.w);
     }
     apply_upper_d(A, rows, l, sm.Xd);
-    // pass 2 (FP32); Gf / Xf reuse the double-float slots
+    return ok;
+}
+
+// CholeskyQR2 of the cluster-distributed rows A (rows x l, in place -> Q); Rc
+// receives the R factor (the same on every CTA).  Pass 1 is double-float (it
+// must survive cond(A) up to ~1/u_fp32); pass 2 starts from cond ~ 1 and is
+// double-float as well when exact_pass2 (then ||Q^H Q - I|| is set by the final
+// FP32 rounding of Q alone, not by an FP32 Gram summed over M rows), FP32
+// otherwise.  Returns false on a Cholesky breakdown.
+__device__ bool cholqr2(cg::cluster_group& cl, float2* A, int rows, int l, const Sm& sm, bool exact_pass2) {
+    bool ok = cholqr_pass_d(cl, A, rows, l, sm, sm.Rc);
+    if (exact_pass2) {
+        ok = cholqr_pass_d(cl, A, rows, l, sm, sm.Z) && ok;  // Z: R2 (scratch until the eigensolve)
+        upper_mul(sm.Z, sm.Rc, sm.T, l);
+        return ok;
+    }
     gram_part_f(A, A, rows, l, true, reinterpret_cast<float2*>(sm.part));
     reduce_f(cl, reinterpret_cast<float2*>(sm.part), sm.Gf, l, true);
     ok = chol_f(sm.Gf, l, sm) && ok;
@@ -709,6 +728,27 @@ __device__ void refine_subspace(const Sm& sm, int l, int nc) {
     __syncthreads();
 }
 
+// Re-orthonormalise the k columns of Z (n x k, row stride k, every CTA holds the
+// same copy) by one double-float CholeskyQR pass: the accumulated FP32 Jacobi
+// rotations leave them orthonormal only to ~sqrt(rounds) u, and U_s = Q Z
+// inherits that; the pass keeps their span.
+__device__ void orthonormalize_cols_d(float2* Z, int n, int k, const Sm& sm) {
+    gram_part_d(Z, n, k, sm.part);
+    __syncthreads();
+    for (int e = threadIdx.x; e < k * (k + 1) / 2; e += kThreads) {
+        int i, j;
+        tri_coords(e, k, i, j);
+        zd g = zload(sm.part[e]);
+        if (i == j) g.im = df{0.f, 0.f};
+        sm.Gd[i * k + j] = zpack(g);
+        if (i != j) sm.Gd[j * k + i] = zpack(zd{g.re, dd_neg(g.im)});
+    }
+    __syncthreads();
+    chol_d(sm.Gd, k, sm);
+    trinv_d(sm.Gd, sm.Xd, k, sm);
+    apply_upper_d(Z, n, k, sm.Xd);
+}
+
 // ---------------------------------------------------------------- kernel ----
 __global__ void __launch_bounds__(kThreads) small_cluster_kernel(const FrameDesc* __restrict__ descs, int mode,
                                                                  int pass) {
@@ -728,7 +768,7 @@ __global__ void __launch_bounds__(kThreads) small_cluster_kernel(const FrameDesc
     load_rows(dp->C, sm.Cs, r0, rows, l);
     if (mode == kOrth) {
         __syncthreads();
-        const bool ok = cholqr2(cl, sm.Cs, rows, l, sm);
+        const bool ok = cholqr2(cl, sm.Cs, rows, l, sm, false);
         store_rows(sm.Cs, dp->V, r0, rows, l);
         if (!ok && rank == 0 && threadIdx.x == 0) set_status(dp->status, FM_ERR_NO_CONVERGENCE);
         return;
@@ -763,7 +803,7 @@ __global__ void __launch_bounds__(kThreads) small_cluster_kernel(const FrameDesc
     __syncthreads();
 
     // C = Q R_c (Q in place of the C rows); V rows are dead from here on
-    bool ok = cholqr2(cl, sm.Cs, rows, l, sm);
+    bool ok = cholqr2(cl, sm.Cs, rows, l, sm, true);
 
     // B = R_c H^+ R_c^H
     for (int e = threadIdx.x; e < l * l; e += kThreads) sm.Gf[e] = sm.H[e];
@@ -826,6 +866,7 @@ __global__ void __launch_bounds__(kThreads) small_cluster_kernel(const FrameDesc
     const int s2 = jacobi(sm.H, sm.Z, sm.w, sm.perm, l, sm);
     const int nc_out = dp->ncols;
     refine_subspace(sm, l, nc_out);
+    orthonormalize_cols_d(sm.Rc, l, nc_out, sm);
     // U_s rows = Q rows * U_B[:, :ncols] (refined, in Rc: l x ncols)
     apply_f(sm.Cs, dp->Us + (int64_t)r0 * dp->kpad, rows, l, sm.Rc, nc_out, nc_out, dp->kpad, false);
     if (rank == 0 && threadIdx.x == 0 && (s2 < 0 || !ok)) set_status(dp->status, FM_ERR_NO_CONVERGENCE);

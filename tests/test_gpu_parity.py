@@ -252,3 +252,37 @@ def test_run_full_size_sampled(ctx):
         assert int(o[4][0]) == fr.K and int(o[5][0]) == 0
         est = np.sort(o[3].cpu().numpy())
         assert np.max(np.abs(est - fr.angles_deg)) < 0.05, (est, fr.angles_deg)
+
+
+@pytest.mark.parametrize("M,K,l,nf,rr", [(64, 3, 13, 3, 0), (100, 1, 4, 2, 0), (128, 8, 16, 40, 0), (200, 16, 20, 20, 0),
+                                         (64, 3, 13, 5, 13), (512, 8, 24, 6, 0)])
+def test_scan_tensor_core_matches_cuda_core(ctx, M, K, l, nf, rr):
+    """Tensor-core scan path of fm_run (tcgen05 3xTF32 scan, main lobes recomputed on CUDA cores) vs the
+    FP32 CUDA-core scan on the same frames.  Away from the main lobes ||U_s^H a||^2 <= 4 ncols and the
+    tensor-core denominator is within about u M ||U_s^H a||^2 <= 4 u M ncols of the exact one; inside them
+    both paths run the same CUDA-core code.  Bound: 16 u M ncols."""
+    from paper_1911_07434_gb300 import binding
+    wl = synth.massive_mimo_frames(nf, seed=M + K, M=M, T=2 * M, K=K, extra=l - K, grid=(-70.0, 70.0, 0.07))
+    outs = {}
+    for path in (binding.FM_COV_SIMT, binding.FM_COV_TC):
+        ctx.set_scan_path(path)
+        try:
+            fs, keep = [], []
+            for fr in wl.frames:
+                X = dev(fr.X)
+                P = torch.empty(fr.L, dtype=torch.float32, device="cuda")
+                idx = torch.empty(fr.K, dtype=torch.int32, device="cuda")
+                deg = torch.empty(fr.K, dtype=torch.float32, device="cuda")
+                n = torch.empty(1, dtype=torch.int32, device="cuda")
+                fs.append(ctx.frame(X, fr.K, fr.l, fr.t, 2, fr.theta0, fr.step, fr.L, P, idx, deg, n, seed=1,
+                                    frame_id=fr.frame_id, rank_restrict=rr))
+                keep.append((X, P, idx, deg, n))
+            ctx.run(fs)
+            torch.cuda.synchronize()
+            assert ctx.last_scan_path() == path
+            outs[path] = [k[1].cpu().numpy().astype(np.float64) for k in keep]
+        finally:
+            ctx.set_scan_path(binding.FM_COV_AUTO)
+    nc = rr if rr else K
+    for a, b in zip(outs[binding.FM_COV_SIMT], outs[binding.FM_COV_TC]):
+        assert np.max(np.abs(1.0 / a - 1.0 / b)) <= 16 * U32 * M * nc, np.max(np.abs(1.0 / a - 1.0 / b))
