@@ -212,6 +212,28 @@ int fm_last_cov_path(const fm_ctx* ctx);
 fm_status fm_set_scan_path(fm_ctx* ctx, int path);
 int fm_last_scan_path(const fm_ctx* ctx);
 
+/* ---- allocation-free spectrum --------------------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * let the library allocate device memory: a radar front end that fixes its
+ * memory map at start-up and must not allocate while frames stream in, or a host
+ * framework that owns every device allocation itself.  fm_spectrum_noalloc
+ * computes exactly what fm_spectrum computes (same kernels, same results) but
+ * takes no context and allocates nothing: its scratch (frame descriptors and
+ * the steering-phase table of the grid) lives in a fixed array inside the
+ * library, about 524 KB, which every GPU that loads the library holds until the
+ * process exits.  Limits: n_frames <= 64 and grid->L <= 65536 (larger requests
+ * return FM_ERR_INVALID_ARG before any work), plus fm_spectrum's own limits.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array and overwrites it: calls that
+ * overlap on the GPU (different streams, or different host threads on one
+ * device) race, so serialise them on one stream.  The descriptors are copied
+ * from host stack memory with a pageable cudaMemcpyAsync, which has taken its
+ * own copy of them when it returns.  Returns FM_OK, FM_ERR_INVALID_ARG or
+ * FM_ERR_CUDA (there is no context, hence no fm_last_error text). */
+fm_status fm_spectrum_noalloc(const void* U, int n_frames, int M, int ncols, double d_wl, const fm_grid* grid,
+                              float* P, fm_stream stream);
+
 /* ---- serving (continuous batching) ------------------------------------------
  * fm_serve_submit: enqueue one frame; the library admits queued frames into
  * device work as workspace within the budget frees up, overlapping them on its

@@ -78,6 +78,7 @@ _SIGS = {
     "fm_last_cov_path": (c_int, [c_void_p]),
     "fm_set_scan_path": (c_int, [c_void_p, c_int]),
     "fm_last_scan_path": (c_int, [c_void_p]),
+    "fm_spectrum_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_double, POINTER(FmGrid), c_void_p, c_void_p]),
     "fm_serve_submit": (c_int, [c_void_p, POINTER(FmFrame), POINTER(c_uint64)]),
     "fm_serve_poll": (c_int, [c_void_p, c_uint64, POINTER(c_int)]),
 }
@@ -189,6 +190,11 @@ def fm_set_scan_path(ctx, path) -> int:
 
 def fm_last_scan_path(ctx) -> int:
     return load().fm_last_scan_path(ctx)
+
+
+def fm_spectrum_noalloc(U, n_frames, M, ncols, d_wl, grid: FmGrid, P, stream) -> int:
+    """Same result as fm_spectrum without any device allocation (see fastmusic.h)."""
+    return load().fm_spectrum_noalloc(U, n_frames, M, ncols, d_wl, byref(grid), P, stream)
 
 
 def fm_serve_submit(ctx, frame: FmFrame):
