@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--no-baseline", action="store_true", help="skip full-eig MUSIC and the CPU oracle")
     ap.add_argument("--cpu-sample", type=int, default=3, help="frames of the workload the oracle times")
+    ap.add_argument("--serve-requests", type=int, default=4000, help="requests of the timed serving run (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=20000.0, help="Poisson arrival rate of the serving run")
     return ap.parse_args()
 
 
@@ -200,6 +202,98 @@ def roofline(stages, ctx, pk, pk_kind, B, M, T, K, L):
             "peak_source": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x sm_max_mhz ({pk_kind})"}
 
 
+def shard_frame_ids(rank: int, batch: int) -> list:
+    """Frames are independent problems: rank r owns frame ids [r * batch, (r + 1) * batch)."""
+    return [rank * batch + b for b in range(batch)]
+
+
+def max_over_ranks(x: float, device) -> float:
+    """Largest value of x over the ranks of the default process group (x itself without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, batch: int, steps: int, seconds: float) -> float:
+    """Whole-job frames/s: every rank ran `steps` batches of `batch` frames; `seconds` is the
+    slowest rank's time."""
+    return world * batch * steps / seconds
+
+
+def serving_run(binding, synth, dev, n_req, rate, budget_gb=40, pool_per_profile=8, seed=0):
+    """Streaming request loop of the serving mix: Poisson arrivals at `rate` drawn equally from
+    the three range profiles (long M=256 / medium M=384 / short M=512), served by
+    fm_serve_submit / fm_serve_poll under a `budget_gb` workspace budget.  Latency of a request =
+    time its completion is observed - its scheduled arrival time (host clock)."""
+    import numpy as np
+    import torch
+    profiles = list(synth.SERVING_PROFILES)
+    pool = []
+    for pi, name in enumerate(profiles):
+        for j in range(pool_per_profile):
+            fr = synth.serving_frame(name, frame_id=pi * 1000 + j, seed=seed)
+            pool.append((fr, torch.from_numpy(np.ascontiguousarray(fr.X)).to(dev)))
+    Lmax = max(fr.L for fr, _ in pool)
+    Kmax = max(fr.K for fr, _ in pool)
+    rng = np.random.default_rng(seed + 77)
+    n_warm = min(400, n_req)
+    n_all = n_warm + n_req
+    pick = [(i % 3) * pool_per_profile + int(rng.integers(pool_per_profile)) for i in range(n_all)]
+    P = torch.empty((n_all, Lmax), dtype=torch.float32, device=dev)
+    idx = torch.empty((n_all, Kmax), dtype=torch.int32, device=dev)
+    deg = torch.empty((n_all, Kmax), dtype=torch.float32, device=dev)
+    npk = torch.empty(n_all, dtype=torch.int32, device=dev)
+    st = torch.zeros(n_all, dtype=torch.int32, device=dev)
+    fs = []
+    for i in range(n_all):
+        fr, X = pool[pick[i]]
+        fs.append(binding.Context.frame(X, fr.K, fr.l, fr.t, binding.FM_RAND_PROJECTION, fr.theta0, fr.step, fr.L,
+                                        P[i], idx[i], deg[i], npk[i:i + 1], seed=1, frame_id=i,
+                                        status=st[i:i + 1]))
+    ctx = binding.Context(budget_bytes=budget_gb << 30, device=dev.index or 0)
+
+    def stream(lo, hi, arrive):
+        lat = []
+        pend = []                        # (ticket, arrival) in arrival order
+        i = lo
+        t0 = time.perf_counter()
+        while i < hi or pend:
+            now = time.perf_counter() - t0
+            while i < hi and arrive[i - lo] <= now:
+                pend.append((ctx.serve_submit(fs[i]), arrive[i - lo]))
+                i += 1
+            keep = []
+            for k, (tk, ta) in enumerate(pend):
+                if k < 32 and ctx.serve_poll(tk):
+                    lat.append(time.perf_counter() - t0 - ta)
+                else:
+                    keep.append((tk, ta))
+            pend = keep
+        return lat, time.perf_counter() - t0
+
+    gaps = rng.exponential(1.0 / rate, size=n_all)
+    stream(0, n_warm, np.cumsum(gaps[:n_warm]))
+    torch.cuda.synchronize()
+    l0 = binding.fm_launch_count(ctx.h)
+    arrive = np.cumsum(gaps[n_warm:])
+    lat, wall = stream(n_warm, n_all, arrive)
+    torch.cuda.synchronize()
+    launches = binding.fm_launch_count(ctx.h) - l0
+    assert int(st.abs().sum()) == 0, "a served frame reported a non-zero status"
+    ctx.close()
+    lat = np.sort(np.asarray(lat)) * 1e3
+    return {"offered_frames_per_s": rate, "frames_per_s": n_req / wall, "requests": n_req,
+            "p50_ms": float(lat[len(lat) // 2]), "p99_ms": float(lat[int(0.99 * (len(lat) - 1))]),
+            "max_ms": float(lat[-1]), "budget_gb": budget_gb, "gpu_launches": int(launches),
+            "profiles": {k: {"M": v[0], "T": v[1], "K_max": v[2], "fov_deg": v[3], "step_deg": v[4]}
+                         for k, v in synth.SERVING_PROFILES.items()},
+            "latency": "observed completion - scheduled Poisson arrival (host clock, polled)"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -223,8 +317,8 @@ def main():
     method_id = binding.FM_RAND_PROJECTION if args.method == "projection" else binding.FM_RAND_SAMPLING
     B = args.batch
     wl = synth.massive_mimo_frames(B, seed=rank)           # each rank: its own frames (weak scaling)
-    for b, fr in enumerate(wl.frames):
-        fr.frame_id = rank * B + b
+    for fr, fid in zip(wl.frames, shard_frame_ids(rank, B)):
+        fr.frame_id = fid
     M, T, K, l, t, L = 512, 1024, 8, 24, 1, 15001
     fr0 = wl.frames[0]
     Xh = torch.from_numpy(np.stack([fr.X for fr in wl.frames])).pin_memory()
@@ -269,11 +363,8 @@ def main():
     step_ms = [step_ev[k].elapsed_time(step_ev[k + 1]) for k in range(args.steps)]
     total_ms = step_ev[0].elapsed_time(step_ev[-1])
     stages = ctx.stage_times(reset=True)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * B * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, dev)
+    value = job_rate(world, B, args.steps, total_ms / 1e3)
 
     # ---- end-to-end through the C ABI (host buffers) ----------------------------
     Ph = torch.empty((B, L), dtype=torch.float32).pin_memory()
@@ -297,11 +388,8 @@ def main():
         degh.copy_(deg, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_value = world * B * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(e2e_s, dev)
+    e2e_value = job_rate(world, B, e2e_steps, e2e_s)
     h2d = Xh.numel() * Xh.element_size()
     d2h = Ph.numel() * 4 + idxh.numel() * 4 + degh.numel() * 4
 
@@ -354,6 +442,11 @@ def main():
                 "method": "standard MUSIC: our covariance kernel + torch.linalg.eigh (cuSOLVER) + our scan/peaks",
                 "speedup_fast_vs_full": (value / world) / (B / (fms / 1e3))}
 
+    # ---- serving mix: continuous batching under Poisson arrivals ----------------
+    serving = None
+    if args.serve_requests > 0:
+        serving = serving_run(binding, synth, dev, args.serve_requests, args.serve_rate)
+
     # ---- CPU oracle baseline -----------------------------------------------------
     cpu = None
     if not args.no_baseline and rank == 0:
@@ -375,7 +468,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": roof, "dominant_stage": dom, "stages": stage_summary,
-        "full_eig_music": full, "cpu_baseline": cpu, "clocks": clk,
+        "serving": serving, "full_eig_music": full, "cpu_baseline": cpu, "clocks": clk,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

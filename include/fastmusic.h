@@ -235,10 +235,20 @@ fm_status fm_spectrum_noalloc(const void* U, int n_frames, int M, int ncols, dou
                               float* P, fm_stream stream);
 
 /* ---- serving (continuous batching) ------------------------------------------
- * fm_serve_submit: enqueue one frame; the library admits queued frames into
- * device work as workspace within the budget frees up, overlapping them on its
- * own streams.  *ticket identifies the request.  fm_serve_poll sets *done = 1
- * once the frame's outputs are complete on the device. */
+ * fm_serve_submit: enqueue one frame (validated as in fm_run; a frame whose
+ * workspace alone exceeds the context budget returns FM_ERR_OOM_BUDGET) and set
+ * *ticket.  The library runs up to 4 slots, each a stream with a private
+ * workspace.  Whenever a slot is free it takes the queued frames in arrival
+ * order, up to 64 and as many as the budget left beside the other slots'
+ * workspaces allows, and runs them as one fm_run batch; frames that arrive
+ * while others run overlap with them on the GPU, and under load the batches
+ * grow.  Queued work advances inside fm_serve_submit and fm_serve_poll.
+ * fm_serve_poll sets *done = 1 once the frame's outputs are complete on the
+ * device (FM_ERR_CUDA with *done = 1 if its batch failed; FM_ERR_NOT_READY for
+ * an unknown ticket).  The caller's X and output buffers must stay valid until
+ * then.  A frame's result does not depend on its batch beyond the scan path:
+ * the tensor-core scan (a batch sharing M, U_s columns and grid) and the
+ * CUDA-core scan agree within the scan tolerance. */
 fm_status fm_serve_submit(fm_ctx* ctx, const fm_frame* frame, uint64_t* ticket);
 fm_status fm_serve_poll(fm_ctx* ctx, uint64_t ticket, int* done);
 

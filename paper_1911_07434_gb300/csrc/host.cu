@@ -64,13 +64,17 @@ struct fm_ctx {
     std::map<uint64_t, int> done;  // ticket -> 1 when complete
     uint64_t next_ticket = 1;
     uint64_t serve_launches = 0;
+    // set on a serving slot's private context: the arena grows with stream-ordered
+    // free/alloc on that slot's stream, which other slots' work never waits for
+    cudaStream_t arena_stream = nullptr;
+    size_t arena_cap = 0;  // serving slot: what the budget leaves beside the other slots
 };
 
 struct fm_ctx::Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     fm_ctx* sub = nullptr;  // a private context (own arena and staging) per slot
-    uint64_t ticket = 0;
+    std::vector<uint64_t> tickets;  // the frames of the batch in flight
     bool busy = false;
 };
 
@@ -131,6 +135,26 @@ fm_status ensure_arena(fm_ctx* c, size_t need) {
     if (need > c->budget)
         return fail(c, FM_ERR_OOM_BUDGET, "workspace of %zu bytes exceeds the context budget of %zu bytes", need,
                     c->budget);
+    if (c->arena_stream) {  // serving slot: free and reallocate in the slot's stream order
+        if (c->arena) {
+            cudaError_t e = cudaFreeAsync(c->arena, c->arena_stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaFreeAsync(workspace)");
+            c->arena = nullptr;
+            c->arena_bytes = 0;
+        }
+        const size_t cap = std::min(c->budget, c->arena_cap);
+        if (need > cap)
+            return fail(c, FM_ERR_OOM_BUDGET, "workspace of %zu bytes exceeds the %zu bytes left in the budget", need,
+                        cap);
+        size_t sz = std::min(cap, need + need / 4);
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&c->arena), sz, c->arena_stream);
+        if (e != cudaSuccess) {
+            c->arena = nullptr;
+            return cuda_fail(c, e, "cudaMallocAsync(workspace)");
+        }
+        c->arena_bytes = sz;
+        return FM_OK;
+    }
     if (c->arena) {
         cudaError_t e = cudaDeviceSynchronize();  // the old arena may still be read by queued work
         if (e != cudaSuccess) return cuda_fail(c, e, "cudaDeviceSynchronize");
@@ -473,9 +497,10 @@ fm_status fm_destroy(fm_ctx* c) {
     cudaSetDevice(c->device);
     for (fm_ctx::Slot* sl : c->slots) {
         if (sl->stream) cudaStreamSynchronize(sl->stream);
+        if (sl->sub) fm_destroy(sl->sub);  // frees its workspace on sl->stream
+        if (sl->stream) cudaStreamSynchronize(sl->stream);
         if (sl->ev) cudaEventDestroy(sl->ev);
         if (sl->stream) cudaStreamDestroy(sl->stream);
-        if (sl->sub) fm_destroy(sl->sub);
         delete sl;
     }
     if (c->staging_done) {
@@ -490,7 +515,10 @@ fm_status fm_destroy(fm_ctx* c) {
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     if (c->arena) {
         cudaDeviceSynchronize();
-        cudaFree(c->arena);
+        if (c->arena_stream)
+            cudaFreeAsync(c->arena, c->arena_stream);
+        else
+            cudaFree(c->arena);
     }
     if (c->pinned) cudaFreeHost(c->pinned);
     delete c;
@@ -822,10 +850,23 @@ int fm_last_scan_path(const fm_ctx* c) { return c ? c->last_scan_path : 0; }
 uint64_t fm_launch_count(const fm_ctx* c) { return c ? c->launches + c->serve_launches : 0; }
 
 // ------------------------------------------------------------ serving ----
-// Continuous batching: each admitted frame runs the whole chain on one of a
-// fixed set of slots (stream + private workspace).  Admission happens when a
-// slot is free and the frame's workspace fits into what is left of the budget;
-// frames that arrive while others are running overlap with them on the device.
+// Continuous batching.  A fixed set of slots (stream + private workspace) runs
+// batches; whenever a slot is free, it takes the queued frames in arrival order,
+// as many as fit (at most kServeMaxBatch, and the batch's workspace within what
+// the budget leaves after the other slots' workspaces), and runs them as one
+// fm_run batch.  Under light load a frame starts alone as soon as it arrives;
+// under heavy load the queue grows while the slots are busy and the next batches
+// are larger.  Frames that arrive while others run overlap with them on the GPU.
+constexpr int kServeMaxSlots = 4;
+constexpr int kServeMaxBatch = 64;
+
+// Only for an idle slot (no work of its stream still reads the workspace).
+static void release_arena(fm_ctx* sub) {
+    cudaFreeAsync(sub->arena, sub->arena_stream);
+    sub->arena = nullptr;
+    sub->arena_bytes = 0;
+}
+
 static size_t serve_held(const fm_ctx* c) {
     size_t held = 0;
     for (const fm_ctx::Slot* sl : c->slots) held += sl->sub ? sl->sub->arena_bytes : 0;
@@ -836,50 +877,71 @@ static void serve_progress(fm_ctx* c) {
     // retire finished slots
     for (fm_ctx::Slot* sl : c->slots) {
         if (sl->busy && cudaEventQuery(sl->ev) == cudaSuccess) {
-            c->done[sl->ticket] = 1;
+            for (uint64_t t : sl->tickets) c->done[t] = 1;
+            sl->tickets.clear();
             sl->busy = false;
         }
     }
-    // admit in arrival order while a slot is free and the workspace fits the budget
+    std::vector<fm_frame> batch;
     while (!c->queue.empty()) {
-        const fm_frame& f = c->queue.front().second;
-        const size_t need = fm_workspace_bytes(&f, 1);
-        fm_ctx::Slot* pick = nullptr;
-        for (fm_ctx::Slot* sl : c->slots)  // a free slot whose workspace already fits
-            if (!sl->busy && sl->sub->arena_bytes >= need) {
-                pick = sl;
+        fm_ctx::Slot* pick = nullptr;  // the free slot with the largest workspace
+        for (fm_ctx::Slot* sl : c->slots)
+            if (!sl->busy && (!pick || sl->sub->arena_bytes > pick->sub->arena_bytes)) pick = sl;
+        if (!pick && (int)c->slots.size() < kServeMaxSlots) {
+            fm_ctx::Slot* sl = new fm_ctx::Slot();
+            if (cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&sl->ev, cudaEventDisableTiming) != cudaSuccess ||
+                fm_create(&sl->sub, c->budget, c->device) != FM_OK) {
+                if (sl->ev) cudaEventDestroy(sl->ev);
+                if (sl->stream) cudaStreamDestroy(sl->stream);
+                delete sl;
                 break;
             }
-        if (!pick) {
-            const size_t grow = need + need / 4;
-            for (fm_ctx::Slot* sl : c->slots)  // a free slot that may grow
-                if (!sl->busy && serve_held(c) - sl->sub->arena_bytes + grow <= c->budget) {
-                    pick = sl;
-                    break;
-                }
-            if (!pick && c->slots.size() < 16 && serve_held(c) + grow <= c->budget) {
-                fm_ctx::Slot* sl = new fm_ctx::Slot();
-                if (cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess ||
-                    cudaEventCreateWithFlags(&sl->ev, cudaEventDisableTiming) != cudaSuccess ||
-                    fm_create(&sl->sub, c->budget, c->device) != FM_OK) {
-                    delete sl;
-                    break;
-                }
-                c->slots.push_back(sl);
-                pick = sl;
+            sl->sub->arena_stream = sl->stream;
+            sl->sub->cov_path = c->cov_path;
+            sl->sub->scan_path = c->scan_path;
+            c->slots.push_back(sl);
+            pick = sl;
+        }
+        if (!pick) break;  // every slot busy: the queue waits and the next batch grows
+        const size_t others = serve_held(c) - pick->sub->arena_bytes;
+        const size_t room = c->budget > others ? c->budget - others : 0;
+        batch.clear();
+        for (const auto& q : c->queue) {
+            if ((int)batch.size() == kServeMaxBatch) break;
+            batch.push_back(q.second);
+            const size_t need = fm_workspace_bytes(batch.data(), (int)batch.size());
+            if (need > pick->sub->arena_bytes && need > room) {  // the slot could not grow that far
+                batch.pop_back();  // empty when not even the first frame fits
+                break;
             }
         }
-        if (!pick) break;  // wait for a slot or for memory
-        const uint64_t ticket = c->queue.front().first;
-        fm_status st = fm_run(pick->sub, &f, 1, reinterpret_cast<fm_stream>(pick->stream));
-        c->queue.pop_front();
+        pick->sub->arena_cap = room;
+        if (batch.empty()) {
+            // release the workspaces of the other idle slots, then retry; with none left
+            // to release, wait for a busy slot to finish
+            bool freed = false;
+            for (fm_ctx::Slot* sl : c->slots)
+                if (!sl->busy && sl != pick && sl->sub->arena) {
+                    release_arena(sl->sub);
+                    freed = true;
+                }
+            if (freed) continue;
+            break;
+        }
+        fm_status st = fm_run(pick->sub, batch.data(), (int)batch.size(), reinterpret_cast<fm_stream>(pick->stream));
+        pick->tickets.clear();
+        for (size_t i = 0; i < batch.size(); ++i) {
+            pick->tickets.push_back(c->queue.front().first);
+            c->queue.pop_front();
+        }
         if (st != FM_OK) {
             c->err = pick->sub->err;
-            c->done[ticket] = -1;
+            for (uint64_t t : pick->tickets) c->done[t] = -1;
+            pick->tickets.clear();
             continue;
         }
         cudaEventRecord(pick->ev, pick->stream);
-        pick->ticket = ticket;
         pick->busy = true;
     }
     uint64_t n = 0;
@@ -913,7 +975,9 @@ fm_status fm_serve_poll(fm_ctx* c, uint64_t ticket, int* done) {
         for (auto& q : c->queue)
             if (q.first == ticket) return FM_OK;
         for (fm_ctx::Slot* sl : c->slots)
-            if (sl->busy && sl->ticket == ticket) return FM_OK;
+            if (sl->busy)
+                for (uint64_t t : sl->tickets)
+                    if (t == ticket) return FM_OK;
         return fail(c, FM_ERR_NOT_READY, "unknown ticket %llu", (unsigned long long)ticket);
     }
     if (it->second < 0) {
