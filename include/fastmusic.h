@@ -66,10 +66,17 @@ typedef enum {
     FM_RAND_PROJECTION = 2  /* fast MUSIC 2, Sec. III-B, Algorithm 2 */
 } fm_method;
 
+/* Operand precision of the two large GEMM-shaped steps, the covariance (Eq. 2)
+ * and the scan (Eq. 10), when they run on the tensor cores; the accumulator is
+ * FP32 in every mode, and the sketch, the small solves and the main-lobe scan
+ * recompute stay FP32 (double-float where stated).  Where the CUDA-core
+ * covariance runs instead (X not 16-byte aligned or ldx odd), it is FP32 in
+ * every mode.  BF16 keeps FP32's exponent range, so no per-frame scaling is
+ * applied. */
 typedef enum {
-    FM_PREC_FP32 = 0, /* all GEMM-shaped steps with FP32 products and FP32 accumulation */
-    FM_PREC_TF32 = 1, /* reserved: TF32 tensor-core operands, FP32 accumulation */
-    FM_PREC_BF16 = 2  /* reserved: BF16 tensor-core operands, FP32 accumulation */
+    FM_PREC_FP32 = 0, /* FP32 products: 3 TF32 MMAs per product (hi*hi + hi*lo + lo*hi) */
+    FM_PREC_TF32 = 1, /* TF32 operands (10-bit mantissa), one MMA per product */
+    FM_PREC_BF16 = 2  /* BF16 operands (7-bit mantissa), one kind::f16 MMA per 16 elements */
 } fm_precision;
 
 /* Uniform linear array (Sec. II-A): M elements, spacing d_wl wavelengths (0 => 0.5). */
@@ -87,9 +94,12 @@ typedef struct {
 
 /* Estimator parameters.  K = number of sources, l = sketch size (the paper's p,
  * K <= l <= min(M, 48)), t = power iterations (Eq. 11; 0..8).  rank_restrict:
- * number of columns of U_s used by the scan, K (0 means K) or l.  refine and
- * prec other than FP32 are reserved and must be 0.  seed keys the Philox
- * stream of Pi / the sampled index set. */
+ * number of columns of U_s used by the scan, K (0 means K) or l.  prec: an
+ * fm_precision.  refine = 1 adds one power step computed in FP32 from the
+ * snapshots, V = orth(C), C = X (X^H V) / T (= R V without forming R), before the
+ * final Rayleigh-Ritz solve, which then uses H = V^H C for both methods; it
+ * wins back the accuracy a TF32 / BF16 covariance loses (fm_run only).  seed
+ * keys the Philox stream of Pi / the sampled index set. */
 typedef struct {
     int method; /* fm_method */
     int K;
@@ -143,10 +153,17 @@ size_t fm_workspace_bytes(const fm_frame* frames, int n_frames);
  * method must be FM_RAND_SAMPLING or FM_RAND_PROJECTION. */
 fm_status fm_run(fm_ctx* ctx, const fm_frame* frames, int n_frames, fm_stream stream);
 
+/* fm_run_subspace: copy U_s (complex64 M x ncols, row-major) of frame `frame` of
+ * the most recent fm_run on this context into U (device), asynchronously on
+ * `stream`.  The copy reads the context's workspace, so it must be issued before
+ * the next call that uses this context; FM_ERR_INVALID_ARG if there is no such
+ * frame. */
+fm_status fm_run_subspace(fm_ctx* ctx, int frame, void* U, fm_stream stream);
+
 /* ---- steps (uniform batches; each frame at a fixed stride) ------------------
  * fm_covariance (Eq. 2): R_b = X_b X_b^H / T for b < n_frames.  X_b = X +
  * b * x_frame_stride complex elements; R_b = R + b*M*M (complex64, full
- * Hermitian matrix written). */
+ * Hermitian matrix written).  prec: an fm_precision (tensor-core path only). */
 fm_status fm_covariance(fm_ctx* ctx, const void* X, int n_frames, int M, int T, int64_t ldx,
                         int64_t x_frame_stride, void* R, int prec, fm_stream stream);
 
@@ -180,8 +197,8 @@ fm_status fm_sample_indices(fm_ctx* ctx, uint64_t seed, uint64_t frame_id, int M
  * events.  fm_stage_times synchronises on them and returns, per stage, the
  * summed milliseconds and the number of launches since the last reset.
  * Stage order: 0 grid table, 1 covariance, 2 sketch, 3 orth, 4 final small
- * solve, 5 scan, 6 peaks. */
-#define FM_N_STAGES 7
+ * solve, 5 scan, 6 peaks, 7 FP32 refinement step. */
+#define FM_N_STAGES 8
 fm_status fm_set_timing(fm_ctx* ctx, int enable);
 fm_status fm_stage_times(fm_ctx* ctx, double* total_ms, int* launches, int reset);
 /* Number of kernel launches issued by this context since creation. */

@@ -32,8 +32,8 @@ FM_PREC_FP32 = 0
 FM_COV_AUTO = 0
 FM_COV_SIMT = 1
 FM_COV_TC = 2
-FM_N_STAGES = 7
-STAGES = ("grid", "covariance", "sketch", "orth", "final", "scan", "peaks")
+FM_N_STAGES = 8
+STAGES = ("grid", "covariance", "sketch", "orth", "final", "scan", "peaks", "refine")
 
 
 class FmArray(ctypes.Structure):
@@ -74,6 +74,7 @@ _SIGS = {
     "fm_set_timing": (c_int, [c_void_p, c_int]),
     "fm_stage_times": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int), c_int]),
     "fm_launch_count": (c_uint64, [c_void_p]),
+    "fm_run_subspace": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "fm_set_cov_path": (c_int, [c_void_p, c_int]),
     "fm_last_cov_path": (c_int, [c_void_p]),
     "fm_set_scan_path": (c_int, [c_void_p, c_int]),
@@ -172,6 +173,10 @@ def fm_stage_times(ctx, reset=False):
     return st, list(ms), list(n)
 
 
+def fm_run_subspace(ctx, frame, U, stream) -> int:
+    return load().fm_run_subspace(ctx, frame, U, stream)
+
+
 def fm_launch_count(ctx) -> int:
     return load().fm_launch_count(ctx)
 
@@ -245,7 +250,7 @@ class Context:
     # frames -----------------------------------------------------------------
     @staticmethod
     def frame(X, K, l, t, method, theta0, step, L, P, peak_idx, peak_deg, n_peaks, seed=0, frame_id=0,
-              d_wl=0.5, status=None, P_db=None, rank_restrict=0) -> FmFrame:
+              d_wl=0.5, status=None, P_db=None, rank_restrict=0, prec=0, refine=0) -> FmFrame:
         """FmFrame for a complex64 CUDA tensor X (M x T, row stride >= T)."""
         M, T = X.shape
         f = FmFrame()
@@ -254,7 +259,7 @@ class Context:
         f.ldx = X.stride(0)
         f.arr = FmArray(M, d_wl)
         f.grid = FmGrid(theta0, step, L)
-        f.p = FmParams(method, K, l, t, FM_PREC_FP32, rank_restrict, 0, 0, seed)
+        f.p = FmParams(method, K, l, t, prec, rank_restrict, refine, 0, seed)
         f.frame_id = frame_id
         f.P_out = P.data_ptr()
         f.P_db_out = P_db.data_ptr() if P_db is not None else None
@@ -267,7 +272,14 @@ class Context:
     def run(self, frames, stream=None):
         self._check(fm_run(self.h, frames, _stream_handle(stream)), "fm_run")
 
-    def covariance(self, X, R=None, stream=None):
+    def run_subspace(self, frame: int, M: int, ncols: int, stream=None):
+        """U_s (M x ncols complex64) of frame `frame` of the last run() on this context."""
+        import torch
+        U = torch.empty((M, ncols), dtype=torch.complex64, device=f"cuda:{self.device}")
+        self._check(fm_run_subspace(self.h, frame, U.data_ptr(), _stream_handle(stream)), "fm_run_subspace")
+        return U
+
+    def covariance(self, X, R=None, stream=None, prec=FM_PREC_FP32):
         """X: (B, M, T) or (M, T) complex64 CUDA tensor -> R (B, M, M) complex64."""
         import torch
         Xb = X if X.dim() == 3 else X.unsqueeze(0)
@@ -276,7 +288,7 @@ class Context:
         if R is None:
             R = torch.empty((B, M, M), dtype=torch.complex64, device=X.device)
         self._check(fm_covariance(self.h, Xb.data_ptr(), B, M, T, Xb.stride(1), Xb.stride(0), R.data_ptr(),
-                                  FM_PREC_FP32, _stream_handle(stream)), "fm_covariance")
+                                  prec, _stream_handle(stream)), "fm_covariance")
         return R
 
     def subspace(self, R, K, l, t, method, seed=0, frame_id0=0, rank_restrict=0, stream=None):

@@ -9,7 +9,10 @@
 //   D_top = Xr_I [Xr_J; Xi_J]^T = [rr | ri],  D_bot = Xi_I [Xr_J; Xi_J]^T = [ir | ii].
 // FP32 accuracy from TF32 tensor cores ("3xTF32"): every operand x is split into
 // hi = rn_tf32(x) and lo = rn_tf32(x - hi), and each product is formed as
-// hi*hi + hi*lo + lo*hi (the dropped lo*lo term is below 2^-22 |x y|).
+// hi*hi + hi*lo + lo*hi (the dropped lo*lo term is below 2^-22 |x y|).  The
+// frame's precision mode selects this (FM_PREC_FP32), hi*hi alone (FM_PREC_TF32),
+// or BF16 operands with one kind::f16 MMA per 16 snapshots (FM_PREC_BF16); the
+// accumulator is FP32 in every mode.
 //
 // Warp roles (192 threads): warp 0 issues the TMA loads of the raw interleaved
 // complex64 tiles (128 rows x 16 snapshots = one 128-byte swizzled box per
@@ -38,6 +41,7 @@ constexpr int kTiles = kNRaw * kRawStage + kNConv * kConvStage;   // 192 KB
 constexpr int kSmemBytes = kTiles + 1024 + 256;                   // + 1024-B alignment slack + barriers
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kIdesc = idesc_tf32(128, 256);  // M = 128 rows of X_I, N = 256 rows of [Xr_J; Xi_J]
+constexpr uint32_t kIdescBf16 = idesc_bf16(128, 256);
 
 __device__ __forceinline__ void tile_coords(int b, int nt, int& ti, int& tj) {
     ti = 0;
@@ -61,8 +65,26 @@ __device__ __forceinline__ void split4(float a, float b, float c, float d, uint4
 }
 
 // Convert one 128-row raw box (interleaved complex, 16 per row) into the planar
-// hi/lo rows of two destination tiles (re -> dre row rr, im -> dim row ri).
-__device__ __forceinline__ void convert_row(const char* raw, int r, char* dre, int rr, char* dim, int ri) {
+// rows of two destination tiles (re -> dre row rr, im -> dim row ri):
+// FP32 (3xTF32) [hi 16 | lo 16] TF32, TF32 [hi 16] only, BF16 16 values in the
+// first 32 bytes of the row.
+__device__ __forceinline__ void convert_row(const char* raw, int r, char* dre, int rr, char* dim, int ri, int prec) {
+    if (prec == FM_PREC_BF16) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // output chunk h: complex 8h .. 8h+7
+            const float4 v0 = *reinterpret_cast<const float4*>(raw + swz(r, 4 * h));
+            const float4 v1 = *reinterpret_cast<const float4*>(raw + swz(r, 4 * h + 1));
+            const float4 v2 = *reinterpret_cast<const float4*>(raw + swz(r, 4 * h + 2));
+            const float4 v3 = *reinterpret_cast<const float4*>(raw + swz(r, 4 * h + 3));
+            const uint4 re = make_uint4(bf16x2_rn(v0.x, v0.z), bf16x2_rn(v1.x, v1.z), bf16x2_rn(v2.x, v2.z),
+                                        bf16x2_rn(v3.x, v3.z));
+            const uint4 im = make_uint4(bf16x2_rn(v0.y, v0.w), bf16x2_rn(v1.y, v1.w), bf16x2_rn(v2.y, v2.w),
+                                        bf16x2_rn(v3.y, v3.w));
+            *reinterpret_cast<uint4*>(dre + swz(rr, h)) = re;
+            *reinterpret_cast<uint4*>(dim + swz(ri, h)) = im;
+        }
+        return;
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {  // output chunk q: complex 4q .. 4q+3
         const float4 v0 = *reinterpret_cast<const float4*>(raw + swz(r, 2 * q));
@@ -71,9 +93,11 @@ __device__ __forceinline__ void convert_row(const char* raw, int r, char* dre, i
         split4(v0.x, v0.z, v1.x, v1.z, rh, rl);
         split4(v0.y, v0.w, v1.y, v1.w, ih, il);
         *reinterpret_cast<uint4*>(dre + swz(rr, q)) = rh;
-        *reinterpret_cast<uint4*>(dre + swz(rr, 4 + q)) = rl;
         *reinterpret_cast<uint4*>(dim + swz(ri, q)) = ih;
-        *reinterpret_cast<uint4*>(dim + swz(ri, 4 + q)) = il;
+        if (prec == FM_PREC_FP32) {
+            *reinterpret_cast<uint4*>(dre + swz(rr, 4 + q)) = rl;
+            *reinterpret_cast<uint4*>(dim + swz(ri, 4 + q)) = il;
+        }
     }
 }
 
@@ -93,7 +117,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 10);
 
     const FrameDesc* dp = descs + blockIdx.y;
-    const int M = dp->M, T = dp->T;
+    const int M = dp->M, T = dp->T, prec = dp->prec;  // prec is uniform over the CTA
     const int nt = (M + kTile - 1) / kTile;
     if ((int)blockIdx.x >= nt * (nt + 1) / 2) return;
     int ti, tj;
@@ -157,18 +181,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 unsigned char* cv = conv + slot * kConvStage;
                 const uint32_t ar = sa(cv), ai = sa(cv + kConvA), bb = sa(cv + 2 * kConvA);
+                if (prec == FM_PREC_BF16) {  // one K = 16 step covers the stage's 16 snapshots
+                    const uint32_t acc0 = s > 0 ? 1u : 0u;
+                    mma_bf16(d_top, desc_sw128(ar), desc_sw128(bb), kIdescBf16, acc0);
+                    mma_bf16(d_bot, desc_sw128(ai), desc_sw128(bb), kIdescBf16, acc0);
+                } else {
 #pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                    const uint32_t acc0 = (s > 0 || kk > 0) ? 1u : 0u;
-                    const uint64_t b_hi = desc_sw128(bb + 32 * kk), b_lo = desc_sw128(bb + 64 + 32 * kk);
-                    const uint64_t r_hi = desc_sw128(ar + 32 * kk), r_lo = desc_sw128(ar + 64 + 32 * kk);
-                    const uint64_t i_hi = desc_sw128(ai + 32 * kk), i_lo = desc_sw128(ai + 64 + 32 * kk);
-                    mma_tf32(d_top, r_hi, b_hi, kIdesc, acc0);
-                    mma_tf32(d_top, r_hi, b_lo, kIdesc, 1u);
-                    mma_tf32(d_top, r_lo, b_hi, kIdesc, 1u);
-                    mma_tf32(d_bot, i_hi, b_hi, kIdesc, acc0);
-                    mma_tf32(d_bot, i_hi, b_lo, kIdesc, 1u);
-                    mma_tf32(d_bot, i_lo, b_hi, kIdesc, 1u);
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint32_t acc0 = (s > 0 || kk > 0) ? 1u : 0u;
+                        const uint64_t b_hi = desc_sw128(bb + 32 * kk), b_lo = desc_sw128(bb + 64 + 32 * kk);
+                        const uint64_t r_hi = desc_sw128(ar + 32 * kk), r_lo = desc_sw128(ar + 64 + 32 * kk);
+                        const uint64_t i_hi = desc_sw128(ai + 32 * kk), i_lo = desc_sw128(ai + 64 + 32 * kk);
+                        mma_tf32(d_top, r_hi, b_hi, kIdesc, acc0);
+                        mma_tf32(d_bot, i_hi, b_hi, kIdesc, acc0);
+                        if (prec == FM_PREC_FP32) {  // 3xTF32: + hi*lo + lo*hi
+                            mma_tf32(d_top, r_hi, b_lo, kIdesc, 1u);
+                            mma_tf32(d_top, r_lo, b_hi, kIdesc, 1u);
+                            mma_tf32(d_bot, i_hi, b_lo, kIdesc, 1u);
+                            mma_tf32(d_bot, i_lo, b_hi, kIdesc, 1u);
+                        }
+                    }
                 }
                 mma_commit(&conv_empty[slot]);  // frees the converted stage once these MMAs finish
             }
@@ -185,8 +217,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const char* rawA = reinterpret_cast<const char*>(raw + rs * kRawStage);
             const char* rawB = diag ? rawA : rawA + kRawBox;
             char* cv = reinterpret_cast<char*>(conv + cs * kConvStage);
-            convert_row(rawA, r, cv, r, cv + kConvA, r);                        // Ar, Ai
-            convert_row(rawB, r, cv + 2 * kConvA, r, cv + 2 * kConvA, 128 + r);  // B = [Br; Bi]
+            convert_row(rawA, r, cv, r, cv + kConvA, r, prec);                        // Ar, Ai
+            convert_row(rawB, r, cv + 2 * kConvA, r, cv + 2 * kConvA, 128 + r, prec);  // B = [Br; Bi]
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(&conv_full[cs]);
             mbar_arrive(&raw_empty[rs]);

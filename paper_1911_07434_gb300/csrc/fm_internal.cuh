@@ -18,11 +18,14 @@ struct FrameDesc {
     int64_t ldx;
     int M, T, K, l, t, method, L, ncols;  // ncols = columns of U_s used by the scan
     int kpad;          // padded column count of Us (multiple of 4)
+    int prec;          // fm_precision of the covariance and scan GEMMs
+    int refine;        // 1: one more power step C = X (X^H V) / T in FP32 before the final solve
     int pad_;
     float2* R;         // M x M
     float2* C;         // M x l  sketch
     float2* V;         // M x l  basis (power steps) / Q
     float2* Us;        // M x kpad (zero-padded)
+    float2* Y;         // T x l  X^H V of the refinement step (refine only)
     int* idx;          // l sampled indices
     float2* qtab;      // L entries (q_hi, q_lo): q = 2 d_wl sin(theta_i), split for exact m*q_hi
     float* P;          // L
@@ -163,7 +166,7 @@ cudaError_t launch_grid_table(const GridDesc* g, int n_grids, int max_L, const F
                               cudaStream_t s);
 cudaError_t launch_covariance_tc(const FrameDesc* d, const void* tmaps, int n_frames, int max_M, cudaStream_t s);
 size_t cov_tc_smem_bytes();
-cudaError_t launch_scan_tc(const FrameDesc* d, int n_frames, int M, int ncols, int L, float* bprep, const void* tmB,
+cudaError_t launch_scan_tc(const FrameDesc* d, int n_frames, int M, int ncols, int L, int prec, float* bprep, const void* tmB,
                            cudaStream_t s);
 int scan_tc_ncp(int ncols);
 cudaError_t launch_covariance(const FrameDesc* d, int n_frames, int max_M, cudaStream_t s);
@@ -171,6 +174,7 @@ cudaError_t launch_sketch(const FrameDesc* d, int n_frames, int max_M, int max_l
                           bool any_dense, cudaStream_t s);
 cudaError_t launch_orth(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, cudaStream_t s);
 cudaError_t launch_final(const FrameDesc* d, int n_frames, int max_M, int max_l, cudaStream_t s);
+cudaError_t launch_refine(const FrameDesc* d, int n_frames, int max_M, int max_T, cudaStream_t s);
 cudaError_t launch_scan(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s);
 cudaError_t launch_scan_fixup(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s);
 cudaError_t launch_peaks(const FrameDesc* d, int n_frames, int max_K, cudaStream_t s);

@@ -26,7 +26,7 @@ namespace {
 constexpr size_t kAlign = 256;
 inline size_t aup(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
-enum Stage { kStGrid = 0, kStCov, kStSketch, kStOrth, kStFinal, kStScan, kStPeaks };
+enum Stage { kStGrid = 0, kStCov, kStSketch, kStOrth, kStFinal, kStScan, kStPeaks, kStRefine };
 
 struct TimedEvent {
     int stage;
@@ -67,6 +67,8 @@ struct fm_ctx {
     // set on a serving slot's private context: the arena grows with stream-ordered
     // free/alloc on that slot's stream, which other slots' work never waits for
     cudaStream_t arena_stream = nullptr;
+    // U_s of the frames of the most recent fm_run: (workspace offset, M, ncols)
+    std::vector<std::tuple<size_t, int, int>> last_us;
     size_t arena_cap = 0;  // serving slot: what the budget leaves beside the other slots
 };
 
@@ -132,6 +134,7 @@ fm_status set_device(fm_ctx* c) {
 
 fm_status ensure_arena(fm_ctx* c, size_t need) {
     if (need <= c->arena_bytes) return FM_OK;
+    c->last_us.clear();  // the U_s kept for fm_run_subspace go with the old workspace
     if (need > c->budget)
         return fail(c, FM_ERR_OOM_BUDGET, "workspace of %zu bytes exceeds the context budget of %zu bytes", need,
                     c->budget);
@@ -220,8 +223,8 @@ const char* check_frame(const fm_frame& f) {
     if (p.K < 1 || p.K > p.l) return "need 1 <= K <= l";
     if (p.l > M || p.l > fm::kLMax) return "need l <= min(M, 48)";
     if (p.t < 0 || p.t > 8) return "t must be in [0, 8]";
-    if (p.prec != FM_PREC_FP32) return "only FM_PREC_FP32 is available";
-    if (p.refine != 0) return "refine is reserved";
+    if (p.prec != FM_PREC_FP32 && p.prec != FM_PREC_TF32 && p.prec != FM_PREC_BF16) return "prec must be 0, 1 or 2";
+    if (p.refine != 0 && p.refine != 1) return "refine must be 0 or 1";
     if (p.rank_restrict != 0 && p.rank_restrict != p.K && p.rank_restrict != p.l) return "rank_restrict must be 0, K or l";
     const int nc = ncols_of(p);
     if (nc > fm::kKPadMax) return "columns of U_s used by the scan must be <= 32";
@@ -233,9 +236,9 @@ const char* check_frame(const fm_frame& f) {
 struct Plan {
     size_t desc_off, tmap_off, grid_off, total;
     bool scan_uniform = false;  // all frames share M, ncols and one grid: batched tensor-core scan possible
-    int scan_M = 0, scan_nc = 0, scan_L = 0;
+    int scan_M = 0, scan_nc = 0, scan_L = 0, scan_prec = 0;
     size_t bprep_off = 0, bprep_rows = 0, bprep_rowlen = 0;
-    std::vector<size_t> R, C, V, Us, idx;  // per-frame offsets (R == SIZE_MAX: caller-owned)
+    std::vector<size_t> R, C, V, Us, idx, Y;  // per-frame offsets (R == SIZE_MAX: caller-owned)
     std::vector<int> grid_of;
     std::vector<GridDesc> grids;
     std::vector<size_t> qtab;
@@ -289,6 +292,9 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
         if (need_sketch) off = aup(off + sizeof(float2) * M * l);
         pl.idx.push_back(need_sketch ? off : SIZE_MAX);
         if (need_sketch) off = aup(off + sizeof(int) * l);
+        const bool y = need_sketch && f[b].p.refine;  // X^H V of the refinement step
+        pl.Y.push_back(y ? off : SIZE_MAX);
+        if (y) off = aup(off + sizeof(float2) * (size_t)f[b].T * l);
         const size_t nc = (size_t)ncols_of(f[b].p);
         pl.Us.push_back(need_Us ? off : SIZE_MAX);
         if (need_Us) off = aup(off + sizeof(float2) * M * nc);
@@ -296,13 +302,14 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
     if (need_R && need_Us && need_grid) {
         // batched tensor-core scan: one B operand row pair per (frame, column of U_s)
         bool uni = pl.grids.size() == 1;
-        const int M0 = f[0].arr.M, nc0 = ncols_of(f[0].p);
-        for (int b = 1; uni && b < n; ++b) uni = f[b].arr.M == M0 && ncols_of(f[b].p) == nc0;
+        const int M0 = f[0].arr.M, nc0 = ncols_of(f[0].p), pr0 = f[0].p.prec;
+        for (int b = 1; uni && b < n; ++b) uni = f[b].arr.M == M0 && ncols_of(f[b].p) == nc0 && f[b].p.prec == pr0;
         if (uni) {
             pl.scan_uniform = true;
             pl.scan_M = M0;
             pl.scan_nc = nc0;
             pl.scan_L = pl.grids[0].L;
+            pl.scan_prec = pr0;
             const int ncp = fm::scan_tc_ncp(nc0), Mp = (M0 + 7) / 8 * 8;
             pl.bprep_rows = (size_t)n * 2 * ncp;
             pl.bprep_rowlen = 4 * (size_t)Mp;
@@ -327,6 +334,8 @@ FrameDesc make_desc(const fm_frame& f) {
     d.L = f.grid.L;
     d.ncols = ncols_of(f.p);
     d.kpad = d.ncols;
+    d.prec = f.p.prec;
+    d.refine = f.p.refine;
     d.P = f.P_out;
     d.Pdb = f.P_db_out;
     d.peak_idx = f.peak_idx;
@@ -342,8 +351,8 @@ FrameDesc make_desc(const fm_frame& f) {
 }
 
 struct Maxes {
-    int M = 0, l = 0, L = 0, K = 0, kpad = 0, t = 0;
-    bool any_sampling = false, any_projection = false, any_status = false;
+    int M = 0, l = 0, L = 0, K = 0, kpad = 0, t = 0, T = 0;
+    bool any_sampling = false, any_projection = false, any_status = false, any_refine = false;
 };
 
 Maxes maxes_of(const std::vector<FrameDesc>& ds) {
@@ -355,6 +364,8 @@ Maxes maxes_of(const std::vector<FrameDesc>& ds) {
         m.K = std::max(m.K, d.K);
         m.kpad = std::max(m.kpad, d.kpad);
         m.t = std::max(m.t, d.t);
+        m.T = std::max(m.T, d.T);
+        m.any_refine |= d.refine != 0;
         m.any_sampling |= d.method == FM_RAND_SAMPLING;
         m.any_projection |= d.method == FM_RAND_PROJECTION;
         m.any_status |= d.status != nullptr;
@@ -468,6 +479,12 @@ fm_status run_subspace_chain(fm_ctx* c, FrameDesc* dd, int n, const Maxes& mx, c
         st = stage(c, kStSketch, s, [&] { return fm::launch_sketch(dd, n, mx.M, mx.l, p, false, true, s); });
         if (st != FM_OK) return st;
     }
+    if (mx.any_refine) {  // V = orth(C), then C = X (X^H V) / T in FP32 (frames with refine only)
+        st = stage(c, kStOrth, s, [&] { return fm::launch_orth(dd, n, mx.M, mx.l, -1, s); });
+        if (st != FM_OK) return st;
+        st = stage(c, kStRefine, s, [&] { return fm::launch_refine(dd, n, mx.M, mx.T, s); });
+        if (st != FM_OK) return st;
+    }
     return stage(c, kStFinal, s, [&] { return fm::launch_final(dd, n, mx.M, mx.l, s); });
 }
 
@@ -548,6 +565,7 @@ fm_status fm_run(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream) {
     st = ensure_arena(c, pl.total);
     if (st != FM_OK) return st;
     std::vector<FrameDesc> ds(n);
+    c->last_us.assign(n, std::make_tuple(SIZE_MAX, 0, 0));
     for (int b = 0; b < n; ++b) {
         FrameDesc d = make_desc(frames[b]);
         d.R = reinterpret_cast<float2*>(c->arena + pl.R[b]);
@@ -555,6 +573,8 @@ fm_status fm_run(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream) {
         d.V = reinterpret_cast<float2*>(c->arena + pl.V[b]);
         d.idx = reinterpret_cast<int*>(c->arena + pl.idx[b]);
         d.Us = reinterpret_cast<float2*>(c->arena + pl.Us[b]);
+        d.Y = pl.Y[b] != SIZE_MAX ? reinterpret_cast<float2*>(c->arena + pl.Y[b]) : nullptr;
+        c->last_us[b] = std::make_tuple(pl.Us[b], d.M, d.ncols);
         d.qtab = reinterpret_cast<float2*>(c->arena + pl.qtab[pl.grid_of[b]]);
         ds[b] = d;
     }
@@ -586,7 +606,7 @@ fm_status fm_run(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream) {
         float* bp = reinterpret_cast<float*>(c->arena + pl.bprep_off);
         const char* bmap_dev = c->arena + pl.tmap_off + sizeof(CUtensorMap) * (size_t)n;
         st = stage(c, kStScan, s, [&] {
-            cudaError_t e = fm::launch_scan_tc(dd, n, pl.scan_M, pl.scan_nc, pl.scan_L, bp, bmap_dev, s);
+            cudaError_t e = fm::launch_scan_tc(dd, n, pl.scan_M, pl.scan_nc, pl.scan_L, pl.scan_prec, bp, bmap_dev, s);
             if (e != cudaSuccess) return e;
             // main-lobe angles again on the FP32 CUDA cores (see scan_kernel<..., FIXUP>)
             return fm::launch_scan_fixup(dd, n, mx.L, mx.M, mx.kpad, s);
@@ -598,12 +618,26 @@ fm_status fm_run(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream) {
     return stage(c, kStPeaks, s, [&] { return fm::launch_peaks(dd, n, mx.K, s); });
 }
 
+fm_status fm_run_subspace(fm_ctx* c, int frame, void* U, fm_stream stream) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (!U || frame < 0 || frame >= (int)c->last_us.size() || std::get<0>(c->last_us[frame]) == SIZE_MAX)
+        return fail(c, FM_ERR_INVALID_ARG, "fm_run_subspace: no frame %d in the last fm_run", frame);
+    fm_status st = set_device(c);
+    if (st != FM_OK) return st;
+    const size_t bytes = sizeof(float2) * (size_t)std::get<1>(c->last_us[frame]) * std::get<2>(c->last_us[frame]);
+    cudaError_t e = cudaMemcpyAsync(U, c->arena + std::get<0>(c->last_us[frame]), bytes, cudaMemcpyDeviceToDevice,
+                                    reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync(U_s)");
+    return FM_OK;
+}
+
 fm_status fm_covariance(fm_ctx* c, const void* X, int n, int M, int T, int64_t ldx, int64_t xstride, void* R,
                         int prec, fm_stream stream) {
     if (!c) return FM_ERR_INVALID_ARG;
     if (!X || !R || n < 1 || M < 1 || M > 65536 || T < 1 || ldx < T || xstride < (int64_t)(M - 1) * ldx + T)
         return fail(c, FM_ERR_INVALID_ARG, "fm_covariance: invalid shape or pointer");
-    if (prec != FM_PREC_FP32) return fail(c, FM_ERR_INVALID_ARG, "fm_covariance: only FM_PREC_FP32 is available");
+    if (prec != FM_PREC_FP32 && prec != FM_PREC_TF32 && prec != FM_PREC_BF16)
+        return fail(c, FM_ERR_INVALID_ARG, "fm_covariance: prec must be 0, 1 or 2");
     fm_status st = set_device(c);
     if (st != FM_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -618,6 +652,7 @@ fm_status fm_covariance(fm_ctx* c, const void* X, int n, int M, int T, int64_t l
         d.ldx = ldx;
         d.M = M;
         d.T = T;
+        d.prec = prec;
         d.R = reinterpret_cast<float2*>(R) + (int64_t)b * M * M;
         ds[b] = d;
     }
@@ -640,6 +675,7 @@ fm_status fm_subspace(fm_ctx* c, const void* R, int n, int M, const fm_params* p
                       int* status, fm_stream stream) {
     if (!c) return FM_ERR_INVALID_ARG;
     if (!R || !U || !p || n < 1) return fail(c, FM_ERR_INVALID_ARG, "fm_subspace: NULL argument");
+    if (p->refine) return fail(c, FM_ERR_INVALID_ARG, "fm_subspace: refine needs the snapshots X (use fm_run)");
     std::vector<fm_frame> fr(n);
     for (int b = 0; b < n; ++b) {
         fm_frame f{};

@@ -10,8 +10,10 @@
 // the CTA itself (the exact phase reduction of scan.cu, one sincospi per
 // element) and written to shared memory as TF32 hi/lo pairs; B (U_s of up to
 // 512 / (2 ncp) frames, already split into hi/lo by scan_bprep_kernel) arrives by
-// TMA.  Each FP32 product is formed as hi*hi + hi*lo + lo*hi (3xTF32).  Two
-// 128 x 256 FP32 accumulators fill the 512 TMEM columns.
+// TMA.  Each FP32 product is formed as hi*hi + hi*lo + lo*hi (3xTF32); the
+// batch's precision mode may instead take hi*hi alone (FM_PREC_TF32) or BF16
+// operands (FM_PREC_BF16, one kind::f16 MMA per 8 antennas).  Two 128 x 256 FP32
+// accumulators fill the 512 TMEM columns.
 //
 // Warp roles (192 threads): warp 0 TMA producer, warp 1 TMEM allocation + MMA
 // issue, warps 2-5 steering generation (one angle row each) and the epilogue.
@@ -33,6 +35,7 @@ constexpr int kTiles = kNStages * kStage;  // 160 KB
 constexpr int kSmemBytes = kTiles + 1024 + 256;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kIdesc = idesc_tf32(128, 256);
+constexpr uint32_t kIdescBf16 = idesc_bf16(128, 256);
 
 __device__ __forceinline__ void split2(float a, float b, uint32_t* hi, uint32_t* lo) {
     hi[0] = tf32_rn(a);
@@ -43,7 +46,7 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t* hi, uint32_t*
 
 // B rows for the frames of one launch: row f*2ncp + 2k (Re) and + 1 (Im); along a
 // row, stage s (8 antennas) holds 32 floats [hi of 16 interleaved values | lo].
-__global__ void scan_bprep_kernel(const FrameDesc* __restrict__ descs, int n_frames, int M, int Mp, int ncp,
+__global__ void scan_bprep_kernel(const FrameDesc* __restrict__ descs, int n_frames, int M, int Mp, int ncp, int prec,
                                   float* __restrict__ Bp) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (f, k, m)
     const int64_t total = (int64_t)n_frames * ncp * Mp;
@@ -58,6 +61,11 @@ __global__ void scan_bprep_kernel(const FrameDesc* __restrict__ descs, int n_fra
     float* re_row = Bp + ((int64_t)f * 2 * ncp + 2 * k) * rowlen;
     float* im_row = re_row + rowlen;
     const int s = m >> 3, p = (2 * m) & 15;
+    if (prec == FM_PREC_BF16) {  // 16 BF16 values in the first 32 bytes of the stage's 128
+        reinterpret_cast<uint32_t*>(re_row)[s * 32 + p / 2] = bf16x2_rn(u.x, u.y);
+        reinterpret_cast<uint32_t*>(im_row)[s * 32 + p / 2] = bf16x2_rn(-u.y, u.x);
+        return;
+    }
     uint32_t hi[2], lo[2];
     split2(u.x, u.y, hi, lo);  // Re row: [ur, ui]
     re_row[s * 32 + p] = __uint_as_float(hi[0]);
@@ -74,7 +82,7 @@ __global__ void scan_bprep_kernel(const FrameDesc* __restrict__ descs, int n_fra
 template <int NCP>
 __global__ void __launch_bounds__(kThreads, 1)
     scan_tc_kernel(const FrameDesc* __restrict__ descs, int n_frames, const CUtensorMap* __restrict__ tmB, int M,
-                   int Mp, int L) {
+                   int Mp, int L, int prec) {
     constexpr int kRowsPerFrame = 2 * NCP;
     constexpr int kFramesPerCta = kRowsB / kRowsPerFrame;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -143,20 +151,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!mbar_wait(&b_full[slot], ph, abort_flag)) break;
                 tc_fence_after();
                 const uint32_t a = sa(base + slot * kStage), b = a + kStageA;
+                if (prec == FM_PREC_BF16) {  // one K = 16 step per stage
+                    const uint32_t acc0 = s > 0 ? 1u : 0u;
+                    mma_bf16(tmem, desc_sw128(a), desc_sw128(b), kIdescBf16, acc0);
+                    if (two) mma_bf16(tmem + 256, desc_sw128(a), desc_sw128(b + 256 * 128), kIdescBf16, acc0);
+                } else {
 #pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                    const uint32_t acc0 = (s > 0 || kk > 0) ? 1u : 0u;
-                    const uint64_t a_hi = desc_sw128(a + 32 * kk), a_lo = desc_sw128(a + 64 + 32 * kk);
-                    const uint64_t b0_hi = desc_sw128(b + 32 * kk), b0_lo = desc_sw128(b + 64 + 32 * kk);
-                    mma_tf32(tmem, a_hi, b0_hi, kIdesc, acc0);
-                    mma_tf32(tmem, a_hi, b0_lo, kIdesc, 1u);
-                    mma_tf32(tmem, a_lo, b0_hi, kIdesc, 1u);
-                    if (two) {
-                        const uint32_t b1 = b + 256 * 128;
-                        const uint64_t b1_hi = desc_sw128(b1 + 32 * kk), b1_lo = desc_sw128(b1 + 64 + 32 * kk);
-                        mma_tf32(tmem + 256, a_hi, b1_hi, kIdesc, acc0);
-                        mma_tf32(tmem + 256, a_hi, b1_lo, kIdesc, 1u);
-                        mma_tf32(tmem + 256, a_lo, b1_hi, kIdesc, 1u);
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint32_t acc0 = (s > 0 || kk > 0) ? 1u : 0u;
+                        const uint64_t a_hi = desc_sw128(a + 32 * kk), a_lo = desc_sw128(a + 64 + 32 * kk);
+                        const uint64_t b0_hi = desc_sw128(b + 32 * kk), b0_lo = desc_sw128(b + 64 + 32 * kk);
+                        mma_tf32(tmem, a_hi, b0_hi, kIdesc, acc0);
+                        if (prec == FM_PREC_FP32) {
+                            mma_tf32(tmem, a_hi, b0_lo, kIdesc, 1u);
+                            mma_tf32(tmem, a_lo, b0_hi, kIdesc, 1u);
+                        }
+                        if (two) {
+                            const uint32_t b1 = b + 256 * 128;
+                            const uint64_t b1_hi = desc_sw128(b1 + 32 * kk), b1_lo = desc_sw128(b1 + 64 + 32 * kk);
+                            mma_tf32(tmem + 256, a_hi, b1_hi, kIdesc, acc0);
+                            if (prec == FM_PREC_FP32) {
+                                mma_tf32(tmem + 256, a_hi, b1_lo, kIdesc, 1u);
+                                mma_tf32(tmem + 256, a_lo, b1_hi, kIdesc, 1u);
+                            }
+                        }
                     }
                 }
                 mma_commit(&empty[slot]);
@@ -173,6 +191,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int slot = s % kNStages;
             if (!mbar_wait(&empty[slot], ((uint32_t)(s / kNStages) & 1u) ^ 1u, abort_flag)) break;
             char* arow = reinterpret_cast<char*>(base + slot * kStage);
+            if (prec == FM_PREC_BF16) {  // 16 BF16 values (8 antennas) in the row's first 32 bytes
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int m0 = 8 * s + 2 * c;
+                    const float2 a0 = (i < L && m0 < M) ? steer_exact(m0, qq.x, qq.y) : make_float2(0.f, 0.f);
+                    const float2 a1 = (i < L && m0 + 1 < M) ? steer_exact(m0 + 1, qq.x, qq.y) : make_float2(0.f, 0.f);
+                    *reinterpret_cast<uint2*>(arow + swz(r, c >> 1) + 8 * (c & 1)) =
+                        make_uint2(bf16x2_rn(a0.x, a0.y), bf16x2_rn(a1.x, a1.y));
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&a_full[slot]);
+                continue;
+            }
 #pragma unroll
             for (int c = 0; c < 4; ++c) {  // chunk c: antennas 8s + 2c, 8s + 2c + 1
                 uint4 hi, lo;
@@ -191,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 lo.z = w[0];
                 lo.w = w[1];
                 *reinterpret_cast<uint4*>(arow + swz(r, c)) = hi;
-                *reinterpret_cast<uint4*>(arow + swz(r, 4 + c)) = lo;
+                if (prec == FM_PREC_FP32) *reinterpret_cast<uint4*>(arow + swz(r, 4 + c)) = lo;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(&a_full[slot]);
@@ -266,14 +297,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <int NCP>
-cudaError_t launch_ncp(const FrameDesc* d, int n_frames, const void* tmB, int M, int Mp, int L, cudaStream_t s) {
+cudaError_t launch_ncp(const FrameDesc* d, int n_frames, const void* tmB, int M, int Mp, int L, int prec,
+                       cudaStream_t s) {
     cudaError_t e =
         cudaFuncSetAttribute(scan_tc_kernel<NCP>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     const int fpc = kRowsB / (2 * NCP);
     dim3 grid((L + kRowsA - 1) / kRowsA, (n_frames + fpc - 1) / fpc);
     scan_tc_kernel<NCP><<<grid, kThreads, kSmemBytes, s>>>(d, n_frames, reinterpret_cast<const CUtensorMap*>(tmB),
-                                                           M, Mp, L);
+                                                           M, Mp, L, prec);
     return cudaGetLastError();
 }
 
@@ -285,20 +317,20 @@ int scan_tc_ncp(int ncols) {
     return p;
 }
 
-cudaError_t launch_scan_tc(const FrameDesc* d, int n_frames, int M, int ncols, int L, float* bprep, const void* tmB,
-                           cudaStream_t s) {
+cudaError_t launch_scan_tc(const FrameDesc* d, int n_frames, int M, int ncols, int L, int prec, float* bprep,
+                           const void* tmB, cudaStream_t s) {
     const int ncp = scan_tc_ncp(ncols);
     const int Mp = (M + 7) / 8 * 8;
     const int64_t total = (int64_t)n_frames * ncp * Mp;
-    scan_bprep_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(d, n_frames, M, Mp, ncp, bprep);
+    scan_bprep_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(d, n_frames, M, Mp, ncp, prec, bprep);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     switch (ncp) {
-        case 1: return launch_ncp<1>(d, n_frames, tmB, M, Mp, L, s);
-        case 2: return launch_ncp<2>(d, n_frames, tmB, M, Mp, L, s);
-        case 4: return launch_ncp<4>(d, n_frames, tmB, M, Mp, L, s);
-        case 8: return launch_ncp<8>(d, n_frames, tmB, M, Mp, L, s);
-        default: return launch_ncp<16>(d, n_frames, tmB, M, Mp, L, s);
+        case 1: return launch_ncp<1>(d, n_frames, tmB, M, Mp, L, prec, s);
+        case 2: return launch_ncp<2>(d, n_frames, tmB, M, Mp, L, prec, s);
+        case 4: return launch_ncp<4>(d, n_frames, tmB, M, Mp, L, prec, s);
+        case 8: return launch_ncp<8>(d, n_frames, tmB, M, Mp, L, prec, s);
+        default: return launch_ncp<16>(d, n_frames, tmB, M, Mp, L, prec, s);
     }
 }
 

@@ -757,7 +757,8 @@ __global__ void __launch_bounds__(kThreads) small_cluster_kernel(const FrameDesc
     const int nc = (int)cl.num_blocks();
     const int rank = (int)cl.block_rank();
     const FrameDesc* dp = descs + blockIdx.x / nc;
-    if (mode == kOrth && dp->t < pass) return;  // uniform over the cluster
+    // pass < 0: the orth that precedes the FP32 refinement step (frames with refine only)
+    if (mode == kOrth && (pass < 0 ? !dp->refine : dp->t < pass)) return;  // uniform over the cluster
     const int M = dp->M, l = dp->l;
     const int Mr = (M + nc - 1) / nc;
     const int r0 = min(M, rank * Mr);
@@ -775,7 +776,9 @@ __global__ void __launch_bounds__(kThreads) small_cluster_kernel(const FrameDesc
     }
 
     // H = P^H C  (core matrix, Eq. 8 / Alg. 2 line 7)
-    const bool sampled0 = (dp->method == FM_RAND_SAMPLING && dp->t == 0);
+    // sampling without power steps: H = C(I, :) (Alg. 1); after a refinement step the
+    // sketch is V-based as in Alg. 2, so H = V^H C
+    const bool sampled0 = (dp->method == FM_RAND_SAMPLING && dp->t == 0 && !dp->refine);
     if (!sampled0) {
         load_rows(dp->V, sm.Vs, r0, rows, l);
         __syncthreads();
