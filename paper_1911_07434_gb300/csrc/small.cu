@@ -670,6 +670,151 @@ __device__ int jacobi(float2* A, float2* Z, float* w, int* perm, int n, const Sm
     return sweeps;
 }
 
+// Eigen-decomposition of B = F F^H through the singular value decomposition of
+// F (n x n, row-major in Frm) by one-sided (Hestenes) Jacobi in FP32: column
+// pairs (p, q) of F are rotated until every pair is orthogonal to the relative
+// tolerance, F <- F J with J the 2 x 2 unitary that diagonalises the pair's Gram
+// matrix [[a, g], [g*, b]] (a = |f_p|^2, b = |f_q|^2, g = f_p^H f_q).  The columns
+// of the converged F are then sigma_k u_k with B u_k = sigma_k^2 u_k.  Pairs follow
+// the same round-robin order as the two-sided solver; within a round the pairs
+// touch disjoint columns, so warp w handles pairs w, w + 8, w + 16 together (lanes
+// over the rows, one block barrier per round).  The column norms are recomputed
+// at the start of every sweep and updated by each rotation (a - t|g|, b + t|g|),
+// so a pair costs one reduced inner product.  Working copy column-major in Wc;
+// eigenvectors (row-major, Z[i n + k]) into Z, eigenvalues into w, and perm
+// orders them descending.  Returns the sweeps used, -1 without convergence.
+__device__ int eig_onesided(const float2* Frm, float2* Wc, float2* Z, float* w, int* perm, int n, const Sm& sm) {
+    const int ne = n + (n & 1), np = ne / 2, nr = ne - 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kPW = 3;  // pairs per warp: np <= 24 = 3 x kWarps
+    for (int e = threadIdx.x; e < n * n; e += kThreads) {
+        const int i = e / n, p = e % n;
+        Wc[p * n + i] = Frm[e];
+    }
+    for (int e = threadIdx.x; e < kMaxSweeps; e += kThreads) sm.flags[e] = 0;
+    __syncthreads();
+    const float tol2 = kJacobiTol * kJacobiTol;
+    int sweeps = -1;
+    for (int sweep = 0; sweep < kMaxSweeps && nr > 0; ++sweep) {
+        for (int k = warp; k < n; k += kWarps) {  // exact column norms for this sweep
+            float a = 0.f;
+            for (int i = lane; i < n; i += 32) a = fmaf(Wc[k * n + i].x, Wc[k * n + i].x, fmaf(Wc[k * n + i].y, Wc[k * n + i].y, a));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) w[k] = a;
+        }
+        // round-robin positions, advanced by one each round
+        int ia[kPW], ib[kPW];
+#pragma unroll
+        for (int j = 0; j < kPW; ++j) {
+            const int k = warp + kWarps * j;
+            ia[j] = (k == 0 || nr == 0) ? 0 : (k - 1) % nr;
+            ib[j] = nr ? (ne - 2 - k + nr) % nr : 0;
+        }
+        __syncthreads();
+        for (int r = 0; r < nr; ++r) {
+            float2* fp[kPW];
+            float2* fq[kPW];
+            float2 xp[kPW][2], xq[kPW][2];
+            float g[kPW][2], na[kPW], nb[kPW];
+            int pi[kPW], qi[kPW];
+            bool live[kPW];
+#pragma unroll
+            for (int j = 0; j < kPW; ++j) {
+                const int k = warp + kWarps * j;
+                const int pa = (k == 0) ? 0 : 1 + ia[j];
+                const int pb = 1 + ib[j];
+                const int p = min(pa, pb), q = max(pa, pb);
+                live[j] = k < np && q < n;  // q == n: the dummy column of an odd n
+                pi[j] = live[j] ? p : 0;
+                qi[j] = live[j] ? q : 0;
+                fp[j] = Wc + pi[j] * n;
+                fq[j] = Wc + qi[j] * n;
+                na[j] = live[j] ? w[p] : 1.f;
+                nb[j] = live[j] ? w[q] : 1.f;
+                float gr = 0.f, gi = 0.f;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int i = lane + 32 * h;
+                    xp[j][h] = (live[j] && i < n) ? fp[j][i] : make_float2(0.f, 0.f);
+                    xq[j][h] = (live[j] && i < n) ? fq[j][i] : make_float2(0.f, 0.f);
+                    gr = fmaf(xp[j][h].x, xq[j][h].x, fmaf(xp[j][h].y, xq[j][h].y, gr));  // conj(f_p) f_q
+                    gi = fmaf(xp[j][h].x, xq[j][h].y, fmaf(-xp[j][h].y, xq[j][h].x, gi));
+                }
+                g[j][0] = gr;
+                g[j][1] = gi;
+                if (++ia[j] == nr) ia[j] = 0;
+                if (++ib[j] == nr) ib[j] = 0;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int j = 0; j < kPW; ++j) {
+                    g[j][0] += __shfl_xor_sync(0xffffffffu, g[j][0], o);
+                    g[j][1] += __shfl_xor_sync(0xffffffffu, g[j][1], o);
+                }
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < kPW; ++j) {
+                const float gr = g[j][0], gi = g[j][1];
+                const float mag2 = fmaf(gr, gr, gi * gi);
+                const bool rot = live[j] && mag2 > FLT_MIN && mag2 > tol2 * na[j] * nb[j];  // warp-uniform
+                const float inv = rsqrtf(fmaxf(mag2, FLT_MIN));
+                const float mag = mag2 * inv;
+                const float tau = 0.5f * (nb[j] - na[j]) * inv;
+                // smaller root of t^2 + 2 tau t - 1 = 0 (t -> 0 as |tau| -> inf)
+                const float t = copysignf(__fdividef(1.f, fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f))), tau);
+                const float c = rsqrtf(fmaf(t, t, 1.f)), sn = t * c;
+                // F <- F U, U = [[c, s], [-s conj(ph), c conj(ph)]], ph = g / |g|
+                const float2 phc = make_float2(gr * inv, -gi * inv);
+                const float2 u10 = cscale(phc, -sn), u11 = cscale(phc, c);
+                if (rot) {
+                    any = true;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int i = lane + 32 * h;
+                        if (i < n) {
+                            fp[j][i] = cadd(cscale(xp[j][h], c), cmul(xq[j][h], u10));
+                            fq[j][i] = cadd(cscale(xp[j][h], sn), cmul(xq[j][h], u11));
+                        }
+                    }
+                    if (lane == 0) {
+                        w[pi[j]] = na[j] - t * mag;
+                        w[qi[j]] = nb[j] + t * mag;
+                    }
+                }
+            }
+            if (any && lane == 0) sm.flags[sweep] = 1;
+            __syncthreads();
+        }
+        if (!sm.flags[sweep]) {
+            sweeps = sweep;
+            break;
+        }
+    }
+    if (nr == 0) sweeps = 0;
+    // eigenvalues |f_k|^2, eigenvectors f_k / |f_k| (row-major into Z)
+    for (int k = warp; k < n; k += kWarps) {
+        float a = 0.f;
+        for (int i = lane; i < n; i += 32) a = fmaf(Wc[k * n + i].x, Wc[k * n + i].x, fmaf(Wc[k * n + i].y, Wc[k * n + i].y, a));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        const float inv = (a > 0.f) ? rsqrtf(a) : 0.f;
+        for (int i = lane; i < n; i += 32) Z[i * n + k] = cscale(Wc[k * n + i], inv);
+        __syncwarp();
+        if (lane == 0) w[k] = a;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kThreads) {
+        int rank = 0;
+        const float wi = w[i];
+        for (int j = 0; j < n; ++j) rank += (w[j] > wi) || (w[j] == wi && j < i);
+        perm[rank] = i;
+    }
+    __syncthreads();
+    return sweeps;
+}
+
 // One Rayleigh-Ritz correction of the leading ncols-dimensional eigenspace of B
 // (in T) after the FP32 Jacobi: with Z0 the FP32 eigenvectors (columns ordered by
 // perm), B' = Z0^H B Z0 is formed for the (other x leading) block with products
@@ -863,10 +1008,19 @@ __global__ void __launch_bounds__(kThreads) small_cluster_kernel(const FrameDesc
         }
         __syncthreads();
     }
-    // eig(B) = U_B L_B U_B^H in FP32 (B kept in T for the refinement below)
-    for (int e = threadIdx.x; e < l * l; e += kThreads) sm.T[e] = sm.H[e];
-    __syncthreads();
-    const int s2 = jacobi(sm.H, sm.Z, sm.w, sm.perm, l, sm);
+    // eig(B) = U_B L_B U_B^H in FP32 (B kept in T for the refinement below): with
+    // B = F F^H (F in T) through the one-sided Jacobi SVD of F, else two-sided
+    // Jacobi on B
+    int s2;
+    if (pd) {
+        s2 = eig_onesided(sm.T, sm.Xf, sm.Z, sm.w, sm.perm, l, sm);  // Xf is free after F was formed
+        for (int e = threadIdx.x; e < l * l; e += kThreads) sm.T[e] = sm.H[e];
+        __syncthreads();
+    } else {
+        for (int e = threadIdx.x; e < l * l; e += kThreads) sm.T[e] = sm.H[e];
+        __syncthreads();
+        s2 = jacobi(sm.H, sm.Z, sm.w, sm.perm, l, sm);
+    }
     const int nc_out = dp->ncols;
     refine_subspace(sm, l, nc_out);
     orthonormalize_cols_d(sm.Rc, l, nc_out, sm);
