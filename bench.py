@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=3, help="frames of the workload the oracle times")
     ap.add_argument("--serve-requests", type=int, default=4000, help="requests of the timed serving run (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=20000.0, help="Poisson arrival rate of the serving run")
+    ap.add_argument("--uneven-frames", type=int, default=4096, help="frames of the uneven-batch run (0: skip)")
     return ap.parse_args()
 
 
@@ -294,6 +295,70 @@ def serving_run(binding, synth, dev, n_req, rate, budget_gb=40, pool_per_profile
             "latency": "observed completion - scheduled Poisson arrival (host clock, polled)"}
 
 
+def uneven_run(binding, synth, dev, n_frames=4096, pool=256, steps=3, seed=0):
+    """Uneven batch: n_frames frames (M in {128, 192, 256, 384, 512}, T log-uniform in
+    [64, 2048], K in [1, 12], l = K + 12, t = 1, 0.05 deg grid over +-75 deg) in one fm_run,
+    timed plainly, as a replayed CUDA graph, and after the path autotuner.  `pool` distinct
+    frames are drawn and copied into n_frames separate device buffers."""
+    import numpy as np
+    import torch
+    wl = synth.uneven_frames(pool, seed=seed)
+    frames, bufs = [], []
+    for i in range(n_frames):
+        fr = wl.frames[i % pool]
+        X = torch.from_numpy(np.ascontiguousarray(fr.X)).to(dev)
+        P = torch.empty(fr.L, dtype=torch.float32, device=dev)
+        idx = torch.empty(fr.K, dtype=torch.int32, device=dev)
+        deg = torch.empty(fr.K, dtype=torch.float32, device=dev)
+        npk = torch.empty(1, dtype=torch.int32, device=dev)
+        st = torch.zeros(1, dtype=torch.int32, device=dev)
+        bufs.append((X, P, idx, deg, npk, st))
+        frames.append(binding.Context.frame(X, fr.K, fr.l, fr.t, binding.FM_RAND_PROJECTION, fr.theta0, fr.step,
+                                            fr.L, P, idx, deg, npk, seed=1, frame_id=i, status=st))
+    ctx = binding.Context(device=dev.index or 0)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, (time.perf_counter() - t0) * 1e3 / steps
+
+    run_ms, run_wall = timed(lambda: ctx.run(frames))
+    l0 = ctx.launch_count()
+    ctx.stage_times(reset=True)
+    ctx.set_timing(True)
+    ctx.run(frames)
+    ctx.set_timing(False)
+    stg = ctx.stage_times(reset=True)
+    per_run = ctx.launch_count() - l0
+    cov, scan, tuned_ms = ctx.autotune(frames, reps=2)
+    run2_ms, _ = timed(lambda: ctx.run(frames))
+    t0 = time.perf_counter()
+    g = ctx.graph(frames)
+    create_s = time.perf_counter() - t0
+    graph_ms, graph_wall = timed(g.launch)
+    g.close()
+    bad = sum(int(b[5].abs().sum().item()) != 0 for b in bufs)
+    ctx.close()
+    names = {binding.FM_COV_TC: "tensor", binding.FM_COV_SIMT: "cuda-core"}
+    return {"frames": n_frames, "distinct_frames": pool, "gpu_launches_per_step": int(per_run),
+            "stage_ms": {k: round(v[0], 4) for k, v in stg.items() if v[1]},
+            "fm_run": {"frames_per_s": n_frames / (run_ms / 1e3), "ms_per_step": run_ms,
+                       "host_wall_ms_per_step": run_wall},
+            "autotuned": {"covariance": names.get(cov), "scan": names.get(scan),
+                          "frames_per_s": n_frames / (run2_ms / 1e3), "ms_per_step": run2_ms},
+            "cuda_graph": {"frames_per_s": n_frames / (graph_ms / 1e3), "ms_per_step": graph_ms,
+                           "host_wall_ms_per_step": graph_wall, "create_s": create_s},
+            "frames_with_nonzero_status": bad}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -447,6 +512,11 @@ def main():
     if args.serve_requests > 0:
         serving = serving_run(binding, synth, dev, args.serve_requests, args.serve_rate)
 
+    # ---- uneven batch: one fm_run, CUDA graph replay, autotuned paths -----------
+    uneven = None
+    if args.uneven_frames > 0:
+        uneven = uneven_run(binding, synth, dev, args.uneven_frames)
+
     # ---- CPU oracle baseline -----------------------------------------------------
     cpu = None
     if not args.no_baseline and rank == 0:
@@ -468,7 +538,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": roof, "dominant_stage": dom, "stages": stage_summary,
-        "serving": serving, "full_eig_music": full, "cpu_baseline": cpu, "clocks": clk,
+        "serving": serving, "uneven_batch": uneven, "full_eig_music": full, "cpu_baseline": cpu, "clocks": clk,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -153,6 +153,34 @@ size_t fm_workspace_bytes(const fm_frame* frames, int n_frames);
  * method must be FM_RAND_SAMPLING or FM_RAND_PROJECTION. */
 fm_status fm_run(fm_ctx* ctx, const fm_frame* frames, int n_frames, fm_stream stream);
 
+/* ---- autotuning -------------------------------------------------------------------
+ * fm_autotune: run fm_run on these frames with every combination of covariance
+ * path and scan path (FM_COV_TC / FM_COV_SIMT each) that they can take, `reps`
+ * timed runs each after one untimed run (CUDA events on `stream`; synchronises
+ * the stream), and keep the fastest combination in the context (as
+ * fm_set_cov_path / fm_set_scan_path would).  Reports the choice and its mean
+ * milliseconds per fm_run (pointers nullable).  The frames' outputs hold the
+ * last run's results. */
+fm_status fm_autotune(fm_ctx* ctx, const fm_frame* frames, int n_frames, fm_stream stream, int reps, int* cov_path,
+                      int* scan_path, float* best_ms);
+
+/* ---- CUDA graphs ----------------------------------------------------------------
+ * fm_graph_create: prepare fm_run's work for these frames once (validation,
+ * workspace of its own within the context's budget, descriptors, tensor maps)
+ * and capture the chain's kernel launches into a CUDA graph.  The frame
+ * pointers are baked in: each fm_graph_launch runs the whole chain again on the
+ * current contents of the same X buffers and writes the same output buffers, so
+ * a caller that streams frames refills the X buffers between launches.  One
+ * plain run of the chain happens inside fm_graph_create (on a private stream,
+ * completed before it returns).  fm_graph_launch is asynchronous on `stream`
+ * and adds one graph launch; launches of one graph must not overlap each other
+ * (they share its workspace).  fm_graph_destroy waits for the device and frees
+ * the graph. */
+typedef struct fm_graph fm_graph;
+fm_status fm_graph_create(fm_ctx* ctx, const fm_frame* frames, int n_frames, fm_graph** graph);
+fm_status fm_graph_launch(fm_graph* graph, fm_stream stream);
+fm_status fm_graph_destroy(fm_graph* graph);
+
 /* fm_run_subspace: copy U_s (complex64 M x ncols, row-major) of frame `frame` of
  * the most recent fm_run on this context into U (device), asynchronously on
  * `stream`.  The copy reads the context's workspace, so it must be issued before
@@ -218,14 +246,19 @@ fm_status fm_set_cov_path(fm_ctx* ctx, int path);
 int fm_last_cov_path(const fm_ctx* ctx);
 
 /* ---- scan kernel selection (same constants) -------------------------------------
- * FM_COV_AUTO (default): inside fm_run, frames that share M, the number of U_s
- * columns and the angle grid are scanned by one batched tensor-core kernel (the
- * steering tile generated in registers serves every frame; tcgen05 MMAs, 3 TF32
- * products per FP32 product); the angles of the main lobes (||U_s^H a||^2 above
- * 4 times the number of U_s columns, where M - ||U_s^H a||^2 cancels) are then
- * recomputed by the FP32 CUDA-core scan.
- * Other batches use the FP32 CUDA-core scan.  fm_spectrum always uses the
- * CUDA-core scan. */
+ * Inside fm_run the frames are grouped by (M, number of U_s columns, angle
+ * grid, prec).  A group on the tensor cores is scanned by one batched launch
+ * (the steering tile generated in registers serves every frame of the group;
+ * tcgen05 MMAs, 3 TF32 products per FP32 product in FP32 mode), after which the
+ * angles of the main lobes (||U_s^H a||^2 above 4 times the number of U_s
+ * columns, where M - ||U_s^H a||^2 cancels) are recomputed by the FP32
+ * CUDA-core scan.  FM_COV_AUTO (default): the tensor cores take the groups
+ * whose frames fill at least a quarter of the kernel's B tile (frames >=
+ * 64 / ncols rounded up to a power of two), the CUDA-core scan the rest;
+ * FM_COV_TC: every group on the tensor cores; FM_COV_SIMT: the CUDA-core scan
+ * for every frame.  fm_last_scan_path reports FM_COV_TC or FM_COV_SIMT when
+ * all frames of the last fm_run took that path, FM_COV_AUTO when both ran.
+ * fm_spectrum always uses the CUDA-core scan. */
 fm_status fm_set_scan_path(fm_ctx* ctx, int path);
 int fm_last_scan_path(const fm_ctx* ctx);
 
@@ -263,9 +296,9 @@ fm_status fm_spectrum_noalloc(const void* U, int n_frames, int M, int ncols, dou
  * fm_serve_poll sets *done = 1 once the frame's outputs are complete on the
  * device (FM_ERR_CUDA with *done = 1 if its batch failed; FM_ERR_NOT_READY for
  * an unknown ticket).  The caller's X and output buffers must stay valid until
- * then.  A frame's result does not depend on its batch beyond the scan path:
- * the tensor-core scan (a batch sharing M, U_s columns and grid) and the
- * CUDA-core scan agree within the scan tolerance. */
+ * then.  A frame's result does not depend on its batch beyond rounding: the
+ * scan groups of a batch, hence the order of the tensor-core accumulation,
+ * depend on the batch, within the scan tolerance. */
 fm_status fm_serve_submit(fm_ctx* ctx, const fm_frame* frame, uint64_t* ticket);
 fm_status fm_serve_poll(fm_ctx* ctx, uint64_t ticket, int* done);
 

@@ -12,7 +12,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, byref, c_double, c_int, c_int64, c_size_t, c_uint64, c_void_p
+from ctypes import POINTER, byref, c_double, c_float, c_int, c_int64, c_size_t, c_uint64, c_void_p
 
 from . import build as _build
 
@@ -75,6 +75,11 @@ _SIGS = {
     "fm_stage_times": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int), c_int]),
     "fm_launch_count": (c_uint64, [c_void_p]),
     "fm_run_subspace": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "fm_autotune": (c_int, [c_void_p, POINTER(FmFrame), c_int, c_void_p, c_int, POINTER(c_int), POINTER(c_int),
+                            POINTER(c_float)]),
+    "fm_graph_create": (c_int, [c_void_p, POINTER(FmFrame), c_int, POINTER(c_void_p)]),
+    "fm_graph_launch": (c_int, [c_void_p, c_void_p]),
+    "fm_graph_destroy": (c_int, [c_void_p]),
     "fm_set_cov_path": (c_int, [c_void_p, c_int]),
     "fm_last_cov_path": (c_int, [c_void_p]),
     "fm_set_scan_path": (c_int, [c_void_p, c_int]),
@@ -171,6 +176,28 @@ def fm_stage_times(ctx, reset=False):
     n = (c_int * FM_N_STAGES)()
     st = load().fm_stage_times(ctx, ms, n, int(reset))
     return st, list(ms), list(n)
+
+
+def fm_autotune(ctx, frames, stream, reps):
+    arr = (FmFrame * len(frames))(*frames)
+    cp, sp, ms = c_int(), c_int(), c_float()
+    st = load().fm_autotune(ctx, arr, len(frames), stream, reps, byref(cp), byref(sp), byref(ms))
+    return st, cp.value, sp.value, ms.value
+
+
+def fm_graph_create(ctx, frames):
+    arr = (FmFrame * len(frames))(*frames)
+    g = c_void_p()
+    st = load().fm_graph_create(ctx, arr, len(frames), byref(g))
+    return st, g.value
+
+
+def fm_graph_launch(graph, stream) -> int:
+    return load().fm_graph_launch(graph, stream)
+
+
+def fm_graph_destroy(graph) -> int:
+    return load().fm_graph_destroy(graph)
 
 
 def fm_run_subspace(ctx, frame, U, stream) -> int:
@@ -272,6 +299,18 @@ class Context:
     def run(self, frames, stream=None):
         self._check(fm_run(self.h, frames, _stream_handle(stream)), "fm_run")
 
+    def autotune(self, frames, reps=3, stream=None):
+        """Pick the fastest covariance / scan paths for these frames; returns (cov, scan, ms)."""
+        st, cp, sp, ms = fm_autotune(self.h, frames, _stream_handle(stream), reps)
+        self._check(st, "fm_autotune")
+        return cp, sp, ms
+
+    def graph(self, frames):
+        """CUDA graph of the whole chain for these frames (see fm_graph_create)."""
+        st, g = fm_graph_create(self.h, frames)
+        self._check(st, "fm_graph_create")
+        return Graph(self, g)
+
     def run_subspace(self, frame: int, M: int, ncols: int, stream=None):
         """U_s (M x ncols complex64) of frame `frame` of the last run() on this context."""
         import torch
@@ -370,3 +409,25 @@ class Context:
         st, d = fm_serve_poll(self.h, ticket)
         self._check(st, "fm_serve_poll")
         return bool(d)
+
+
+class Graph:
+    """A captured fm_run chain; launch() re-runs it on the frames' current inputs."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.h = handle
+
+    def launch(self, stream=None):
+        self.ctx._check(fm_graph_launch(self.h, _stream_handle(stream)), "fm_graph_launch")
+
+    def close(self):
+        if self.h:
+            fm_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kThreads, 2) cov_fp32_kernel(const FrameDesc* 
 cudaError_t launch_covariance(const FrameDesc* d, int n_frames, int max_M, cudaStream_t s) {
     const int nt = (max_M + kTile - 1) / kTile;
     dim3 grid(nt * (nt + 1) / 2, n_frames);
+    count_launch();
     cov_fp32_kernel<<<grid, kThreads, kSmemBytes, s>>>(d);
     return cudaGetLastError();
 }

@@ -273,6 +273,7 @@ cudaError_t launch_covariance_tc(const FrameDesc* d, const void* tmaps, int n_fr
     if (e != cudaSuccess) return e;
     const int nt = (max_M + kTile - 1) / kTile;
     dim3 grid(nt * (nt + 1) / 2, n_frames);
+    count_launch();
     cov_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(d, reinterpret_cast<const CUtensorMap*>(tmaps));
     return cudaGetLastError();
 }

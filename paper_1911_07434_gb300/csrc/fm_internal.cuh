@@ -20,7 +20,7 @@ struct FrameDesc {
     int kpad;          // padded column count of Us (multiple of 4)
     int prec;          // fm_precision of the covariance and scan GEMMs
     int refine;        // 1: one more power step C = X (X^H V) / T in FP32 before the final solve
-    int pad_;
+    int scan_tc;       // 1: scanned by the tensor-core kernel (then main lobes by the fixup scan)
     float2* R;         // M x M
     float2* C;         // M x l  sketch
     float2* V;         // M x l  basis (power steps) / Q
@@ -161,6 +161,11 @@ __device__ __forceinline__ void set_status(int* status, int code) {
 }
 
 // ---------------------------------------------------------- launch wrappers --
+// Kernel launches issued by the calling host thread (every launch site bumps it),
+// so the host side can report exactly how many kernels a call launched.
+extern thread_local uint64_t g_kernel_launches;
+inline void count_launch() { ++g_kernel_launches; }
+
 // Implemented in the .cu files; each returns cudaGetLastError() after launching.
 cudaError_t launch_grid_table(const GridDesc* g, int n_grids, int max_L, const FrameDesc* d, int n_frames,
                               cudaStream_t s);

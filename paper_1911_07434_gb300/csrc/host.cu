@@ -116,9 +116,10 @@ fm_status stage(fm_ctx* c, int st, cudaStream_t s, F&& launch) {
         b = get_event(c);
         cudaEventRecord(a, s);
     }
+    const uint64_t k0 = fm::g_kernel_launches;
     cudaError_t e = launch();
+    c->launches += fm::g_kernel_launches - k0;
     if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
-    c->launches++;
     if (c->timing) {
         cudaEventRecord(b, s);
         c->pending.push_back({st, a, b});
@@ -235,9 +236,13 @@ const char* check_frame(const fm_frame& f) {
 
 struct Plan {
     size_t desc_off, tmap_off, grid_off, total;
-    bool scan_uniform = false;  // all frames share M, ncols and one grid: batched tensor-core scan possible
-    int scan_M = 0, scan_nc = 0, scan_L = 0, scan_prec = 0;
-    size_t bprep_off = 0, bprep_rows = 0, bprep_rowlen = 0;
+    // tensor-core scan groups: maximal runs of consecutive frames sharing M, ncols,
+    // grid and prec (fm_run orders the frames so that each group is one run)
+    struct ScanGroup {
+        int f0, nf, M, nc, L, prec;
+        size_t bprep_off, rows, rowlen;
+    };
+    std::vector<ScanGroup> scan_groups;
     std::vector<size_t> R, C, V, Us, idx, Y;  // per-frame offsets (R == SIZE_MAX: caller-owned)
     std::vector<int> grid_of;
     std::vector<GridDesc> grids;
@@ -252,8 +257,8 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
     size_t off = 0;
     pl.desc_off = off;
     off = aup(off + sizeof(FrameDesc) * (size_t)n);
-    pl.tmap_off = off;  // TMA tensor maps: one per frame's X (covariance), then one for the scan's B
-    if (need_R) off = aup(off + sizeof(CUtensorMap) * ((size_t)n + 1));
+    pl.tmap_off = off;  // TMA tensor maps: one per frame's X (covariance), then one per scan group's B
+    if (need_R) off = aup(off + sizeof(CUtensorMap) * (2 * (size_t)n));
     std::map<GridKey, int> gmap;
     pl.grid_of.assign(n, -1);
     if (need_grid) {
@@ -300,21 +305,24 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
         if (need_Us) off = aup(off + sizeof(float2) * M * nc);
     }
     if (need_R && need_Us && need_grid) {
-        // batched tensor-core scan: one B operand row pair per (frame, column of U_s)
-        bool uni = pl.grids.size() == 1;
-        const int M0 = f[0].arr.M, nc0 = ncols_of(f[0].p), pr0 = f[0].p.prec;
-        for (int b = 1; uni && b < n; ++b) uni = f[b].arr.M == M0 && ncols_of(f[b].p) == nc0 && f[b].p.prec == pr0;
-        if (uni) {
-            pl.scan_uniform = true;
-            pl.scan_M = M0;
-            pl.scan_nc = nc0;
-            pl.scan_L = pl.grids[0].L;
-            pl.scan_prec = pr0;
+        for (int b = 0; b < n;) {
+            const int M0 = f[b].arr.M, nc0 = ncols_of(f[b].p), pr0 = f[b].p.prec, g0 = pl.grid_of[b];
+            int e = b + 1;
+            while (e < n && f[e].arr.M == M0 && ncols_of(f[e].p) == nc0 && f[e].p.prec == pr0 && pl.grid_of[e] == g0) ++e;
+            Plan::ScanGroup sg{};
+            sg.f0 = b;
+            sg.nf = e - b;
+            sg.M = M0;
+            sg.nc = nc0;
+            sg.L = pl.grids[g0].L;
+            sg.prec = pr0;
             const int ncp = fm::scan_tc_ncp(nc0), Mp = (M0 + 7) / 8 * 8;
-            pl.bprep_rows = (size_t)n * 2 * ncp;
-            pl.bprep_rowlen = 4 * (size_t)Mp;
-            pl.bprep_off = off;
-            off = aup(off + sizeof(float) * pl.bprep_rows * pl.bprep_rowlen);
+            sg.rows = (size_t)sg.nf * 2 * ncp;  // one B operand row pair per (frame, column of U_s)
+            sg.rowlen = 4 * (size_t)Mp;
+            sg.bprep_off = off;
+            off = aup(off + sizeof(float) * sg.rows * sg.rowlen);
+            pl.scan_groups.push_back(sg);
+            b = e;
         }
     }
     pl.total = off;
@@ -449,14 +457,17 @@ fm_status launch_cov(fm_ctx* c, bool tc, FrameDesc* dd, const char* tm_dev, int 
 
 // Uploads descriptors (+ grids) and returns device pointers.
 fm_status upload_descs(fm_ctx* c, const Plan& pl, std::vector<FrameDesc>& ds, const std::vector<CUtensorMap>& maps,
-                       cudaStream_t s, FrameDesc** dd, GridDesc** dg, const CUtensorMap* extra_map = nullptr) {
+                       cudaStream_t s, FrameDesc** dd, GridDesc** dg,
+                       const std::vector<CUtensorMap>* group_maps = nullptr) {
     const size_t bytes = pl.grid_off + sizeof(GridDesc) * pl.grids.size();
     char* host = nullptr;
     fm_status st = staging(c, bytes, &host);
     if (st != FM_OK) return st;
     memcpy(host + pl.desc_off, ds.data(), sizeof(FrameDesc) * ds.size());
     if (!maps.empty()) memcpy(host + pl.tmap_off, maps.data(), sizeof(CUtensorMap) * maps.size());
-    if (extra_map) memcpy(host + pl.tmap_off + sizeof(CUtensorMap) * ds.size(), extra_map, sizeof(CUtensorMap));
+    if (group_maps && !group_maps->empty())
+        memcpy(host + pl.tmap_off + sizeof(CUtensorMap) * ds.size(), group_maps->data(),
+               sizeof(CUtensorMap) * group_maps->size());
     std::vector<GridDesc> g = pl.grids;
     for (size_t i = 0; i < g.size(); ++i) g[i].qtab = reinterpret_cast<float2*>(c->arena + pl.qtab[i]);
     if (!g.empty()) memcpy(host + pl.grid_off, g.data(), sizeof(GridDesc) * g.size());
@@ -551,6 +562,119 @@ size_t fm_workspace_bytes(const fm_frame* frames, int n) {
     return plan_frames(frames, n, true, true, true, true).total;
 }
 
+// ---- fm_run, split into host preparation and the device chain -----------------
+// Frames are processed in an order that puts the frames of each tensor-core
+// scan group (same M, ncols, grid, prec) next to each other; order[k] is the
+// caller's index of the k-th frame.
+struct RunPrep {
+    int n = 0;
+    Plan pl;
+    std::vector<int> order;
+    Maxes mx;
+    bool cov_tc = false, scan_tc = false, scan_simt = true;
+    std::vector<char> group_tc;  // per scan group: runs on the tensor cores
+    FrameDesc* dd = nullptr;
+    GridDesc* dg = nullptr;
+};
+
+static fm_status prepare_run(fm_ctx* c, const fm_frame* frames, int n, cudaStream_t s, RunPrep& rp) {
+    rp.n = n;
+    rp.order.resize(n);
+    for (int b = 0; b < n; ++b) rp.order[b] = b;
+    auto key = [&](int b) {
+        const fm_frame& f = frames[b];
+        const double d = f.arr.d_wl > 0.0 ? f.arr.d_wl : 0.5;
+        return std::make_tuple(f.arr.M, ncols_of(f.p), f.p.prec, f.grid.theta0_deg, f.grid.step_deg, d, f.grid.L);
+    };
+    std::stable_sort(rp.order.begin(), rp.order.end(), [&](int x, int y) { return key(x) < key(y); });
+    std::vector<fm_frame> sorted(n);
+    for (int k = 0; k < n; ++k) sorted[k] = frames[rp.order[k]];
+    rp.pl = plan_frames(sorted.data(), n, true, true, true, true);
+    const Plan& pl = rp.pl;
+    fm_status st = ensure_arena(c, pl.total);
+    if (st != FM_OK) return st;
+    std::vector<FrameDesc> ds(n);
+    c->last_us.assign(n, std::make_tuple(SIZE_MAX, 0, 0));
+    for (int k = 0; k < n; ++k) {
+        FrameDesc d = make_desc(sorted[k]);
+        d.R = reinterpret_cast<float2*>(c->arena + pl.R[k]);
+        d.C = reinterpret_cast<float2*>(c->arena + pl.C[k]);
+        d.V = reinterpret_cast<float2*>(c->arena + pl.V[k]);
+        d.idx = reinterpret_cast<int*>(c->arena + pl.idx[k]);
+        d.Us = reinterpret_cast<float2*>(c->arena + pl.Us[k]);
+        d.Y = pl.Y[k] != SIZE_MAX ? reinterpret_cast<float2*>(c->arena + pl.Y[k]) : nullptr;
+        c->last_us[rp.order[k]] = std::make_tuple(pl.Us[k], d.M, d.ncols);
+        d.qtab = reinterpret_cast<float2*>(c->arena + pl.qtab[pl.grid_of[k]]);
+        ds[k] = d;
+    }
+    std::vector<CUtensorMap> maps;
+    st = choose_cov_path(c, ds, maps, &rp.cov_tc);
+    if (st != FM_OK) return st;
+    // scan: one batched tensor-core launch per scan group that fills at least a
+    // quarter of the kernel's 512-row B tile (FM_COV_TC: every group), the CUDA-core
+    // scan for the other frames, then the CUDA-core main-lobe recompute of the
+    // tensor-core frames
+    std::vector<CUtensorMap> gmaps(pl.scan_groups.size());
+    rp.group_tc.assign(pl.scan_groups.size(), 0);
+    int n_tc = 0;
+    for (size_t g = 0; g < pl.scan_groups.size(); ++g) {
+        const Plan::ScanGroup& sg = pl.scan_groups[g];
+        const int fpc = 256 / fm::scan_tc_ncp(sg.nc);  // frames per CTA
+        bool use = c->scan_path == FM_COV_TC || (c->scan_path == FM_COV_AUTO && 4 * sg.nf >= fpc);
+        if (use) {
+            use = encode_bprep_tmap(reinterpret_cast<float*>(c->arena + sg.bprep_off), sg.rows, sg.rowlen, &gmaps[g]);
+            if (!use && c->scan_path == FM_COV_TC)
+                return fail(c, FM_ERR_INVALID_ARG, "tensor-core scan: tensor map encoding failed");
+        }
+        rp.group_tc[g] = use;
+        if (use) {
+            n_tc += sg.nf;
+            for (int k = sg.f0; k < sg.f0 + sg.nf; ++k) ds[k].scan_tc = 1;
+        }
+    }
+    rp.scan_tc = n_tc > 0;
+    rp.scan_simt = n_tc < n;
+    c->last_scan_path = n_tc == n ? FM_COV_TC : (n_tc == 0 ? FM_COV_SIMT : FM_COV_AUTO);
+    st = upload_descs(c, pl, ds, maps, s, &rp.dd, &rp.dg, rp.scan_tc ? &gmaps : nullptr);
+    if (st != FM_OK) return st;
+    rp.mx = maxes_of(ds);
+    return FM_OK;
+}
+
+static fm_status enqueue_run(fm_ctx* c, const RunPrep& rp, cudaStream_t s) {
+    const Plan& pl = rp.pl;
+    const Maxes& mx = rp.mx;
+    FrameDesc* dd = rp.dd;
+    const int n = rp.n, ng = (int)pl.grids.size();
+    fm_status st = stage(c, kStGrid, s, [&] { return fm::launch_grid_table(rp.dg, ng, mx.L, dd, n, s); });
+    if (st != FM_OK) return st;
+    st = launch_cov(c, rp.cov_tc, dd, c->arena + pl.tmap_off, n, mx.M, s);
+    if (st != FM_OK) return st;
+    st = run_subspace_chain(c, dd, n, mx, s);
+    if (st != FM_OK) return st;
+    st = stage(c, kStScan, s, [&] {
+        if (rp.scan_simt) {  // frames without a tensor-core group (the kernel skips the others)
+            cudaError_t e = fm::launch_scan(dd, n, mx.L, mx.M, mx.kpad, s);
+            if (e != cudaSuccess) return e;
+        }
+        if (rp.scan_tc) {
+            for (size_t g = 0; g < pl.scan_groups.size(); ++g) {
+                if (!rp.group_tc[g]) continue;
+                const Plan::ScanGroup& sg = pl.scan_groups[g];
+                float* bp = reinterpret_cast<float*>(c->arena + sg.bprep_off);
+                const char* bmap_dev = c->arena + pl.tmap_off + sizeof(CUtensorMap) * ((size_t)n + g);
+                cudaError_t e = fm::launch_scan_tc(dd + sg.f0, sg.nf, sg.M, sg.nc, sg.L, sg.prec, bp, bmap_dev, s);
+                if (e != cudaSuccess) return e;
+            }
+            // main-lobe angles again on the FP32 CUDA cores (see scan_kernel<..., FIXUP>)
+            return fm::launch_scan_fixup(dd, n, mx.L, mx.M, mx.kpad, s);
+        }
+        return cudaSuccess;
+    });
+    if (st != FM_OK) return st;
+    return stage(c, kStPeaks, s, [&] { return fm::launch_peaks(dd, n, mx.K, s); });
+}
+
 fm_status fm_run(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream) {
     if (!c) return FM_ERR_INVALID_ARG;
     if (!frames || n < 1) return fail(c, FM_ERR_INVALID_ARG, "no frames");
@@ -561,61 +685,151 @@ fm_status fm_run(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream) {
     fm_status st = set_device(c);
     if (st != FM_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    Plan pl = plan_frames(frames, n, true, true, true, true);
-    st = ensure_arena(c, pl.total);
+    RunPrep rp;
+    st = prepare_run(c, frames, n, s, rp);
     if (st != FM_OK) return st;
-    std::vector<FrameDesc> ds(n);
-    c->last_us.assign(n, std::make_tuple(SIZE_MAX, 0, 0));
+    return enqueue_run(c, rp, s);
+}
+
+// ---- autotuning of the kernel paths -------------------------------------------
+// Times fm_run on the caller's frames for every combination of covariance path
+// and scan path that these frames can take (tensor-core 128 x 256 tiles or
+// CUDA-core tiles), keeps the fastest in the context and reports it.
+fm_status fm_autotune(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream, int reps, int* cov_path,
+                      int* scan_path, float* best_ms) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (!frames || n < 1 || reps < 1) return fail(c, FM_ERR_INVALID_ARG, "fm_autotune: no frames or reps < 1");
+    fm_status st = set_device(c);
+    if (st != FM_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int saved_cov = c->cov_path, saved_scan = c->scan_path;
+    const bool saved_timing = c->timing;
+    c->timing = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = -1.f;
+    int bc = saved_cov, bs = saved_scan;
+    const int paths[2] = {FM_COV_TC, FM_COV_SIMT};
+    for (int cp : paths)
+        for (int sp : paths) {
+            c->cov_path = cp;
+            c->scan_path = sp;
+            if (fm_run(c, frames, n, stream) != FM_OK) continue;  // this path is not open to these frames
+            cudaEventRecord(e0, s);
+            bool ok = true;
+            for (int r = 0; r < reps && ok; ++r) ok = fm_run(c, frames, n, stream) == FM_OK;
+            cudaEventRecord(e1, s);
+            if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= (float)reps;
+            if (best < 0.f || ms < best) {
+                best = ms;
+                bc = cp;
+                bs = sp;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->timing = saved_timing;
+    c->cov_path = bc;
+    c->scan_path = bs;
+    if (best < 0.f) {
+        c->cov_path = saved_cov;
+        c->scan_path = saved_scan;
+        return fail(c, FM_ERR_INVALID_ARG, "fm_autotune: no path ran these frames");
+    }
+    c->err.clear();
+    if (cov_path) *cov_path = bc;
+    if (scan_path) *scan_path = bs;
+    if (best_ms) *best_ms = best;
+    return FM_OK;
+}
+
+// ---- CUDA graphs ------------------------------------------------------------
+// A graph owns a private context (its own workspace and descriptors, prepared
+// once) and the instantiated capture of the chain's kernel launches.
+struct fm_graph {
+    fm_ctx* parent = nullptr;
+    fm_ctx* sub = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t kernels = 0;  // kernel launches per graph launch
+};
+
+fm_status fm_graph_create(fm_ctx* c, const fm_frame* frames, int n, fm_graph** out) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (!out || !frames || n < 1) return fail(c, FM_ERR_INVALID_ARG, "fm_graph_create: no frames");
+    *out = nullptr;
     for (int b = 0; b < n; ++b) {
-        FrameDesc d = make_desc(frames[b]);
-        d.R = reinterpret_cast<float2*>(c->arena + pl.R[b]);
-        d.C = reinterpret_cast<float2*>(c->arena + pl.C[b]);
-        d.V = reinterpret_cast<float2*>(c->arena + pl.V[b]);
-        d.idx = reinterpret_cast<int*>(c->arena + pl.idx[b]);
-        d.Us = reinterpret_cast<float2*>(c->arena + pl.Us[b]);
-        d.Y = pl.Y[b] != SIZE_MAX ? reinterpret_cast<float2*>(c->arena + pl.Y[b]) : nullptr;
-        c->last_us[b] = std::make_tuple(pl.Us[b], d.M, d.ncols);
-        d.qtab = reinterpret_cast<float2*>(c->arena + pl.qtab[pl.grid_of[b]]);
-        ds[b] = d;
+        const char* why = check_frame(frames[b]);
+        if (why) return fail(c, FM_ERR_INVALID_ARG, "fm_graph_create: frame %d: %s", b, why);
     }
-    std::vector<CUtensorMap> maps;
-    bool tc = false;
-    st = choose_cov_path(c, ds, maps, &tc);
+    fm_status st = set_device(c);
     if (st != FM_OK) return st;
-    // scan: batched tensor-core kernel when the frames share M, ncols and the grid
-    CUtensorMap bmap;
-    bool scan_tc = pl.scan_uniform && c->scan_path != FM_COV_SIMT &&
-                   encode_bprep_tmap(reinterpret_cast<float*>(c->arena + pl.bprep_off), pl.bprep_rows,
-                                     pl.bprep_rowlen, &bmap);
-    if (!scan_tc && c->scan_path == FM_COV_TC)
-        return fail(c, FM_ERR_INVALID_ARG, "tensor-core scan needs frames sharing M, ncols and the grid");
-    c->last_scan_path = scan_tc ? FM_COV_TC : FM_COV_SIMT;
-    FrameDesc* dd;
-    GridDesc* dg;
-    st = upload_descs(c, pl, ds, maps, s, &dd, &dg, scan_tc ? &bmap : nullptr);
+    fm_graph* g = new fm_graph();
+    g->parent = c;
+    cudaStream_t cs = nullptr;
+    auto bail = [&](fm_status code) {
+        if (cs) cudaStreamDestroy(cs);
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        if (g->sub) {
+            if (!g->sub->err.empty()) c->err = g->sub->err;  // the failure was recorded on the graph's context
+            fm_destroy(g->sub);
+        }
+        delete g;
+        return code;
+    };
+    if (fm_create(&g->sub, c->budget, c->device) != FM_OK) return bail(fail(c, FM_ERR_CUDA, "fm_graph_create: context"));
+    g->sub->cov_path = c->cov_path;
+    g->sub->scan_path = c->scan_path;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamCreate"));
+    RunPrep rp;
+    st = prepare_run(g->sub, frames, n, cs, rp);
+    if (st != FM_OK) return bail(st);
+    st = enqueue_run(g->sub, rp, cs);  // one plain run: uploads land, kernel attributes are set
+    if (st != FM_OK) return bail(st);
+    e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamSynchronize"));
+    const uint64_t l0 = g->sub->launches;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamBeginCapture"));
+    st = enqueue_run(g->sub, rp, cs);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cs, &graph);
+    g->graph = graph;
+    if (st != FM_OK) return bail(st);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamEndCapture"));
+    g->kernels = g->sub->launches - l0;
+    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaGraphInstantiate"));
+    cudaStreamDestroy(cs);
+    *out = g;
+    return FM_OK;
+}
+
+fm_status fm_graph_launch(fm_graph* g, fm_stream stream) {
+    if (!g) return FM_ERR_INVALID_ARG;
+    fm_status st = set_device(g->parent);
     if (st != FM_OK) return st;
-    const Maxes mx = maxes_of(ds);
-    const int ng = (int)pl.grids.size();
-    st = stage(c, kStGrid, s, [&] { return fm::launch_grid_table(dg, ng, mx.L, dd, n, s); });
-    if (st != FM_OK) return st;
-    st = launch_cov(c, tc, dd, c->arena + pl.tmap_off, n, mx.M, s);
-    if (st != FM_OK) return st;
-    st = run_subspace_chain(c, dd, n, mx, s);
-    if (st != FM_OK) return st;
-    if (scan_tc) {
-        float* bp = reinterpret_cast<float*>(c->arena + pl.bprep_off);
-        const char* bmap_dev = c->arena + pl.tmap_off + sizeof(CUtensorMap) * (size_t)n;
-        st = stage(c, kStScan, s, [&] {
-            cudaError_t e = fm::launch_scan_tc(dd, n, pl.scan_M, pl.scan_nc, pl.scan_L, pl.scan_prec, bp, bmap_dev, s);
-            if (e != cudaSuccess) return e;
-            // main-lobe angles again on the FP32 CUDA cores (see scan_kernel<..., FIXUP>)
-            return fm::launch_scan_fixup(dd, n, mx.L, mx.M, mx.kpad, s);
-        });
-    } else {
-        st = stage(c, kStScan, s, [&] { return fm::launch_scan(dd, n, mx.L, mx.M, mx.kpad, s); });
-    }
-    if (st != FM_OK) return st;
-    return stage(c, kStPeaks, s, [&] { return fm::launch_peaks(dd, n, mx.K, s); });
+    cudaError_t e = cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(g->parent, e, "cudaGraphLaunch");
+    g->parent->launches += g->kernels;
+    return FM_OK;
+}
+
+fm_status fm_graph_destroy(fm_graph* g) {
+    if (!g) return FM_ERR_INVALID_ARG;
+    cudaSetDevice(g->parent->device);
+    cudaDeviceSynchronize();  // a launch may still be in flight
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->sub) fm_destroy(g->sub);
+    delete g;
+    return FM_OK;
 }
 
 fm_status fm_run_subspace(fm_ctx* c, int frame, void* U, fm_stream stream) {
@@ -814,7 +1028,7 @@ fm_status fm_test_matrix(fm_ctx* c, uint64_t seed, uint64_t frame_id, int M, int
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = fm::launch_test_matrix(seed, frame_id, M, l, reinterpret_cast<float2*>(Pi), s);
     if (e != cudaSuccess) return cuda_fail(c, e, "test matrix launch");
-    c->launches++;
+    c->launches += 1;
     return FM_OK;
 }
 
@@ -827,7 +1041,7 @@ fm_status fm_sample_indices(fm_ctx* c, uint64_t seed, uint64_t frame_id, int M, 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = fm::launch_sample_indices(seed, frame_id, M, l, idx, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "sample indices launch");
-    c->launches++;
+    c->launches += 1;
     return FM_OK;
 }
 

@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(kThreads) peaks_kernel(const FrameDesc* __rest
 
 cudaError_t launch_peaks(const FrameDesc* d, int n_frames, int max_K, cudaStream_t s) {
     (void)max_K;
+    count_launch();
     peaks_kernel<<<n_frames, kThreads, 0, s>>>(d);
     return cudaGetLastError();
 }

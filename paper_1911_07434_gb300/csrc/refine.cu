@@ -91,10 +91,12 @@ __global__ void __launch_bounds__(kThreads) xgemm_kernel(const FrameDesc* __rest
 
 cudaError_t launch_refine(const FrameDesc* d, int n_frames, int max_M, int max_T, cudaStream_t s) {
     dim3 g1((max_T + kRows - 1) / kRows, n_frames);
+    count_launch();
     xgemm_kernel<true><<<g1, kThreads, 0, s>>>(d);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 g2((max_M + kRows - 1) / kRows, n_frames);
+    count_launch();
     xgemm_kernel<false><<<g2, kThreads, 0, s>>>(d);
     return cudaGetLastError();
 }

@@ -15,6 +15,9 @@
 #include "fm_internal.cuh"
 
 namespace fm {
+
+thread_local uint64_t g_kernel_launches = 0;
+
 namespace {
 
 constexpr int kThreads = 256;
@@ -101,6 +104,7 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restr
     extern __shared__ float4 smem_raw[];
     float2* Usm = reinterpret_cast<float2*>(smem_raw);  // [M][KP]
     const FrameDesc* dp = descs + blockIdx.y;
+    if ((dp->scan_tc != 0) != FIXUP) return;  // the plain scan skips tensor-core frames, the fixup the others
     const int M = dp->M, L = dp->L, kp = dp->kpad;
     const int i0 = blockIdx.x * kThreads;
     if (i0 >= L) return;
@@ -192,6 +196,7 @@ cudaError_t launch_kp(const FrameDesc* d, int n_frames, int max_L, int max_M, cu
         if (e != cudaSuccess) return e;
     }
     dim3 grid((max_L + kThreads - 1) / kThreads, n_frames);
+    count_launch();
     scan_kernel<KP, NB, FIXUP><<<grid, kThreads, smem, s>>>(d);
     return cudaGetLastError();
 }
@@ -218,6 +223,7 @@ cudaError_t launch_grid_table(const GridDesc* g, int n_grids, int max_L, const F
                               cudaStream_t s) {
     const int gx = (max(max_L, d ? n_frames : 0) + 255) / 256;
     dim3 grid(gx, n_grids + 1);
+    count_launch();
     grid_table_kernel<<<grid, 256, 0, s>>>(g, n_grids, d, n_frames);
     return cudaGetLastError();
 }

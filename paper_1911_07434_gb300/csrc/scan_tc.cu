@@ -304,6 +304,7 @@ cudaError_t launch_ncp(const FrameDesc* d, int n_frames, const void* tmB, int M,
     if (e != cudaSuccess) return e;
     const int fpc = kRowsB / (2 * NCP);
     dim3 grid((L + kRowsA - 1) / kRowsA, (n_frames + fpc - 1) / fpc);
+    count_launch();
     scan_tc_kernel<NCP><<<grid, kThreads, kSmemBytes, s>>>(d, n_frames, reinterpret_cast<const CUtensorMap*>(tmB),
                                                            M, Mp, L, prec);
     return cudaGetLastError();
@@ -322,6 +323,7 @@ cudaError_t launch_scan_tc(const FrameDesc* d, int n_frames, int M, int ncols, i
     const int ncp = scan_tc_ncp(ncols);
     const int Mp = (M + 7) / 8 * 8;
     const int64_t total = (int64_t)n_frames * ncp * Mp;
+    count_launch();
     scan_bprep_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(d, n_frames, M, Mp, ncp, prec, bprep);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -190,6 +190,7 @@ cudaError_t launch_dense(const FrameDesc* d, int n_frames, int max_M, int max_l,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
+    count_launch();
     sketch_dense_kernel<NQ><<<dim3((max_M + kRows - 1) / kRows, n_frames), kThreads, smem, s>>>(d, pass);
     return cudaGetLastError();
 }
@@ -200,12 +201,14 @@ cudaError_t launch_sketch(const FrameDesc* d, int n_frames, int max_M, int max_l
                           bool any_dense, cudaStream_t s) {
     if (pass == 0 && any_gather) {
         const size_t gsm = sizeof(int) * (size_t)(max_M + max_l);
+        count_launch();
         sketch_gather_kernel<<<dim3((max_M + 255) / 256, n_frames), 256, gsm, s>>>(d);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (!any_dense) return cudaSuccess;
     if (pass == 0) {
+        count_launch();
         omega_kernel<<<dim3((max_M * max_l + 255) / 256, n_frames), 256, 0, s>>>(d);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -221,11 +224,13 @@ cudaError_t launch_sketch(const FrameDesc* d, int n_frames, int max_M, int max_l
 
 cudaError_t launch_test_matrix(uint64_t seed, uint64_t frame_id, int M, int l, float2* out, cudaStream_t s) {
     const int64_t n = (int64_t)M * l;
+    count_launch();
     test_matrix_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(seed, frame_id, M, l, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sample_indices(uint64_t seed, uint64_t frame_id, int M, int l, int* out, cudaStream_t s) {
+    count_launch();
     sample_indices_kernel<<<1, 32, sizeof(int) * (size_t)(M + l), s>>>(seed, frame_id, M, l, out);
     return cudaGetLastError();
 }

@@ -1053,6 +1053,7 @@ cudaError_t launch_small(const FrameDesc* d, int n_frames, int max_M, int max_l,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    count_launch();
     e = cudaLaunchKernelEx(&cfg, small_cluster_kernel, d, mode, pass);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -2,11 +2,11 @@
 
 Each frame's result must be the same when it runs alone through fm_run and when it
 is served inside a mix of frames of the three range profiles (M = 256 / 384 / 512,
-different T, K, l and grids), within the scan tolerance: alone, a one-frame batch
-takes the tensor-core scan; in a mixed batch the CUDA-core scan runs, so the
-denominators M - ||U_s^H a||^2 may differ by rounding (bound 16 u M ncols, the
-tensor-core vs CUDA-core scan bound), and a peak may move by one grid point only
-where the two neighbours' denominators are that close.
+different T, K, l and grids), within the scan tolerance: the tensor-core scan runs
+per group of frames sharing M, U_s columns and grid, and a group's batch changes
+with the mix, so the denominators M - ||U_s^H a||^2 may differ by rounding (bound
+16 u M ncols, the tensor-core vs CUDA-core scan bound), and a peak may move by one
+grid point only where the two neighbours' denominators are that close.
 """
 import numpy as np
 import pytest
