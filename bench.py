@@ -425,6 +425,8 @@ def main():
     clk = clocks.stop()
     ctx.set_timing(False)
     launches = ctx.launch_count() - launches0
+    paths = {"covariance": "tensor" if ctx.last_cov_path() == binding.FM_COV_TC else "cuda-core",
+             "scan": {binding.FM_COV_TC: "tensor", binding.FM_COV_SIMT: "cuda-core"}.get(ctx.last_scan_path(), "mixed")}
     step_ms = [step_ev[k].elapsed_time(step_ev[k + 1]) for k in range(args.steps)]
     total_ms = step_ev[0].elapsed_time(step_ev[-1])
     stages = ctx.stage_times(reset=True)
@@ -533,8 +535,7 @@ def main():
         "config": workload_config(args.method, B),
         "latency_ms": {"p50_step": srt[len(srt) // 2], "p99_step": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
                        "single_frame": single},
-        "kernel_paths": {"covariance": "tensor" if ctx.last_cov_path() == binding.FM_COV_TC else "cuda-core",
-                         "scan": "tensor" if ctx.last_scan_path() == binding.FM_COV_TC else "cuda-core"},
+        "kernel_paths": paths,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": roof, "dominant_stage": dom, "stages": stage_summary,
