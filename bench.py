@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=4000, help="requests of the timed serving run (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=20000.0, help="Poisson arrival rate of the serving run")
     ap.add_argument("--uneven-frames", type=int, default=4096, help="frames of the uneven-batch run (0: skip)")
+    ap.add_argument("--precision-frames", type=int, default=32, help="frames of the precision study (0: skip)")
     return ap.parse_args()
 
 
@@ -359,6 +360,54 @@ def uneven_run(binding, synth, dev, n_frames=4096, pool=256, steps=3, seed=0):
             "frames_with_nonzero_status": bad}
 
 
+def precision_run(binding, synth, dev, n_frames=32, steps=3, seed=0):
+    """Precision study (M=1024, T=2048, K=16, l=48, t=1, 36001-point grid, 32 frames): frames/s
+    of each precision mode with and without the FP32 refinement step, and each mode's distance
+    to the all-FP32 run on the same frames (projector ||U U^H - U32 U32^H||_F, max over frames;
+    peak indices equal)."""
+    import numpy as np
+    import torch
+    wl = synth.precision_study_frames(n_frames, seed=seed)
+    f0 = wl.frames[0]
+    M, T = f0.X.shape
+    K, l, t, L = f0.K, f0.l, f0.t, f0.L
+    X = torch.from_numpy(np.stack([f.X for f in wl.frames])).to(dev)
+    P = torch.empty((n_frames, L), dtype=torch.float32, device=dev)
+    idx = torch.empty((n_frames, K), dtype=torch.int32, device=dev)
+    deg = torch.empty((n_frames, K), dtype=torch.float32, device=dev)
+    npk = torch.empty(n_frames, dtype=torch.int32, device=dev)
+    st = torch.zeros(n_frames, dtype=torch.int32, device=dev)
+    ctx = binding.Context(device=dev.index or 0)
+    stream = torch.cuda.current_stream()
+    out, ref = {}, None
+    names = {binding.FM_PREC_FP32: "fp32", binding.FM_PREC_TF32: "tf32", binding.FM_PREC_BF16: "bf16"}
+    for prec in (binding.FM_PREC_FP32, binding.FM_PREC_TF32, binding.FM_PREC_BF16):
+        for refine in (0, 1):
+            fs = [ctx.frame(X[b], K, l, t, binding.FM_RAND_PROJECTION, f0.theta0, f0.step, L, P[b], idx[b], deg[b],
+                            npk[b:b + 1], seed=1, frame_id=wl.frames[b].frame_id, status=st[b:b + 1], prec=prec,
+                            refine=refine) for b in range(n_frames)]
+            ctx.run(fs)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                ctx.run(fs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            U = [ctx.run_subspace(b, M, K).cpu().numpy().astype(np.complex128) for b in range(n_frames)]
+            pk = np.sort(idx.cpu().numpy(), axis=1)
+            r = {"frames_per_s": n_frames / (ms / 1e3), "ms_per_step": ms, "status_ok": int(st.abs().sum()) == 0}
+            if ref is None:
+                ref = (U, pk)
+            else:
+                r["proj_vs_fp32"] = max(float(np.linalg.norm(u @ u.conj().T - v @ v.conj().T)) for u, v in zip(U, ref[0]))
+                r["peaks_equal_fp32"] = bool(np.array_equal(pk, ref[1]))
+            out[f"{names[prec]}{'+refine' if refine else ''}"] = r
+    ctx.close()
+    return {"workload": wl.name, "frames": n_frames, "modes": out}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -519,6 +568,11 @@ def main():
     if args.uneven_frames > 0:
         uneven = uneven_run(binding, synth, dev, args.uneven_frames)
 
+    # ---- precision study: TF32 / BF16 operands, FP32 refinement -------------------
+    precision = None
+    if args.precision_frames > 0:
+        precision = precision_run(binding, synth, dev, args.precision_frames)
+
     # ---- CPU oracle baseline -----------------------------------------------------
     cpu = None
     if not args.no_baseline and rank == 0:
@@ -539,7 +593,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": roof, "dominant_stage": dom, "stages": stage_summary,
-        "serving": serving, "uneven_batch": uneven, "full_eig_music": full, "cpu_baseline": cpu, "clocks": clk,
+        "serving": serving, "uneven_batch": uneven, "precision_study": precision, "full_eig_music": full, "cpu_baseline": cpu, "clocks": clk,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -29,6 +29,8 @@ FM_RAND_SAMPLING = 1
 FM_RAND_PROJECTION = 2
 
 FM_PREC_FP32 = 0
+FM_PREC_TF32 = 1
+FM_PREC_BF16 = 2
 FM_COV_AUTO = 0
 FM_COV_SIMT = 1
 FM_COV_TC = 2

@@ -110,3 +110,15 @@ def test_refine_rejected_without_snapshots(ctx):
         ctx._check(binding.fm_subspace(ctx.h, R.data_ptr(), 1, 32, binding.FmParams(2, 2, 8, 1, 0, 0, 1, 0, 0), 0,
                                        torch.empty((32, 2), dtype=torch.complex64, device="cuda").data_ptr(),
                                        None, None), "fm_subspace")
+
+
+def test_fp32_projector_at_precision_study_size(ctx):
+    """The FP32 target (projector <= 1e-5 against the oracle) at the largest workload,
+    M = 1024, T = 2048, K = 16, l = 48: the eigensolver's stopping test and the
+    Rayleigh-Ritz correction must hold up at l = 48 too."""
+    wl = synth.precision_study_frames(2, seed=0)
+    got = _run(ctx, wl, 2, 0, 0)
+    for fr, (U, P, idx, st) in zip(wl.frames, got):
+        assert st == 0
+        Uo, _, _ = oracle.fast_music(oracle.covariance(fr.X), fr.K, fr.l, fr.t, 2, 5, fr.frame_id)
+        assert _proj_err(U, Uo) <= 1e-5
