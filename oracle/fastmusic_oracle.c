@@ -498,7 +498,7 @@ int orc_fast_music(const zc* R, int M, int K, int l, int t, int method, uint64_t
         goto done;
     }
 
-    /* Step 1: sketch C = S Pi (Algorithm 1 lines 3-4, Algorithm 2 lines 3-4) */
+    /* Step 1: sketch C = S Pi (the sketch step of Algorithms 1 and 2) */
     if (method == 1) {
         rc = orc_sample_indices(seed, frame_id, M, l, idx);
         if (rc < 0) goto done;
@@ -511,14 +511,14 @@ int orc_fast_music(const zc* R, int M, int K, int l, int t, int method, uint64_t
         zgemm_nn(M, l, M, R, Pi, C);
     }
     memcpy(P, Pi, sizeof(zc) * Ml);
-    /* power iterations (Eq. 11, Algorithm 2 line 5): V = orth(C), C = S V */
+    /* power iterations (Eq. 11, Algorithm 2): V = orth(C), C = S V */
     for (int it = 0; it < t; ++it) {
         rc = orc_householder_qr(M, l, C, Vq, Rq);
         if (rc < 0) goto done;
         zgemm_nn(M, l, M, R, Vq, C);
         memcpy(P, Vq, sizeof(zc) * Ml);
     }
-    /* core matrix: W = pinv(P^H S P) = pinv(P^H C) (Eq. 8, Algorithm 2 line 7) */
+    /* core matrix: W = pinv(P^H S P) = pinv(P^H C) (Eq. 8, Algorithm 2) */
     zgemm_hn(l, l, M, P, C, H);
     for (int i = 0; i < l; ++i) /* exact Hermitian part */
         for (int j = i; j < l; ++j) {
@@ -531,10 +531,10 @@ int orc_fast_music(const zc* R, int M, int K, int l, int t, int method, uint64_t
 
     /* Step 2: rank restriction */
     if (form == 0) {
-        /* SVD of C (Algorithm 1 line 7, Algorithm 2 line 8): U_c = Vq, Sigma_c = sv, V_c = Wsv */
+        /* SVD of C (Algorithms 1 and 2): U_c = Vq, Sigma_c = sv, V_c = Wsv */
         rc = orc_svd_jacobi(M, l, C, Vq, sv, Wsv, fmax(1e-14, (double)M * 2.220446049250313e-16), 60);
         if (rc < 0) goto done;
-        /* B = Sigma_c V_c^H W V_c Sigma_c (Algorithm 1 line 8) */
+        /* B = Sigma_c V_c^H W V_c Sigma_c (rank restriction, Algorithm 1) */
         zgemm_hn(l, l, l, Wsv, W, T1);   /* V_c^H W */
         zgemm_nn(l, l, l, T1, Wsv, B);   /* (V_c^H W) V_c */
         for (int i = 0; i < l; ++i)
@@ -551,11 +551,11 @@ int orc_fast_music(const zc* R, int M, int K, int l, int t, int method, uint64_t
                 B[(size_t)i * l + j] = acc;
             }
     }
-    /* SVD of the Hermitian PSD B = eigendecomposition, descending (Algorithm 1 line 8) */
+    /* SVD of the Hermitian PSD B = eigendecomposition, descending (Algorithm 1) */
     rc = orc_eigh_jacobi(l, B, wl, UB, 1e-14, 60);
     if (rc < 0) goto done;
     if (lamB) memcpy(lamB, wl, sizeof(double) * (size_t)l);
-    /* U~ = U_c U_B (Algorithm 1 line 9) */
+    /* U~ = U_c U_B (Algorithm 1) */
     zgemm_nn(M, l, l, Vq, UB, Ub);
     for (int i = 0; i < M; ++i)
         for (int k = 0; k < ncols; ++k) U[(size_t)i * ncols + k] = Ub[(size_t)i * l + k];

@@ -1,7 +1,7 @@
 // small.cu -- per-frame l x l work of Algorithms 1 and 2 (Sec. III).
 //
 //   ORTH  (power step, Eq. 11):  V = orth(C)
-//   FINAL (Alg. 1 lines 5-9 / Alg. 2 lines 7-10):
+//   FINAL (the core-matrix, rank-restriction and eigen steps of Alg. 1 / Alg. 2):
 //         H = P^H C   with P = V (t >= 1; for projection with t = 0, V holds Pi)
 //                     or H = C(I, :) = R(I, I) (sampling, t = 0)       (Eq. 8)
 //         C = Q R_c                         (QR in place of SVD(C): Q = U_c Z, Z unitary)
@@ -925,7 +925,7 @@ __global__ void __launch_bounds__(kThreads) small_cluster_kernel(const FrameDesc
         return;
     }
 
-    // H = P^H C  (core matrix, Eq. 8 / Alg. 2 line 7)
+    // H = P^H C  (core matrix, Eq. 8 / Alg. 2)
     // sampling without power steps: H = C(I, :) (Alg. 1); after a refinement step the
     // sketch is V-based as in Alg. 2, so H = V^H C
     const bool sampled0 = (dp->method == FM_RAND_SAMPLING && dp->t == 0 && !dp->refine);
