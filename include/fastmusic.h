@@ -188,6 +188,22 @@ fm_status fm_graph_destroy(fm_graph* graph);
  * frame. */
 fm_status fm_run_subspace(fm_ctx* ctx, int frame, void* U, fm_stream stream);
 
+/* fm_run_host: fm_run for frames whose X and outputs are in host memory
+ * (page-locked memory lets the copies run asynchronously; pageable memory works
+ * but the copies then block the host).  Asynchronous: the call enqueues, on
+ * streams of the context, the host -> device copies of every X (rows of T
+ * complex elements taken with stride ldx) into one of two device staging
+ * slots, the whole chain, and the device -> host copies of every output, and
+ * makes `stream` wait for the last copy, so once `stream` has passed the call
+ * the host outputs are written.  Consecutive calls overlap: the copies of one
+ * call run while the previous call computes.  The host X must hold its data
+ * when the call is made (the copies in do not wait for earlier work on
+ * `stream`), and the caller keeps the host buffers of a call untouched until
+ * `stream` has passed it.  The staging slots are
+ * device memory of the context outside the workspace budget (the frames' X and
+ * outputs, twice). */
+fm_status fm_run_host(fm_ctx* ctx, const fm_frame* frames, int n_frames, fm_stream stream);
+
 /* ---- steps (uniform batches; each frame at a fixed stride) ------------------
  * fm_covariance (Eq. 2): R_b = X_b X_b^H / T for b < n_frames.  X_b = X +
  * b * x_frame_stride complex elements; R_b = R + b*M*M (complex64, full

@@ -77,6 +77,7 @@ _SIGS = {
     "fm_stage_times": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int), c_int]),
     "fm_launch_count": (c_uint64, [c_void_p]),
     "fm_run_subspace": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "fm_run_host": (c_int, [c_void_p, POINTER(FmFrame), c_int, c_void_p]),
     "fm_autotune": (c_int, [c_void_p, POINTER(FmFrame), c_int, c_void_p, c_int, POINTER(c_int), POINTER(c_int),
                             POINTER(c_float)]),
     "fm_graph_create": (c_int, [c_void_p, POINTER(FmFrame), c_int, POINTER(c_void_p)]),
@@ -202,6 +203,11 @@ def fm_graph_destroy(graph) -> int:
     return load().fm_graph_destroy(graph)
 
 
+def fm_run_host(ctx, frames, stream) -> int:
+    arr = (FmFrame * len(frames))(*frames)
+    return load().fm_run_host(ctx, arr, len(frames), stream)
+
+
 def fm_run_subspace(ctx, frame, U, stream) -> int:
     return load().fm_run_subspace(ctx, frame, U, stream)
 
@@ -297,6 +303,10 @@ class Context:
         f.n_peaks = n_peaks.data_ptr()
         f.status = status.data_ptr() if status is not None else None
         return f
+
+    def run_host(self, frames, stream=None):
+        """fm_run on frames whose X and outputs are host (pinned) tensors; asynchronous."""
+        self._check(fm_run_host(self.h, frames, _stream_handle(stream)), "fm_run_host")
 
     def run(self, frames, stream=None):
         self._check(fm_run(self.h, frames, _stream_handle(stream)), "fm_run")

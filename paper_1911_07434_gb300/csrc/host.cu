@@ -67,6 +67,16 @@ struct fm_ctx {
     // set on a serving slot's private context: the arena grows with stream-ordered
     // free/alloc on that slot's stream, which other slots' work never waits for
     cudaStream_t arena_stream = nullptr;
+    // fm_run_host: copy and compute streams, two device staging slots
+    struct HostSlot {
+        char* buf = nullptr;
+        size_t bytes = 0;
+        cudaEvent_t h2d = nullptr, comp = nullptr, d2h = nullptr;
+        bool used = false;
+    };
+    HostSlot hslot[2];
+    int hnext = 0;
+    cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
     // U_s of the frames of the most recent fm_run: (workspace offset, M, ncols)
     std::vector<std::tuple<size_t, int, int>> last_us;
     size_t arena_cap = 0;  // serving slot: what the budget leaves beside the other slots
@@ -531,6 +541,18 @@ fm_status fm_destroy(fm_ctx* c) {
         if (sl->stream) cudaStreamDestroy(sl->stream);
         delete sl;
     }
+    for (fm_ctx::HostSlot& h : c->hslot) {
+        if (h.d2h) cudaEventSynchronize(h.d2h);
+        if (h.buf) cudaFree(h.buf);
+        if (h.h2d) cudaEventDestroy(h.h2d);
+        if (h.comp) cudaEventDestroy(h.comp);
+        if (h.d2h) cudaEventDestroy(h.d2h);
+    }
+    for (cudaStream_t hs : {c->s_h2d, c->s_comp, c->s_d2h})
+        if (hs) {
+            cudaStreamSynchronize(hs);
+            cudaStreamDestroy(hs);
+        }
     if (c->staging_done) {
         cudaEventSynchronize(c->staging_done);
         cudaEventDestroy(c->staging_done);
@@ -689,6 +711,113 @@ fm_status fm_run(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream) {
     st = prepare_run(c, frames, n, s, rp);
     if (st != FM_OK) return st;
     return enqueue_run(c, rp, s);
+}
+
+// ---- fm_run with host buffers ---------------------------------------------------
+// Three context streams: host -> device copies, the chain, device -> host copies,
+// chained by events, with two device staging slots so that the copies of one
+// call overlap the chain of the previous one.
+fm_status fm_run_host(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (!frames || n < 1) return fail(c, FM_ERR_INVALID_ARG, "fm_run_host: no frames");
+    for (int b = 0; b < n; ++b) {
+        const char* why = check_frame(frames[b]);
+        if (why) return fail(c, FM_ERR_INVALID_ARG, "fm_run_host: frame %d: %s", b, why);
+    }
+    fm_status st = set_device(c);
+    if (st != FM_OK) return st;
+    cudaError_t e = cudaSuccess;
+    for (cudaStream_t* hs : {&c->s_h2d, &c->s_comp, &c->s_d2h})
+        if (!*hs && (e = cudaStreamCreateWithFlags(hs, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(c, e, "cudaStreamCreate");
+    fm_ctx::HostSlot& h = c->hslot[c->hnext];
+    c->hnext ^= 1;
+    for (cudaEvent_t* ev : {&h.h2d, &h.comp, &h.d2h})
+        if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(c, e, "cudaEventCreate");
+    // device staging layout: per frame packed X (M x T), then every output
+    std::vector<size_t> xo(n), po(n), dbo(n), io(n), dgo(n), no(n), so(n);
+    size_t off = 0;
+    for (int b = 0; b < n; ++b) {
+        const fm_frame& f = frames[b];
+        const size_t M = (size_t)f.arr.M, K = (size_t)f.p.K, L = (size_t)f.grid.L;
+        xo[b] = off;
+        off = aup(off + 8 * M * (size_t)f.T);
+        po[b] = off;
+        off = aup(off + 4 * L);
+        dbo[b] = off;
+        if (f.P_db_out) off = aup(off + 4 * L);
+        io[b] = off;
+        off = aup(off + 4 * K);
+        dgo[b] = off;
+        off = aup(off + 4 * K);
+        no[b] = off;
+        off = aup(off + 4);
+        so[b] = off;
+        off = aup(off + 4);
+    }
+    if (off > h.bytes) {
+        if (h.used) cudaEventSynchronize(h.d2h);  // the slot's previous call is done with it
+        if (h.buf) cudaFree(h.buf);
+        h.buf = nullptr;
+        h.bytes = 0;
+        e = cudaMalloc(&h.buf, off + off / 4);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(host-run staging)");
+        h.bytes = off + off / 4;
+    }
+    cudaStream_t us = reinterpret_cast<cudaStream_t>(stream);
+    // copies in: once this slot's previous results have left (the host X must hold its
+    // data when the call is made; waiting on `stream` here would also wait for the
+    // previous call's copies out, which `stream` is made to wait for, and serialise)
+    if (h.used) cudaStreamWaitEvent(c->s_h2d, h.d2h, 0);
+    std::vector<fm_frame> dev(frames, frames + n);
+    for (int b = 0; b < n; ++b) {
+        const fm_frame& f = frames[b];
+        const size_t row = 8 * (size_t)f.T;
+        if (f.ldx == f.T)  // one contiguous block
+            e = cudaMemcpyAsync(h.buf + xo[b], f.X, row * (size_t)f.arr.M, cudaMemcpyHostToDevice, c->s_h2d);
+        else
+            e = cudaMemcpy2DAsync(h.buf + xo[b], row, f.X, 8 * (size_t)f.ldx, row, (size_t)f.arr.M,
+                                  cudaMemcpyHostToDevice, c->s_h2d);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy2DAsync(X)");
+        dev[b].X = h.buf + xo[b];
+        dev[b].ldx = f.T;
+        dev[b].P_out = reinterpret_cast<float*>(h.buf + po[b]);
+        dev[b].P_db_out = f.P_db_out ? reinterpret_cast<float*>(h.buf + dbo[b]) : nullptr;
+        dev[b].peak_idx = reinterpret_cast<int*>(h.buf + io[b]);
+        dev[b].peak_deg = reinterpret_cast<float*>(h.buf + dgo[b]);
+        dev[b].n_peaks = reinterpret_cast<int*>(h.buf + no[b]);
+        dev[b].status = reinterpret_cast<int*>(h.buf + so[b]);
+    }
+    cudaEventRecord(h.h2d, c->s_h2d);
+    // the chain
+    cudaStreamWaitEvent(c->s_comp, h.h2d, 0);
+    RunPrep rp;
+    st = prepare_run(c, dev.data(), n, c->s_comp, rp);
+    if (st != FM_OK) return st;
+    st = enqueue_run(c, rp, c->s_comp);
+    if (st != FM_OK) return st;
+    cudaEventRecord(h.comp, c->s_comp);
+    // copies out
+    cudaStreamWaitEvent(c->s_d2h, h.comp, 0);
+    for (int b = 0; b < n; ++b) {
+        const fm_frame& f = frames[b];
+        const size_t L = (size_t)f.grid.L, K = (size_t)f.p.K;
+        e = cudaMemcpyAsync(f.P_out, h.buf + po[b], 4 * L, cudaMemcpyDeviceToHost, c->s_d2h);
+        if (e == cudaSuccess && f.P_db_out)
+            e = cudaMemcpyAsync(f.P_db_out, h.buf + dbo[b], 4 * L, cudaMemcpyDeviceToHost, c->s_d2h);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(f.peak_idx, h.buf + io[b], 4 * K, cudaMemcpyDeviceToHost, c->s_d2h);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(f.peak_deg, h.buf + dgo[b], 4 * K, cudaMemcpyDeviceToHost, c->s_d2h);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(f.n_peaks, h.buf + no[b], 4, cudaMemcpyDeviceToHost, c->s_d2h);
+        if (e == cudaSuccess && f.status)
+            e = cudaMemcpyAsync(f.status, h.buf + so[b], 4, cudaMemcpyDeviceToHost, c->s_d2h);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync(outputs)");
+    }
+    cudaEventRecord(h.d2h, c->s_d2h);
+    h.used = true;
+    e = cudaStreamWaitEvent(us, h.d2h, 0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamWaitEvent");
+    return FM_OK;
 }
 
 // ---- autotuning of the kernel paths -------------------------------------------

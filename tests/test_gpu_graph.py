@@ -123,3 +123,35 @@ def test_autotune_picks_a_working_path(lib):
             assert st == 0 and np.all(P > 0)
     finally:
         ctx.close()
+
+
+def test_run_host_matches_device_run(lib):
+    """fm_run_host (host X and outputs, strided rows) gives fm_run's results bit for bit,
+    also with two calls in flight on one stream."""
+    ctx = lib.Context(device=0)
+    try:
+        wl = synth.uneven_frames(10, seed=12)
+        b = Batch(lib, wl)
+        ctx.run(b.frames)
+        ref = b.results()
+        hosts, frames = [], []
+        for fr in wl.frames:
+            M, T = fr.X.shape
+            Xh = torch.zeros((M, T + 3), dtype=torch.complex64).pin_memory()  # ldx = T + 3
+            Xh[:, :T] = torch.from_numpy(fr.X)
+            P = torch.full((fr.L,), -1.0, dtype=torch.float32).pin_memory()
+            idx = torch.full((fr.K,), -7, dtype=torch.int32).pin_memory()
+            deg = torch.empty(fr.K, dtype=torch.float32).pin_memory()
+            n = torch.zeros(1, dtype=torch.int32).pin_memory()
+            st = torch.full((1,), -1, dtype=torch.int32).pin_memory()
+            hosts.append((Xh, P, idx, deg, n, st))
+            frames.append(lib.Context.frame(Xh[:, :T], fr.K, fr.l, fr.t, 2, fr.theta0, fr.step, fr.L, P, idx, deg, n,
+                                            seed=3, frame_id=fr.frame_id, status=st))
+        ctx.run_host(frames)
+        ctx.run_host(frames)  # second call overlaps the first one's chain
+        torch.cuda.synchronize()
+        for (P0, i0, s0), (Xh, P, idx, deg, n, st) in zip(ref, hosts):
+            assert int(st.item()) == 0
+            assert np.array_equal(P0, P.numpy()) and np.array_equal(i0, idx.numpy())
+    finally:
+        ctx.close()
