@@ -7,6 +7,8 @@
 // fresh register accumulator which is then added to the running total, which
 // keeps the FP32 rounding error near sqrt(kChunk) + sqrt(T / kChunk) ulps
 // instead of sqrt(T).
+#include <algorithm>
+
 #include "fm_internal.cuh"
 
 namespace fm {
@@ -138,7 +140,29 @@ __global__ void __launch_bounds__(kThreads, 2) cov_fp32_kernel(const FrameDesc* 
     }
 }
 
+// Copy the caller's X (leading dimension ldx_in, odd or misaligned for TMA) into
+// the workspace copy the tensor-core covariance reads (even ldx, 256-byte base).
+// Consecutive threads take consecutive snapshots of a row: coalesced both ways.
+__global__ void repack_kernel(const FrameDesc* __restrict__ descs) {
+    const FrameDesc* dp = descs + blockIdx.y;
+    if (!dp->Xin) return;
+    const int M = dp->M, T = dp->T;
+    const int64_t n = (int64_t)M * T;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = e / T, t = e % T;
+        const_cast<float2*>(dp->X)[m * dp->ldx + t] = dp->Xin[m * dp->ldx_in + t];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_repack(const FrameDesc* d, int n_frames, int max_M, int max_T, cudaStream_t s) {
+    const int64_t n = (int64_t)max_M * max_T;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 256);
+    count_launch();
+    repack_kernel<<<dim3(blocks, n_frames), 256, 0, s>>>(d);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_covariance(const FrameDesc* d, int n_frames, int max_M, cudaStream_t s) {
     const int nt = (max_M + kTile - 1) / kTile;

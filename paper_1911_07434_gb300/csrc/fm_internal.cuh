@@ -16,6 +16,8 @@ constexpr int kKPadMax = 32;   // largest padded K in the scan
 struct FrameDesc {
     const float2* X;   // M x T, leading dim ldx
     int64_t ldx;
+    const float2* Xin; // caller's X when X is a repacked copy (rows of T, even ldx), else null
+    int64_t ldx_in;
     int M, T, K, l, t, method, L, ncols;  // ncols = columns of U_s used by the scan
     int kpad;          // padded column count of Us (multiple of 4)
     int prec;          // fm_precision of the covariance and scan GEMMs
@@ -175,6 +177,7 @@ cudaError_t launch_scan_tc(const FrameDesc* d, int n_frames, int M, int ncols, i
                            cudaStream_t s);
 int scan_tc_ncp(int ncols);
 cudaError_t launch_covariance(const FrameDesc* d, int n_frames, int max_M, cudaStream_t s);
+cudaError_t launch_repack(const FrameDesc* d, int n_frames, int max_M, int max_T, cudaStream_t s);
 cudaError_t launch_sketch(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, bool any_gather,
                           bool any_dense, cudaStream_t s);
 cudaError_t launch_orth(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, cudaStream_t s);

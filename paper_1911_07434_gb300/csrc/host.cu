@@ -254,6 +254,7 @@ struct Plan {
     };
     std::vector<ScanGroup> scan_groups;
     std::vector<size_t> R, C, V, Us, idx, Y;  // per-frame offsets (R == SIZE_MAX: caller-owned)
+    std::vector<size_t> Xpad;  // repacked copy of X for the tensor-core covariance (SIZE_MAX: none)
     std::vector<int> grid_of;
     std::vector<GridDesc> grids;
     std::vector<size_t> qtab;
@@ -299,6 +300,10 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
     }
     for (int b = 0; b < n; ++b) {
         const size_t M = (size_t)f[b].arr.M, l = (size_t)f[b].p.l;
+        // TMA needs a 16-byte aligned base and an even ldx: other frames get a padded copy
+        const bool pad = need_R && ((reinterpret_cast<uintptr_t>(f[b].X) % 16) != 0 || (f[b].ldx % 2) != 0);
+        pl.Xpad.push_back(pad ? off : SIZE_MAX);
+        if (pad) off = aup(off + sizeof(float2) * M * (size_t)(f[b].T + (f[b].T & 1)));
         pl.R.push_back(need_R ? off : SIZE_MAX);
         if (need_R) off = aup(off + sizeof(float2) * M * M);
         pl.C.push_back(need_sketch ? off : SIZE_MAX);
@@ -593,7 +598,7 @@ struct RunPrep {
     Plan pl;
     std::vector<int> order;
     Maxes mx;
-    bool cov_tc = false, scan_tc = false, scan_simt = true;
+    bool cov_tc = false, scan_tc = false, scan_simt = true, any_repack = false;
     std::vector<char> group_tc;  // per scan group: runs on the tensor cores
     FrameDesc* dd = nullptr;
     GridDesc* dg = nullptr;
@@ -625,6 +630,13 @@ static fm_status prepare_run(fm_ctx* c, const fm_frame* frames, int n, cudaStrea
         d.idx = reinterpret_cast<int*>(c->arena + pl.idx[k]);
         d.Us = reinterpret_cast<float2*>(c->arena + pl.Us[k]);
         d.Y = pl.Y[k] != SIZE_MAX ? reinterpret_cast<float2*>(c->arena + pl.Y[k]) : nullptr;
+        if (pl.Xpad[k] != SIZE_MAX && c->cov_path != FM_COV_SIMT) {
+            d.Xin = d.X;
+            d.ldx_in = d.ldx;
+            d.X = reinterpret_cast<const float2*>(c->arena + pl.Xpad[k]);
+            d.ldx = d.T + (d.T & 1);
+            rp.any_repack = true;
+        }
         c->last_us[rp.order[k]] = std::make_tuple(pl.Us[k], d.M, d.ncols);
         d.qtab = reinterpret_cast<float2*>(c->arena + pl.qtab[pl.grid_of[k]]);
         ds[k] = d;
@@ -670,6 +682,10 @@ static fm_status enqueue_run(fm_ctx* c, const RunPrep& rp, cudaStream_t s) {
     const int n = rp.n, ng = (int)pl.grids.size();
     fm_status st = stage(c, kStGrid, s, [&] { return fm::launch_grid_table(rp.dg, ng, mx.L, dd, n, s); });
     if (st != FM_OK) return st;
+    if (rp.any_repack) {  // frames whose X TMA cannot read get a padded copy first
+        st = stage(c, kStCov, s, [&] { return fm::launch_repack(dd, n, mx.M, mx.T, s); });
+        if (st != FM_OK) return st;
+    }
     st = launch_cov(c, rp.cov_tc, dd, c->arena + pl.tmap_off, n, mx.M, s);
     if (st != FM_OK) return st;
     st = run_subspace_chain(c, dd, n, mx, s);
@@ -742,7 +758,7 @@ fm_status fm_run_host(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream
         const fm_frame& f = frames[b];
         const size_t M = (size_t)f.arr.M, K = (size_t)f.p.K, L = (size_t)f.grid.L;
         xo[b] = off;
-        off = aup(off + 8 * M * (size_t)f.T);
+        off = aup(off + 8 * M * (size_t)(f.T + (f.T & 1)));  // rows padded to an even length
         po[b] = off;
         off = aup(off + 4 * L);
         dbo[b] = off;
@@ -774,14 +790,15 @@ fm_status fm_run_host(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream
     for (int b = 0; b < n; ++b) {
         const fm_frame& f = frames[b];
         const size_t row = 8 * (size_t)f.T;
-        if (f.ldx == f.T)  // one contiguous block
+        const int64_t ldd = f.T + (f.T & 1);
+        if (f.ldx == f.T && ldd == f.T)  // one contiguous block
             e = cudaMemcpyAsync(h.buf + xo[b], f.X, row * (size_t)f.arr.M, cudaMemcpyHostToDevice, c->s_h2d);
         else
-            e = cudaMemcpy2DAsync(h.buf + xo[b], row, f.X, 8 * (size_t)f.ldx, row, (size_t)f.arr.M,
+            e = cudaMemcpy2DAsync(h.buf + xo[b], 8 * (size_t)ldd, f.X, 8 * (size_t)f.ldx, row, (size_t)f.arr.M,
                                   cudaMemcpyHostToDevice, c->s_h2d);
         if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy2DAsync(X)");
         dev[b].X = h.buf + xo[b];
-        dev[b].ldx = f.T;
+        dev[b].ldx = ldd;
         dev[b].P_out = reinterpret_cast<float*>(h.buf + po[b]);
         dev[b].P_db_out = f.P_db_out ? reinterpret_cast<float*>(h.buf + dbo[b]) : nullptr;
         dev[b].peak_idx = reinterpret_cast<int*>(h.buf + io[b]);
