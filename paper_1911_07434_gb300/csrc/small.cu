@@ -699,8 +699,11 @@ __device__ int eig_onesided(const float2* Frm, float2* Wc, float2* Z, float* w, 
     for (int e = threadIdx.x; e < kMaxSweeps; e += kThreads) sm.flags[e] = 0;
     __syncthreads();
     const float tol2 = kOneSidedTol * kOneSidedTol;
+    // largest |g|^2 / (a b) met in the sweep, as int bits (non-negative floats order as ints)
+    int* sweep_max = sm.flags + kMaxSweeps + 6;
     int sweeps = -1;
     for (int sweep = 0; sweep < kMaxSweeps && nr > 0; ++sweep) {
+        if (threadIdx.x == 0) *sweep_max = 0;
         for (int k = warp; k < n; k += kWarps) {  // exact column norms for this sweep
             float a = 0.f;
             for (int i = lane; i < n; i += 32) a = fmaf(Wc[k * n + i].x, Wc[k * n + i].x, fmaf(Wc[k * n + i].y, Wc[k * n + i].y, a));
@@ -758,44 +761,64 @@ __device__ int eig_onesided(const float2* Frm, float2* Wc, float2* Z, float* w, 
                     g[j][0] += __shfl_xor_sync(0xffffffffu, g[j][0], o);
                     g[j][1] += __shfl_xor_sync(0xffffffffu, g[j][1], o);
                 }
+            // rotation parameters of every pair in straight-line code (identity where the
+            // pair is already orthogonal to the tolerance), then the column updates
             bool any = false;
+            float ratio = 0.f;
+            float cc[kPW], ss[kPW], tm[kPW];
+            float2 u10[kPW], u11[kPW];
 #pragma unroll
             for (int j = 0; j < kPW; ++j) {
                 const float gr = g[j][0], gi = g[j][1];
                 const float mag2 = fmaf(gr, gr, gi * gi);
-                const bool rot = live[j] && mag2 > FLT_MIN && mag2 > tol2 * na[j] * nb[j];  // warp-uniform
+                const float ab = na[j] * nb[j];
+                const bool rot = live[j] && mag2 > FLT_MIN && mag2 > tol2 * ab;  // warp-uniform
+                if (live[j] && ab > 0.f) ratio = fmaxf(ratio, __fdividef(mag2, ab));
                 const float inv = rsqrtf(fmaxf(mag2, FLT_MIN));
                 const float mag = mag2 * inv;
                 const float tau = 0.5f * (nb[j] - na[j]) * inv;
                 // smaller root of t^2 + 2 tau t - 1 = 0 (t -> 0 as |tau| -> inf)
-                const float t = copysignf(__fdividef(1.f, fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f))), tau);
-                const float c = rsqrtf(fmaf(t, t, 1.f)), sn = t * c;
-                // F <- F U, U = [[c, s], [-s conj(ph), c conj(ph)]], ph = g / |g|
-                const float2 phc = make_float2(gr * inv, -gi * inv);
-                const float2 u10 = cscale(phc, -sn), u11 = cscale(phc, c);
-                if (rot) {
-                    any = true;
+                const float q1 = fmaf(tau, tau, 1.f);
+                const float t = rot ? copysignf(__fdividef(1.f, fabsf(tau) + q1 * rsqrtf(q1)), tau) : 0.f;
+                const float c = rsqrtf(fmaf(t, t, 1.f));
+                cc[j] = c;
+                ss[j] = t * c;
+                tm[j] = t * mag;
+                // F <- F U, U = [[c, s], [-s conj(ph), c conj(ph)]], ph = g / |g| (1 if no rotation)
+                const float2 phc = rot ? make_float2(gr * inv, -gi * inv) : make_float2(1.f, 0.f);
+                u10[j] = cscale(phc, -ss[j]);
+                u11[j] = cscale(phc, c);
+                any |= rot;
+            }
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int i = lane + 32 * h;
-                        if (i < n) {
-                            fp[j][i] = cadd(cscale(xp[j][h], c), cmul(xq[j][h], u10));
-                            fq[j][i] = cadd(cscale(xp[j][h], sn), cmul(xq[j][h], u11));
-                        }
-                    }
-                    if (lane == 0) {
-                        w[pi[j]] = na[j] - t * mag;
-                        w[qi[j]] = nb[j] + t * mag;
+            for (int j = 0; j < kPW; ++j) {
+                if (!live[j]) continue;  // a dead pair's pointers alias column 0 of a live one
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int i = lane + 32 * h;
+                    if (i < n) {
+                        fp[j][i] = cadd(cscale(xp[j][h], cc[j]), cmul(xq[j][h], u10[j]));
+                        fq[j][i] = cadd(cscale(xp[j][h], ss[j]), cmul(xq[j][h], u11[j]));
                     }
                 }
+                if (lane == 0) {
+                    w[pi[j]] = na[j] - tm[j];
+                    w[qi[j]] = nb[j] + tm[j];
+                }
             }
-            if (any && lane == 0) sm.flags[sweep] = 1;
+            if (lane == 0) {
+                if (any) sm.flags[sweep] = 1;
+                atomicMax(sweep_max, __float_as_int(ratio));
+            }
             __syncthreads();
         }
-        if (!sm.flags[sweep]) {
-            sweeps = sweep;
+        // converged: no rotation in this sweep, or every pair of it was within 1e-4 before its
+        // rotation, so after it (quadratic convergence) within 1e-8 < the tolerance
+        if (!sm.flags[sweep] || __int_as_float(*sweep_max) < 1e-8f) {
+            sweeps = sweep + (sm.flags[sweep] ? 1 : 0);
             break;
         }
+        __syncthreads();  // every thread has read *sweep_max before the next sweep resets it
     }
     if (nr == 0) sweeps = 0;
     // eigenvalues |f_k|^2, eigenvectors f_k / |f_k| (row-major into Z)
