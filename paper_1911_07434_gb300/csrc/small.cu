@@ -306,15 +306,27 @@ __device__ void reduce_d(cg::cluster_group& cl, float4* part, float4* out, int l
 
 // ------------------------------------------------------ Cholesky / inverse --
 // In place, G = R^H R with R upper (FP32).  Returns false on a non-positive pivot.
-__device__ bool chol_f(float2* G, int l, const Sm& sm) {
-    if (threadIdx.x == 0) sm.flags[kMaxSweeps + 4] = 0;
+// floor_rel > 0 (CholeskyQR of a sketch): a pivot below floor_rel x the largest
+// diagonal entry, i.e. a numerically rank-deficient C, is raised to that floor, so
+// Q = C R^{-1} stays finite and spans range(C); only a non-finite pivot fails.
+// floor_rel = 0 (the core matrix H): any non-positive pivot fails.
+__device__ bool chol_f(float2* G, int l, const Sm& sm, float floor_rel = 0.f) {
+    if (threadIdx.x == 0) {
+        sm.flags[kMaxSweeps + 4] = 0;
+        float dmax = 0.f;
+        for (int k = 0; k < l; ++k) dmax = fmaxf(dmax, G[k * l + k].x);
+        sm.scal[2] = floor_rel * dmax;
+    }
     __syncthreads();
+    const float dfloor = sm.scal[2];
     for (int k = 0; k < l; ++k) {
         if (threadIdx.x == 0) {
             float d = G[k * l + k].x;
-            if (!(d > 0.f)) {
+            if (!isfinite(d) || (floor_rel == 0.f && !(d > 0.f))) {
                 sm.flags[kMaxSweeps + 4] = 1;
                 d = 1e-30f;
+            } else if (!(d > dfloor)) {
+                d = dfloor > 0.f ? dfloor : 1e-30f;
             }
             const float r = sqrtf(d);
             G[k * l + k] = make_float2(r, 0.f);
@@ -340,15 +352,25 @@ __device__ bool chol_f(float2* G, int l, const Sm& sm) {
     return sm.flags[kMaxSweeps + 4] == 0;
 }
 
+// Pivots below 2^-40 x the largest diagonal entry (a numerically rank-deficient
+// sketch) are raised to that floor; only a non-finite pivot fails.
 __device__ bool chol_d(float4* G, int l, const Sm& sm) {
-    if (threadIdx.x == 0) sm.flags[kMaxSweeps + 4] = 0;
+    if (threadIdx.x == 0) {
+        sm.flags[kMaxSweeps + 4] = 0;
+        float dmax = 0.f;
+        for (int k = 0; k < l; ++k) dmax = fmaxf(dmax, G[k * l + k].x);
+        sm.scal[2] = 0x1p-40f * dmax;
+    }
     __syncthreads();
+    const float dfloor = sm.scal[2];
     for (int k = 0; k < l; ++k) {
         if (threadIdx.x == 0) {
             df d = zload(G[k * l + k]).re;
-            if (!(d.hi > 0.f)) {
+            if (!isfinite(d.hi)) {
                 sm.flags[kMaxSweeps + 4] = 1;
                 d = df{1e-30f, 0.f};
+            } else if (!(d.hi > dfloor)) {
+                d = df{dfloor > 0.f ? dfloor : 1e-30f, 0.f};
             }
             const df r = dd_sqrt(d);
             G[k * l + k] = make_float4(r.hi, r.lo, 0.f, 0.f);
@@ -528,11 +550,28 @@ __device__ bool cholqr2(cg::cluster_group& cl, float2* A, int rows, int l, const
     }
     gram_part_f(A, A, rows, l, true, reinterpret_cast<float2*>(sm.part));
     reduce_f(cl, reinterpret_cast<float2*>(sm.part), sm.Gf, l, true);
-    ok = chol_f(sm.Gf, l, sm) && ok;
+    ok = chol_f(sm.Gf, l, sm, 0x1p-20f) && ok;
     trinv_f(sm.Gf, sm.Xf, l);
     apply_f(A, A, rows, l, sm.Xf, l, l, l, true);
     upper_mul(sm.Gf, sm.Rc, sm.T, l);
     return ok;
+}
+
+// perm <- indices of w ordered by value descending, ties by index.  NaN sorts as
+// -inf, so perm is a permutation of 0..n-1 whatever w holds (its entries index
+// shared-memory arrays).
+__device__ void sort_desc(const float* w, int* perm, int n) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kThreads) {
+        int rank = 0;
+        const float wi = isnan(w[i]) ? -INFINITY : w[i];
+        for (int j = 0; j < n; ++j) {
+            const float wj = isnan(w[j]) ? -INFINITY : w[j];
+            rank += (wj > wi) || (wj == wi && j < i);
+        }
+        perm[rank] = i;
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------- Jacobi ----
@@ -665,13 +704,7 @@ __device__ int jacobi(float2* A, float2* Z, float* w, int* perm, int n, const Sm
     if (nr == 0) sweeps = 0;
     for (int i = threadIdx.x; i < n; i += kThreads) w[i] = A[i * n + i].x;
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += kThreads) {
-        int rank = 0;
-        const float wi = w[i];
-        for (int j = 0; j < n; ++j) rank += (w[j] > wi) || (w[j] == wi && j < i);
-        perm[rank] = i;
-    }
-    __syncthreads();
+    sort_desc(w, perm, n);
     return sweeps;
 }
 
@@ -833,13 +866,7 @@ __device__ int eig_onesided(const float2* Frm, float2* Wc, float2* Z, float* w, 
         if (lane == 0) w[k] = a;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += kThreads) {
-        int rank = 0;
-        const float wi = w[i];
-        for (int j = 0; j < n; ++j) rank += (w[j] > wi) || (w[j] == wi && j < i);
-        perm[rank] = i;
-    }
-    __syncthreads();
+    sort_desc(w, perm, n);
     return sweeps;
 }
 
