@@ -10,18 +10,57 @@
 //   XH = true : a = snapshot t, k = antenna m, A = conj(X[m][t]), B = V, out = Y;
 //   XH = false: a = antenna m,  k = snapshot t, A = X[m][t],       B = Y, out = C / T.
 // A CTA owns 64 rows a and all l <= 48 columns; k runs in chunks of 32 through
-// shared memory, and each thread accumulates a 4 x 3 register tile.
+// double-buffered shared memory (cp.async: the next chunk streams in while the
+// current one is used), and each thread accumulates a 4 x 3 register tile.
 #include "fm_internal.cuh"
 
 namespace fm {
 namespace {
 
 constexpr int kRows = 64, kChunk = 32, kCols = 48, kThreads = 256;
+constexpr int kAStride = kRows + 1;                                        // As[kk][aa] row stride
+constexpr int kBufElems = kChunk * kAStride + kChunk * kCols;              // one stage, float2 units
+constexpr size_t kSmemBytes = 2 * sizeof(float2) * (size_t)kBufElems;      // double-buffered
+
+// 8-byte global -> shared copy that completes asynchronously; src_bytes = 0 fills zeros.
+__device__ __forceinline__ void cp_async8(float2* dst, const float2* src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Stage k-chunk k0 of A (As[kk][aa]) and B (Bs[kk][j]) into one buffer.
+template <bool XH>
+__device__ __forceinline__ void load_chunk(float2* buf, const float2* __restrict__ X, int64_t ldx,
+                                           const float2* __restrict__ B, int l, int a0, int n_rows, int inner,
+                                           int k0) {
+    float2* As = buf;
+    float2* Bs = buf + kChunk * kAStride;
+    for (int e = threadIdx.x; e < kChunk * kRows; e += kThreads) {
+        int kk, aa;
+        if (XH) {  // consecutive threads: consecutive snapshots t = a of one antenna row m = k
+            kk = e / kRows;
+            aa = e % kRows;
+        } else {   // consecutive threads: consecutive snapshots t = k of one antenna row m = a
+            aa = e / kChunk;
+            kk = e % kChunk;
+        }
+        const bool ok = (k0 + kk < inner) && (a0 + aa < n_rows);
+        const int64_t off = XH ? (int64_t)(k0 + kk) * ldx + a0 + aa : (int64_t)(a0 + aa) * ldx + k0 + kk;
+        cp_async8(As + kk * kAStride + aa, ok ? X + off : X, ok);
+    }
+    for (int e = threadIdx.x; e < kChunk * kCols; e += kThreads) {
+        const int kk = e / kCols, j = e % kCols;
+        const bool ok = (k0 + kk < inner) && (j < l);
+        cp_async8(Bs + kk * kCols + j, ok ? B + (int64_t)(k0 + kk) * l + j : B, ok);
+    }
+}
 
 template <bool XH>
 __global__ void __launch_bounds__(kThreads) xgemm_kernel(const FrameDesc* __restrict__ descs) {
-    __shared__ float2 As[kChunk][kRows + 1];
-    __shared__ float2 Bs[kChunk][kCols];
+    extern __shared__ float2 smem[];
     const FrameDesc* dp = descs + blockIdx.y;
     if (!dp->refine) return;
     const int M = dp->M, T = dp->T, l = dp->l;
@@ -38,40 +77,38 @@ __global__ void __launch_bounds__(kThreads) xgemm_kernel(const FrameDesc* __rest
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[r][c] = make_float2(0.f, 0.f);
 
-    for (int k0 = 0; k0 < inner; k0 += kChunk) {
-        for (int e = threadIdx.x; e < kChunk * kRows; e += kThreads) {
-            float2 v = make_float2(0.f, 0.f);
-            if (XH) {  // consecutive threads: consecutive snapshots of one antenna row
-                const int kk = e / kRows, aa = e % kRows;
-                if (k0 + kk < inner && a0 + aa < n_rows) {
-                    v = X[(int64_t)(k0 + kk) * ldx + a0 + aa];
-                    v.y = -v.y;
-                }
-                As[kk][aa] = v;
-            } else {   // consecutive threads: consecutive snapshots of one antenna row
-                const int aa = e / kChunk, kk = e % kChunk;
-                if (k0 + kk < inner && a0 + aa < n_rows) v = X[(int64_t)(a0 + aa) * ldx + k0 + kk];
-                As[kk][aa] = v;
-            }
-        }
-        for (int e = threadIdx.x; e < kChunk * kCols; e += kThreads) {
-            const int kk = e / kCols, j = e % kCols;
-            Bs[kk][j] = (k0 + kk < inner && j < l) ? B[(int64_t)(k0 + kk) * l + j] : make_float2(0.f, 0.f);
+    const int nchunks = (inner + kChunk - 1) / kChunk;
+    load_chunk<XH>(smem, X, ldx, B, l, a0, n_rows, inner, 0);
+    cp_async_commit();
+    for (int c = 0; c < nchunks; ++c) {
+        if (c + 1 < nchunks) {  // the next chunk streams in while this one is used
+            load_chunk<XH>(smem + ((c + 1) & 1) * kBufElems, X, ldx, B, l, a0, n_rows, inner, (c + 1) * kChunk);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
+        const float2* As = smem + (c & 1) * kBufElems;
+        const float2* Bs = As + kChunk * kAStride;
 #pragma unroll 4
         for (int kk = 0; kk < kChunk; ++kk) {
             float2 a[4], b[3];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) a[r] = As[kk][ta + 16 * r];
+            for (int r = 0; r < 4; ++r) a[r] = As[kk * kAStride + ta + 16 * r];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) b[c] = Bs[kk][3 * tj + c];
+            for (int q = 0; q < 3; ++q) b[q] = Bs[kk * kCols + 3 * tj + q];
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) cfma(acc[r][c], a[r], b[c]);
+                for (int q = 0; q < 3; ++q) {
+                    if (XH)
+                        cfmac(acc[r][q], a[r], b[q]);  // conj(X) V
+                    else
+                        cfma(acc[r][q], a[r], b[q]);
+                }
         }
-        __syncthreads();
+        __syncthreads();  // the buffer is refilled two chunks later
     }
     float2* __restrict__ out = XH ? dp->Y : dp->C;
     const float scale = XH ? 1.0f : (float)(1.0 / (double)T);
@@ -80,9 +117,9 @@ __global__ void __launch_bounds__(kThreads) xgemm_kernel(const FrameDesc* __rest
         const int a = a0 + ta + 16 * r;
         if (a >= n_rows) continue;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int j = 3 * tj + c;
-            if (j < l) out[(int64_t)a * l + j] = make_float2(acc[r][c].x * scale, acc[r][c].y * scale);
+        for (int q = 0; q < 3; ++q) {
+            const int j = 3 * tj + q;
+            if (j < l) out[(int64_t)a * l + j] = make_float2(acc[r][q].x * scale, acc[r][q].y * scale);
         }
     }
 }
@@ -90,14 +127,18 @@ __global__ void __launch_bounds__(kThreads) xgemm_kernel(const FrameDesc* __rest
 }  // namespace
 
 cudaError_t launch_refine(const FrameDesc* d, int n_frames, int max_M, int max_T, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(xgemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(xgemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
     dim3 g1((max_T + kRows - 1) / kRows, n_frames);
     count_launch();
-    xgemm_kernel<true><<<g1, kThreads, 0, s>>>(d);
-    cudaError_t e = cudaGetLastError();
+    xgemm_kernel<true><<<g1, kThreads, kSmemBytes, s>>>(d);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 g2((max_M + kRows - 1) / kRows, n_frames);
     count_launch();
-    xgemm_kernel<false><<<g2, kThreads, 0, s>>>(d);
+    xgemm_kernel<false><<<g2, kThreads, kSmemBytes, s>>>(d);
     return cudaGetLastError();
 }
 
