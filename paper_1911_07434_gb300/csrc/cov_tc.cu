@@ -14,12 +14,13 @@
 // or BF16 operands with one kind::f16 MMA per 16 snapshots (FM_PREC_BF16); the
 // accumulator is FP32 in every mode.
 //
-// Warp roles (192 threads): warp 0 issues the TMA loads of the raw interleaved
+// Warp roles (320 threads): warp 0 issues the TMA loads of the raw interleaved
 // complex64 tiles (128 rows x 16 snapshots = one 128-byte swizzled box per
 // operand and stage); warp 1 allocates TMEM and issues the MMAs (one thread);
-// warps 2-5 split each raw stage into planar hi/lo operand tiles in the
-// 128-byte-swizzled K-major layout the MMA descriptors expect, and finally run
-// the epilogue (TMEM -> registers -> R tile and its conjugate mirror).  Raw and
+// warps 2-9 (one row of A or of B each) split each raw stage into planar operand
+// tiles in the 128-byte-swizzled K-major layout the MMA descriptors expect, and
+// finally run the epilogue (TMEM -> registers -> R tile and its conjugate
+// mirror).  Raw and
 // converted stages are double-buffered and handed over with mbarriers; every
 // wait is bounded and records FM_ERR_TIMEOUT in the frame status on expiry.
 #include "tc_common.cuh"
@@ -36,7 +37,8 @@ constexpr int kConvB = 2 * kTile * 128;            // 32 KB: 256 rows ([Xr_J; Xi
 constexpr int kRawStage = 2 * kRawBox;             // A and B boxes
 constexpr int kConvStage = 2 * kConvA + kConvB;    // Ar, Ai, B
 constexpr int kNRaw = 2, kNConv = 2;
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 convert + epilogue
+constexpr int kConv = kThreads - 64;
 constexpr int kTiles = kNRaw * kRawStage + kNConv * kConvStage;   // 192 KB
 constexpr int kSmemBytes = kTiles + 1024 + 256;                   // + 1024-B alignment slack + barriers
 constexpr uint32_t kTmemCols = 512;
@@ -131,10 +133,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kNRaw; ++s) {
             mbar_init(&raw_full[s], 1);
-            mbar_init(&raw_empty[s], 128);
+            mbar_init(&raw_empty[s], kConv);
         }
         for (int s = 0; s < kNConv; ++s) {
-            mbar_init(&conv_full[s], 128);
+            mbar_init(&conv_full[s], kConv);
             mbar_init(&conv_empty[s], 1);
         }
         mbar_init(acc_full, 1);
@@ -209,7 +211,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ------------------------------------------- converters, then epilogue --
-        const int r = threadIdx.x - 64;  // 0..127: one row of each tile
+        const int r = threadIdx.x - 64;  // 0..255: row r of A (r < 128) or row r - 128 of B
+        const bool is_b = r >= kTile;
+        const int rr = r & (kTile - 1);
         for (int s = 0; s < nstages; ++s) {
             const int rs = s % kNRaw, cs = s % kNConv;
             if (!mbar_wait(&raw_full[rs], (uint32_t)(s / kNRaw) & 1u, abort_flag)) break;
@@ -217,13 +221,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             const char* rawA = reinterpret_cast<const char*>(raw + rs * kRawStage);
             const char* rawB = diag ? rawA : rawA + kRawBox;
             char* cv = reinterpret_cast<char*>(conv + cs * kConvStage);
-            convert_row(rawA, r, cv, r, cv + kConvA, r, prec);                        // Ar, Ai
-            convert_row(rawB, r, cv + 2 * kConvA, r, cv + 2 * kConvA, 128 + r, prec);  // B = [Br; Bi]
+            if (!is_b)
+                convert_row(rawA, rr, cv, rr, cv + kConvA, rr, prec);                         // Ar, Ai
+            else
+                convert_row(rawB, rr, cv + 2 * kConvA, rr, cv + 2 * kConvA, 128 + rr, prec);  // B = [Br; Bi]
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(&conv_full[cs]);
             mbar_arrive(&raw_empty[rs]);
         }
-        // epilogue: rows 32 * (warp % 4) + lane of the tile
+        // epilogue: rows 32 * (warp % 4) + lane of the tile (a warp reads only its TMEM
+        // lane quadrant), complex columns [64 h, 64 h + 64) with h = 0 for warps 2-5
         // warp-uniform: tcgen05.ld below is .sync.aligned
         const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full, 0u, abort_flag));
         tc_fence_after();
@@ -234,7 +241,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
             const float invT = (float)(1.0 / (double)T);
             float2* __restrict__ R = dp->R;
-            for (int c0 = 0; c0 < kTile; c0 += 16) {
+            const int h = (warp - 2) >> 2;
+            for (int c0 = 64 * h; c0 < 64 * h + 64; c0 += 16) {
                 uint32_t rr[16], ri[16], ir[16], ii[16];
                 tmem_ld16(tl + c0, rr);
                 tmem_ld16(tl + 128 + c0, ri);
