@@ -15,8 +15,9 @@
 // operands (FM_PREC_BF16, one kind::f16 MMA per 8 antennas).  Two 128 x 256 FP32
 // accumulators fill the 512 TMEM columns.
 //
-// Warp roles (192 threads): warp 0 TMA producer, warp 1 TMEM allocation + MMA
-// issue, warps 2-5 steering generation (one angle row each) and the epilogue.
+// Warp roles (320 threads): warp 0 TMA producer, warp 1 TMEM allocation + MMA
+// issue, warps 2-9 steering generation (two threads per angle row, half of each
+// stage's antennas each) and the epilogue.
 #include "tc_common.cuh"
 
 namespace fm {
@@ -30,7 +31,7 @@ constexpr int kStageA = kRowsA * 128;      // 16 KB: [hi 16 | lo 16] floats per 
 constexpr int kStageB = kRowsB * 128;      // 64 KB
 constexpr int kStage = kStageA + kStageB;
 constexpr int kNStages = 2;
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 steering + epilogue
 constexpr int kTiles = kNStages * kStage;  // 160 KB
 constexpr int kSmemBytes = kTiles + 1024 + 256;
 constexpr uint32_t kTmemCols = 512;
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kNStages; ++s) {
-            mbar_init(&a_full[s], 128);
+            mbar_init(&a_full[s], kThreads - 64);
             mbar_init(&b_full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -184,7 +185,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ------------------------------------------ steering generation --------
-        const int r = threadIdx.x - 64;
+        // two threads per angle row: half g generates antenna pairs c = 2 g, 2 g + 1 of each stage
+        const int r = (threadIdx.x - 64) & (kRowsA - 1), g = (threadIdx.x - 64) >> 7;
         const int i = i0 + r;
         const float2 qq = (i < L) ? descs[0].qtab[i] : make_float2(0.f, 0.f);
         for (int s = 0; s < nstages; ++s) {
@@ -193,7 +195,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             char* arow = reinterpret_cast<char*>(base + slot * kStage);
             if (prec == FM_PREC_BF16) {  // 16 BF16 values (8 antennas) in the row's first 32 bytes
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int c = 2 * g + cc;
                     const int m0 = 8 * s + 2 * c;
                     const float2 a0 = (i < L && m0 < M) ? steer_exact(m0, qq.x, qq.y) : make_float2(0.f, 0.f);
                     const float2 a1 = (i < L && m0 + 1 < M) ? steer_exact(m0 + 1, qq.x, qq.y) : make_float2(0.f, 0.f);
@@ -205,7 +208,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 continue;
             }
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {  // chunk c: antennas 8s + 2c, 8s + 2c + 1
+            for (int cc = 0; cc < 2; ++cc) {  // chunk c: antennas 8s + 2c, 8s + 2c + 1
+                const int c = 2 * g + cc;
                 uint4 hi, lo;
                 uint32_t h[2], w[2];
                 const int m0 = 8 * s + 2 * c;
@@ -231,14 +235,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full, 0u, abort_flag));
         tc_fence_after();
         if (ok) {
-            const int q = warp & 3;
+            // a warp reads its TMEM lane quadrant; the two warps of a quadrant split the columns
+            const int q = warp & 3, half = (warp - 2) >> 2;
             const int row = 32 * q + lane;
             const int ia = i0 + row;
             const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
             const float Mf = (float)M;
             if constexpr (kRowsPerFrame <= 16) {
                 const int nchunks = (nrows + 15) / 16;
-                for (int ch = 0; ch < nchunks; ++ch) {
+                for (int ch = half; ch < nchunks; ch += 2) {
                     uint32_t v[16];
                     tmem_ld16(tl + 16 * ch, v);
                     tmem_wait_ld();
@@ -261,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
             } else {
-                for (int f = 0; f < nf; ++f) {
+                for (int f = half; f < nf; f += 2) {
                     float acc = 0.f;
 #pragma unroll
                     for (int h = 0; h < kRowsPerFrame / 16; ++h) {
