@@ -9,9 +9,9 @@
 //   pass p >= 1        : C = R V with V the basis from the previous orth step.
 //
 // Dense form: each CTA owns 64 rows of R and all l columns of C.  Threads hold a
-// 4-row x ceil(l/8)-column register tile; R and V stream through shared memory
-// in 32-column chunks with the next chunk prefetched into registers while the
-// current one is consumed.  FP32 products, two-level accumulation (per chunk,
+// 4-row x ceil(l/8)-column register tile; R and V stream through double-buffered
+// shared memory in 32-column chunks (cp.async: the next chunk arrives while the
+// current one is consumed).  FP32 products, two-level accumulation (per chunk,
 // then into the running sum).  R is read from HBM exactly once per pass.
 #include "fm_internal.cuh"
 
@@ -25,6 +25,11 @@ constexpr int kRowT = 4;       // rows per thread (rg + 16 r)
 constexpr int kColG = 8;       // column groups (cg + 8 q)
 constexpr int kMaxQ = kLMax / kColG;
 constexpr int kALoads = kRows * kKc / kThreads;  // 16 complex per thread per chunk
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
 
 template <int NQ>
 __global__ void __launch_bounds__(kThreads) sketch_dense_kernel(const FrameDesc* __restrict__ descs, int pass) {
@@ -50,52 +55,36 @@ __global__ void __launch_bounds__(kThreads) sketch_dense_kernel(const FrameDesc*
 #pragma unroll
         for (int q = 0; q < NQ; ++q) acc[r][q] = tmp[r][q] = make_float2(0.f, 0.f);
 
-    // prefetch registers: A chunk (64 x 32) = 16 per thread; B chunk (32 x l) <= 16 per thread
-    float2 pa[kALoads], pb[kALoads];
+    // chunk k0 of R rows (64 x 32) and of V (32 x l) into buffer buf, asynchronously
     const int nb = kKc * l;
-    auto gload = [&](int k0) {
+    auto load_chunk = [&](int buf, int k0) {
 #pragma unroll
         for (int u = 0; u < kALoads; ++u) {
             const int e = tid + u * kThreads;
-            const int rr = e >> 5, kk = e & 31;  // kKc == 32
+            const int rr = e >> 5, kk = e & 31;  // kKc == 32: a warp reads 32 consecutive entries of a row
             const int gr = r0 + rr, gk = k0 + kk;
-            pa[u] = (gr < M && gk < M) ? R[(int64_t)gr * M + gk] : make_float2(0.f, 0.f);
+            const bool ok = gr < M && gk < M;
+            cp_async8(&As[buf][rr][kk], ok ? R + (int64_t)gr * M + gk : R, ok);
         }
-#pragma unroll
-        for (int u = 0; u < kALoads; ++u) {
-            const int e = tid + u * kThreads;
-            float2 v = make_float2(0.f, 0.f);
-            if (e < nb) {
-                const int kk = e / l, j = e - kk * l;
-                const int gk = k0 + kk;
-                if (gk < M) v = V[(int64_t)gk * l + j];
-            }
-            pb[u] = v;
+        for (int e = tid; e < nb; e += kThreads) {
+            const int kk = e / l;
+            const bool ok = k0 + kk < M;
+            cp_async8(Bbase + buf * nb + e, ok ? V + (int64_t)k0 * l + e : V, ok);
         }
-    };
-    auto sstore = [&](int buf) {
-#pragma unroll
-        for (int u = 0; u < kALoads; ++u) {
-            const int e = tid + u * kThreads;
-            As[buf][e >> 5][e & 31] = pa[u];
-        }
-#pragma unroll
-        for (int u = 0; u < kALoads; ++u) {
-            const int e = tid + u * kThreads;
-            if (e < nb) {
-                const int kk = e / l, j = e - kk * l;
-                Bbase[(buf * kKc + kk) * l + j] = pb[u];
-            }
-        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     };
 
     const int nchunks = (M + kKc - 1) / kKc;
-    gload(0);
-    sstore(0);
-    __syncthreads();
+    load_chunk(0, 0);
     for (int c = 0; c < nchunks; ++c) {
         const int buf = c & 1;
-        if (c + 1 < nchunks) gload((c + 1) * kKc);
+        if (c + 1 < nchunks) {  // the next chunk streams in while this one is used
+            load_chunk(buf ^ 1, (c + 1) * kKc);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
 #pragma unroll 8
         for (int kk = 0; kk < kKc; ++kk) {
             float2 a[kRowT], b[NQ];
@@ -104,7 +93,7 @@ __global__ void __launch_bounds__(kThreads) sketch_dense_kernel(const FrameDesc*
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 const int j = cg + kColG * q;
-                b[q] = (j < l) ? Bbase[(buf * kKc + kk) * l + j] : make_float2(0.f, 0.f);
+                b[q] = (j < l) ? Bbase[buf * nb + kk * l + j] : make_float2(0.f, 0.f);
             }
 #pragma unroll
             for (int r = 0; r < kRowT; ++r)
@@ -120,8 +109,7 @@ __global__ void __launch_bounds__(kThreads) sketch_dense_kernel(const FrameDesc*
                     tmp[r][q] = make_float2(0.f, 0.f);
                 }
         }
-        if (c + 1 < nchunks) sstore(buf ^ 1);
-        __syncthreads();
+        __syncthreads();  // the buffer is refilled by the next iteration's load
     }
 #pragma unroll
     for (int r = 0; r < kRowT; ++r) {
