@@ -968,8 +968,12 @@ __global__ void __launch_bounds__(kThreads) small_cluster_kernel(const FrameDesc
 
     load_rows(dp->C, sm.Cs, r0, rows, l);
     if (mode == kOrth) {
+        // The power step only needs a well-conditioned basis of range(C): the core
+        // matrix H = V^H C and the Nystrom form C H^+ C^H do not depend on which
+        // basis V is.  One double-float CholeskyQR pass leaves V orthonormal to about
+        // u cond(C) (cond(V) ~ 1), so the second pass of CholeskyQR2 is not taken.
         __syncthreads();
-        const bool ok = cholqr2(cl, sm.Cs, rows, l, sm, false);
+        const bool ok = cholqr_pass_d(cl, sm.Cs, rows, l, sm, sm.Rc);
         store_rows(sm.Cs, dp->V, r0, rows, l);
         if (!ok && rank == 0 && threadIdx.x == 0) set_status(dp->status, FM_ERR_NO_CONVERGENCE);
         return;
