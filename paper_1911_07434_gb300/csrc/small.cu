@@ -950,7 +950,7 @@ __device__ void orthonormalize_cols_d(float2* Z, int n, int k, const Sm& sm) {
 }
 
 // ---------------------------------------------------------------- kernel ----
-__global__ void __launch_bounds__(kThreads) small_cluster_kernel(const FrameDesc* __restrict__ descs, int mode,
+__global__ void __launch_bounds__(kThreads, 3) small_cluster_kernel(const FrameDesc* __restrict__ descs, int mode,
                                                                  int pass) {
     extern __shared__ float4 smem_raw[];
     cg::cluster_group cl = cg::this_cluster();
