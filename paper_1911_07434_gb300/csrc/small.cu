@@ -254,15 +254,31 @@ __device__ void gram_part_d(const float2* A, int rows, int l, float4* part) {
     for (int e = threadIdx.x; e < n; e += kThreads) {
         int i, j;
         tri_coords(e, l, i, j);
-        df re{0.f, 0.f}, im{0.f, 0.f};
-        for (int r = 0; r < rows; ++r) {
-            const float2 a = A[r * l + i], b = A[r * l + j];
-            dd_acc(re, a.x, b.x);
-            dd_acc(re, a.y, b.y);
-            dd_acc(im, a.x, b.y);
-            dd_acc(im, -a.y, b.x);
+        // four interleaved double-float partial sums (rows r = 4 u + v) shorten the
+        // dependent chain; they are combined in a fixed order at the end
+        df re[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        df im[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        int r = 0;
+        for (; r + 4 <= rows; r += 4) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float2 a = A[(r + v) * l + i], b = A[(r + v) * l + j];
+                dd_acc(re[v], a.x, b.x);
+                dd_acc(re[v], a.y, b.y);
+                dd_acc(im[v], a.x, b.y);
+                dd_acc(im[v], -a.y, b.x);
+            }
         }
-        part[e] = zpack(zd{quick_two_sum(re.hi, re.lo), quick_two_sum(im.hi, im.lo)});
+        for (; r < rows; ++r) {
+            const float2 a = A[r * l + i], b = A[r * l + j];
+            dd_acc(re[0], a.x, b.x);
+            dd_acc(re[0], a.y, b.y);
+            dd_acc(im[0], a.x, b.y);
+            dd_acc(im[0], -a.y, b.x);
+        }
+        const df sr = dd_add(dd_add(re[0], re[1]), dd_add(re[2], re[3]));
+        const df si = dd_add(dd_add(im[0], im[1]), dd_add(im[2], im[3]));
+        part[e] = zpack(zd{quick_two_sum(sr.hi, sr.lo), quick_two_sum(si.hi, si.lo)});
     }
 }
 
@@ -443,35 +459,49 @@ __device__ void trinv_d(const float4* R, float4* X, int l, const Sm& sm) {
 }
 
 // In place, row-local: rows of A (rows x l) <- A * X for X upper triangular given
-// in double-float (hi, lo) pairs.  Warp w owns rows w, w + 8, ...; a row is
+// in double-float (hi, lo) pairs.  Warp w owns rows 4w .. 4w + 3, then 32 further
+// on, and so on; lane c accumulates column c of its four rows at once; a row is
 // overwritten only after the whole warp has read it.
 __device__ void apply_upper_d(float2* A, int rows, int l, const float4* X) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int r = warp; r < rows; r += kWarps) {
-        float2 out[2];
+    constexpr int kRB = 4;  // rows per warp pass: four independent accumulation chains per lane
+    for (int r0 = warp * kRB; r0 < rows; r0 += kWarps * kRB) {
+        float2 out[kRB][2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int c = lane + 32 * h;
-            out[h] = make_float2(0.f, 0.f);
-            if (c >= l) continue;
-            df re{0.f, 0.f}, im{0.f, 0.f};
-            for (int k = 0; k <= c; ++k) {
-                const float2 a = A[r * l + k];
-                const float4 x = X[k * l + c];  // (re.hi, re.lo, im.hi, im.lo)
-                dd_acc(re, a.x, x.x);
-                dd_acc(re, -a.y, x.z);
-                dd_acc(im, a.x, x.z);
-                dd_acc(im, a.y, x.x);
-                re.lo = fmaf(a.x, x.y, fmaf(-a.y, x.w, re.lo));
-                im.lo = fmaf(a.x, x.w, fmaf(a.y, x.y, im.lo));
+            df re[kRB], im[kRB];
+#pragma unroll
+            for (int u = 0; u < kRB; ++u) re[u] = im[u] = df{0.f, 0.f};
+            if (c < l) {
+                for (int k = 0; k <= c; ++k) {
+                    const float4 x = X[k * l + c];  // (re.hi, re.lo, im.hi, im.lo)
+#pragma unroll
+                    for (int u = 0; u < kRB; ++u) {
+                        const int r = min(r0 + u, rows - 1);  // rows past the end repeat the last one
+                        const float2 a = A[r * l + k];
+                        dd_acc(re[u], a.x, x.x);
+                        dd_acc(re[u], -a.y, x.z);
+                        dd_acc(im[u], a.x, x.z);
+                        dd_acc(im[u], a.y, x.x);
+                        re[u].lo = fmaf(a.x, x.y, fmaf(-a.y, x.w, re[u].lo));
+                        im[u].lo = fmaf(a.x, x.w, fmaf(a.y, x.y, im[u].lo));
+                    }
+                }
             }
-            out[h] = make_float2(re.hi + re.lo, im.hi + im.lo);
+#pragma unroll
+            for (int u = 0; u < kRB; ++u) out[u][h] = make_float2(re[u].hi + re[u].lo, im[u].hi + im[u].lo);
         }
         __syncwarp();
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int c = lane + 32 * h;
-            if (c < l) A[r * l + c] = out[h];
+        for (int u = 0; u < kRB; ++u) {
+            const int r = r0 + u;
+            if (r >= rows) continue;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = lane + 32 * h;
+                if (c < l) A[r * l + c] = out[u][h];
+            }
         }
         __syncwarp();
     }
