@@ -459,51 +459,47 @@ __device__ void trinv_d(const float4* R, float4* X, int l, const Sm& sm) {
 }
 
 // In place, row-local: rows of A (rows x l) <- A * X for X upper triangular given
-// in double-float (hi, lo) pairs.  Warp w owns rows 4w .. 4w + 3, then 32 further
-// on, and so on; lane c accumulates column c of its four rows at once; a row is
-// overwritten only after the whole warp has read it.
+// in double-float (hi, lo) pairs.  Output (r, c) sums k = 0 .. c, so a task pairs
+// column c with column l - 1 - c of the same row (l + 1 terms per task whatever c)
+// to balance the threads; every result is held in registers until the whole block
+// has read A, then written in place.
 __device__ void apply_upper_d(float2* A, int rows, int l, const float4* X) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int kRB = 4;  // rows per warp pass: four independent accumulation chains per lane
-    for (int r0 = warp * kRB; r0 < rows; r0 += kWarps * kRB) {
-        float2 out[kRB][2];
+    constexpr int kMaxTasks = (kMaxRows * ((kLMax + 1) / 2) + kThreads - 1) / kThreads;  // 12 at l = 48
+    const int half = (l + 1) / 2;       // column pairs per row (the middle column alone if l is odd)
+    const int ntask = rows * half;
+    float2 out[kMaxTasks][2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int c = lane + 32 * h;
-            df re[kRB], im[kRB];
+    for (int u = 0; u < kMaxTasks; ++u) {
+        const int task = threadIdx.x + u * kThreads;
+        out[u][0] = out[u][1] = make_float2(0.f, 0.f);
+        if (task >= ntask) continue;
+        const int r = task / half, cp = task - r * half;
 #pragma unroll
-            for (int u = 0; u < kRB; ++u) re[u] = im[u] = df{0.f, 0.f};
-            if (c < l) {
-                for (int k = 0; k <= c; ++k) {
-                    const float4 x = X[k * l + c];  // (re.hi, re.lo, im.hi, im.lo)
-#pragma unroll
-                    for (int u = 0; u < kRB; ++u) {
-                        const int r = min(r0 + u, rows - 1);  // rows past the end repeat the last one
-                        const float2 a = A[r * l + k];
-                        dd_acc(re[u], a.x, x.x);
-                        dd_acc(re[u], -a.y, x.z);
-                        dd_acc(im[u], a.x, x.z);
-                        dd_acc(im[u], a.y, x.x);
-                        re[u].lo = fmaf(a.x, x.y, fmaf(-a.y, x.w, re[u].lo));
-                        im[u].lo = fmaf(a.x, x.w, fmaf(a.y, x.y, im[u].lo));
-                    }
-                }
+        for (int side = 0; side < 2; ++side) {
+            const int c = side ? l - 1 - cp : cp;
+            if (side && c == cp) continue;  // odd l: the middle column once
+            df re{0.f, 0.f}, im{0.f, 0.f};
+            for (int k = 0; k <= c; ++k) {
+                const float2 a = A[r * l + k];
+                const float4 x = X[k * l + c];  // (re.hi, re.lo, im.hi, im.lo)
+                dd_acc(re, a.x, x.x);
+                dd_acc(re, -a.y, x.z);
+                dd_acc(im, a.x, x.z);
+                dd_acc(im, a.y, x.x);
+                re.lo = fmaf(a.x, x.y, fmaf(-a.y, x.w, re.lo));
+                im.lo = fmaf(a.x, x.w, fmaf(a.y, x.y, im.lo));
             }
-#pragma unroll
-            for (int u = 0; u < kRB; ++u) out[u][h] = make_float2(re[u].hi + re[u].lo, im[u].hi + im[u].lo);
+            out[u][side] = make_float2(re.hi + re.lo, im.hi + im.lo);
         }
-        __syncwarp();
+    }
+    __syncthreads();
 #pragma unroll
-        for (int u = 0; u < kRB; ++u) {
-            const int r = r0 + u;
-            if (r >= rows) continue;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int c = lane + 32 * h;
-                if (c < l) A[r * l + c] = out[u][h];
-            }
-        }
-        __syncwarp();
+    for (int u = 0; u < kMaxTasks; ++u) {
+        const int task = threadIdx.x + u * kThreads;
+        if (task >= ntask) continue;
+        const int r = task / half, cp = task - r * half;
+        A[r * l + cp] = out[u][0];
+        if (l - 1 - cp != cp) A[r * l + l - 1 - cp] = out[u][1];
     }
     __syncthreads();
 }
