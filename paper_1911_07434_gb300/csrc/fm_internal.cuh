@@ -23,11 +23,14 @@ struct FrameDesc {
     int prec;          // fm_precision of the covariance and scan GEMMs
     int refine;        // 1: one more power step C = X (X^H V) / T in FP32 before the final solve
     int scan_tc;       // 1: scanned by the tensor-core kernel (then main lobes by the fixup scan)
+    int sketch_tc;     // 1: the tensor-core sketch is prepared for this frame (Bsk, tensor maps)
+    int pad2_;
     float2* R;         // M x M
     float2* C;         // M x l  sketch
     float2* V;         // M x l  basis (power steps) / Q
     float2* Us;        // M x kpad (zero-padded)
     float2* Y;         // T x l  X^H V of the refinement step (refine only)
+    float* Bsk;        // 2 l_pad x 2M  B rows of the tensor-core sketch (sketch_tc only)
     int* idx;          // l sampled indices
     float2* qtab;      // L entries (q_hi, q_lo): q = 2 d_wl sin(theta_i), split for exact m*q_hi
     float* P;          // L
@@ -162,6 +165,16 @@ __device__ __forceinline__ void set_status(int* status, int code) {
     if (status) atomicOr(status, 1 << code);
 }
 
+// Sketch passes that run on the tensor cores (sketch_tc.cu): every pass of a frame in
+// TF32 / BF16 mode; in FP32 mode every pass but the last, whose product the final
+// solve reads (sampling has no product at pass 0).
+__host__ __device__ inline bool sketch_on_tc(int method, int prec, int t, int pass) {
+    if (pass == 0 && method != FM_RAND_PROJECTION) return false;
+    if (prec != FM_PREC_FP32) return true;
+    return pass < t;
+}
+__host__ __device__ inline int sketch_tc_lpad(int l) { return (l + 7) / 8 * 8; }
+
 // ---------------------------------------------------------- launch wrappers --
 // Kernel launches issued by the calling host thread (every launch site bumps it),
 // so the host side can report exactly how many kernels a call launched.
@@ -183,6 +196,8 @@ cudaError_t launch_sketch(const FrameDesc* d, int n_frames, int max_M, int max_l
 cudaError_t launch_orth(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, cudaStream_t s);
 cudaError_t launch_final(const FrameDesc* d, int n_frames, int max_M, int max_l, cudaStream_t s);
 cudaError_t launch_refine(const FrameDesc* d, int n_frames, int max_M, int max_T, cudaStream_t s);
+cudaError_t launch_sketch_tc(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, const void* tmA,
+                             const void* tmB, cudaStream_t s);
 cudaError_t launch_scan(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s);
 cudaError_t launch_scan_fixup(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s);
 cudaError_t launch_peaks(const FrameDesc* d, int n_frames, int max_K, cudaStream_t s);

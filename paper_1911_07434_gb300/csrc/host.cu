@@ -255,6 +255,7 @@ struct Plan {
     std::vector<ScanGroup> scan_groups;
     std::vector<size_t> R, C, V, Us, idx, Y;  // per-frame offsets (R == SIZE_MAX: caller-owned)
     std::vector<size_t> Xpad;  // repacked copy of X for the tensor-core covariance (SIZE_MAX: none)
+    std::vector<size_t> Bsk;   // B rows of the tensor-core sketch (SIZE_MAX: none)
     std::vector<int> grid_of;
     std::vector<GridDesc> grids;
     std::vector<size_t> qtab;
@@ -268,8 +269,10 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
     size_t off = 0;
     pl.desc_off = off;
     off = aup(off + sizeof(FrameDesc) * (size_t)n);
-    pl.tmap_off = off;  // TMA tensor maps: one per frame's X (covariance), then one per scan group's B
-    if (need_R) off = aup(off + sizeof(CUtensorMap) * (2 * (size_t)n));
+    // TMA tensor maps: per frame X (covariance); per scan group B; per frame R and the
+    // B rows of the tensor-core sketch
+    pl.tmap_off = off;
+    if (need_R) off = aup(off + sizeof(CUtensorMap) * (4 * (size_t)n));
     std::map<GridKey, int> gmap;
     pl.grid_of.assign(n, -1);
     if (need_grid) {
@@ -312,6 +315,11 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
         if (need_sketch) off = aup(off + sizeof(float2) * M * l);
         pl.idx.push_back(need_sketch ? off : SIZE_MAX);
         if (need_sketch) off = aup(off + sizeof(int) * l);
+        bool tcsk = false;  // some pass of this frame runs on the tensor-core sketch
+        for (int pass = 0; need_R && pass <= f[b].p.t; ++pass)
+            tcsk |= fm::sketch_on_tc(f[b].p.method, f[b].p.prec, f[b].p.t, pass);
+        pl.Bsk.push_back(tcsk ? off : SIZE_MAX);
+        if (tcsk) off = aup(off + sizeof(float) * 2 * (size_t)fm::sketch_tc_lpad((int)l) * 2 * M);
         const bool y = need_sketch && f[b].p.refine;  // X^H V of the refinement step
         pl.Y.push_back(y ? off : SIZE_MAX);
         if (y) off = aup(off + sizeof(float2) * (size_t)f[b].T * l);
@@ -433,6 +441,26 @@ bool encode_tmap(const FrameDesc& d, CUtensorMap* out) {
     return r == CUDA_SUCCESS;
 }
 
+// The tensor-core sketch: R viewed as M x 2M FP32 (boxes of 128 rows x 32 floats) and
+// its B rows (2 l_pad x 2M FP32, one box of all 2 l_pad rows x 32 floats).
+bool encode_sketch_tmaps(const FrameDesc& d, CUtensorMap* a, CUtensorMap* b) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return false;
+    const int nb = 2 * fm::sketch_tc_lpad(d.l);
+    cuuint64_t dims[2] = {(cuuint64_t)(2 * (int64_t)d.M), (cuuint64_t)d.M};
+    cuuint64_t strides[1] = {(cuuint64_t)d.M * 8};
+    cuuint32_t box[2] = {32, 128};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(a, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d.R, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    cuuint64_t dims_b[2] = {(cuuint64_t)(2 * (int64_t)d.M), (cuuint64_t)nb};
+    cuuint32_t box_b[2] = {32, (cuuint32_t)nb};
+    r = enc(b, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d.Bsk, dims_b, strides, box_b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // The scan's B operand (rows x rowlen FP32, rowlen = 4 Mp), boxes of 256 rows x 32 floats.
 bool encode_bprep_tmap(const float* base, size_t rows, size_t rowlen, CUtensorMap* out) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
@@ -473,7 +501,8 @@ fm_status launch_cov(fm_ctx* c, bool tc, FrameDesc* dd, const char* tm_dev, int 
 // Uploads descriptors (+ grids) and returns device pointers.
 fm_status upload_descs(fm_ctx* c, const Plan& pl, std::vector<FrameDesc>& ds, const std::vector<CUtensorMap>& maps,
                        cudaStream_t s, FrameDesc** dd, GridDesc** dg,
-                       const std::vector<CUtensorMap>* group_maps = nullptr) {
+                       const std::vector<CUtensorMap>* group_maps = nullptr,
+                       const std::vector<CUtensorMap>* sketch_maps = nullptr) {
     const size_t bytes = pl.grid_off + sizeof(GridDesc) * pl.grids.size();
     char* host = nullptr;
     fm_status st = staging(c, bytes, &host);
@@ -483,6 +512,9 @@ fm_status upload_descs(fm_ctx* c, const Plan& pl, std::vector<FrameDesc>& ds, co
     if (group_maps && !group_maps->empty())
         memcpy(host + pl.tmap_off + sizeof(CUtensorMap) * ds.size(), group_maps->data(),
                sizeof(CUtensorMap) * group_maps->size());
+    if (sketch_maps && !sketch_maps->empty())  // [2n, 3n): R, [3n, 4n): B rows
+        memcpy(host + pl.tmap_off + sizeof(CUtensorMap) * 2 * ds.size(), sketch_maps->data(),
+               sizeof(CUtensorMap) * sketch_maps->size());
     std::vector<GridDesc> g = pl.grids;
     for (size_t i = 0; i < g.size(); ++i) g[i].qtab = reinterpret_cast<float2*>(c->arena + pl.qtab[i]);
     if (!g.empty()) memcpy(host + pl.grid_off, g.data(), sizeof(GridDesc) * g.size());
@@ -494,15 +526,22 @@ fm_status upload_descs(fm_ctx* c, const Plan& pl, std::vector<FrameDesc>& ds, co
 }
 
 // The fast-MUSIC chain from R (already formed) to U_s.
-fm_status run_subspace_chain(fm_ctx* c, FrameDesc* dd, int n, const Maxes& mx, cudaStream_t s) {
-    fm_status st = stage(c, kStSketch, s, [&] {
-        return fm::launch_sketch(dd, n, mx.M, mx.l, 0, mx.any_sampling, mx.any_projection, s);
-    });
+// tc_pass[p]: some frame takes the tensor-core sketch at pass p (sketch maps at
+// sk_maps: n maps over R, then n over the B rows).
+fm_status run_subspace_chain(fm_ctx* c, FrameDesc* dd, int n, const Maxes& mx, cudaStream_t s,
+                             const char* sk_maps = nullptr, const std::vector<char>* tc_pass = nullptr) {
+    auto sketch = [&](int p, bool gather, bool dense) {
+        cudaError_t e = fm::launch_sketch(dd, n, mx.M, mx.l, p, gather, dense, s);
+        if (e == cudaSuccess && sk_maps && tc_pass && (*tc_pass)[p])
+            e = fm::launch_sketch_tc(dd, n, mx.M, mx.l, p, sk_maps, sk_maps + sizeof(CUtensorMap) * (size_t)n, s);
+        return e;
+    };
+    fm_status st = stage(c, kStSketch, s, [&] { return sketch(0, mx.any_sampling, mx.any_projection); });
     if (st != FM_OK) return st;
     for (int p = 1; p <= mx.t; ++p) {
         st = stage(c, kStOrth, s, [&] { return fm::launch_orth(dd, n, mx.M, mx.l, p, s); });
         if (st != FM_OK) return st;
-        st = stage(c, kStSketch, s, [&] { return fm::launch_sketch(dd, n, mx.M, mx.l, p, false, true, s); });
+        st = stage(c, kStSketch, s, [&] { return sketch(p, false, true); });
         if (st != FM_OK) return st;
     }
     if (mx.any_refine) {  // V = orth(C), then C = X (X^H V) / T in FP32 (frames with refine only)
@@ -600,6 +639,7 @@ struct RunPrep {
     Maxes mx;
     bool cov_tc = false, scan_tc = false, scan_simt = true, any_repack = false;
     std::vector<char> group_tc;  // per scan group: runs on the tensor cores
+    std::vector<char> tc_pass;   // per sketch pass: some frame takes the tensor-core sketch
     FrameDesc* dd = nullptr;
     GridDesc* dg = nullptr;
 };
@@ -630,6 +670,10 @@ static fm_status prepare_run(fm_ctx* c, const fm_frame* frames, int n, cudaStrea
         d.idx = reinterpret_cast<int*>(c->arena + pl.idx[k]);
         d.Us = reinterpret_cast<float2*>(c->arena + pl.Us[k]);
         d.Y = pl.Y[k] != SIZE_MAX ? reinterpret_cast<float2*>(c->arena + pl.Y[k]) : nullptr;
+        if (pl.Bsk[k] != SIZE_MAX) {
+            d.Bsk = reinterpret_cast<float*>(c->arena + pl.Bsk[k]);
+            d.sketch_tc = 1;
+        }
         if (pl.Xpad[k] != SIZE_MAX && c->cov_path != FM_COV_SIMT) {
             d.Xin = d.X;
             d.ldx_in = d.ldx;
@@ -644,6 +688,19 @@ static fm_status prepare_run(fm_ctx* c, const fm_frame* frames, int n, cudaStrea
     std::vector<CUtensorMap> maps;
     st = choose_cov_path(c, ds, maps, &rp.cov_tc);
     if (st != FM_OK) return st;
+    // tensor-core sketch: maps over R and the B rows of every frame that takes it
+    std::vector<CUtensorMap> skmaps(2 * (size_t)n);
+    memset(skmaps.data(), 0, sizeof(CUtensorMap) * skmaps.size());
+    rp.tc_pass.assign(9, 0);
+    for (int k = 0; k < n; ++k) {
+        if (!ds[k].sketch_tc) continue;
+        if (!encode_sketch_tmaps(ds[k], &skmaps[k], &skmaps[n + k])) {
+            ds[k].sketch_tc = 0;  // the CUDA-core sketch takes every pass of this frame
+            continue;
+        }
+        for (int p = 0; p <= ds[k].t; ++p)
+            if (fm::sketch_on_tc(ds[k].method, ds[k].prec, ds[k].t, p)) rp.tc_pass[p] = 1;
+    }
     // scan: one batched tensor-core launch per scan group that fills at least a
     // quarter of the kernel's 512-row B tile (FM_COV_TC: every group), the CUDA-core
     // scan for the other frames, then the CUDA-core main-lobe recompute of the
@@ -669,7 +726,7 @@ static fm_status prepare_run(fm_ctx* c, const fm_frame* frames, int n, cudaStrea
     rp.scan_tc = n_tc > 0;
     rp.scan_simt = n_tc < n;
     c->last_scan_path = n_tc == n ? FM_COV_TC : (n_tc == 0 ? FM_COV_SIMT : FM_COV_AUTO);
-    st = upload_descs(c, pl, ds, maps, s, &rp.dd, &rp.dg, rp.scan_tc ? &gmaps : nullptr);
+    st = upload_descs(c, pl, ds, maps, s, &rp.dd, &rp.dg, rp.scan_tc ? &gmaps : nullptr, &skmaps);
     if (st != FM_OK) return st;
     rp.mx = maxes_of(ds);
     return FM_OK;
@@ -688,7 +745,8 @@ static fm_status enqueue_run(fm_ctx* c, const RunPrep& rp, cudaStream_t s) {
     }
     st = launch_cov(c, rp.cov_tc, dd, c->arena + pl.tmap_off, n, mx.M, s);
     if (st != FM_OK) return st;
-    st = run_subspace_chain(c, dd, n, mx, s);
+    st = run_subspace_chain(c, dd, n, mx, s, c->arena + pl.tmap_off + sizeof(CUtensorMap) * 2 * (size_t)n,
+                            &rp.tc_pass);
     if (st != FM_OK) return st;
     st = stage(c, kStScan, s, [&] {
         if (rp.scan_simt) {  // frames without a tensor-core group (the kernel skips the others)

@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(kThreads) sketch_dense_kernel(const FrameDesc*
     const int M = dp->M, l = dp->l;
     if (pass > dp->t) return;
     if (pass == 0 && dp->method != FM_RAND_PROJECTION) return;
+    if (dp->sketch_tc && sketch_on_tc(dp->method, dp->prec, dp->t, pass)) return;  // sketch_tc.cu takes it
     const int r0 = blockIdx.x * kRows;
     if (r0 >= M) return;
     const float2* __restrict__ R = dp->R;
