@@ -204,6 +204,14 @@ fm_status fm_run_subspace(fm_ctx* ctx, int frame, void* U, fm_stream stream);
  * outputs, twice). */
 fm_status fm_run_host(fm_ctx* ctx, const fm_frame* frames, int n_frames, fm_stream stream);
 
+/* fm_selftest_wait_timeout: self-test of failure detection (the paper has no
+ * counterpart).  Launches one warp that waits, with the bounded mbarrier wait of
+ * the tensor-core kernels, on a barrier that nothing arrives on; after limit_ms
+ * (converted to SM clocks at the device's maximum clock) the wait gives up, the
+ * kernel ORs the FM_ERR_TIMEOUT bit (1 << FM_ERR_TIMEOUT) into *status (device
+ * int) and returns normally, so the context stays usable.  limit_ms in (0, 1e4]. */
+fm_status fm_selftest_wait_timeout(fm_ctx* ctx, int* status, double limit_ms, fm_stream stream);
+
 /* ---- steps (uniform batches; each frame at a fixed stride) ------------------
  * fm_covariance (Eq. 2): R_b = X_b X_b^H / T for b < n_frames.  X_b = X +
  * b * x_frame_stride complex elements; R_b = R + b*M*M (complex64, full

@@ -78,6 +78,7 @@ _SIGS = {
     "fm_launch_count": (c_uint64, [c_void_p]),
     "fm_run_subspace": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "fm_run_host": (c_int, [c_void_p, POINTER(FmFrame), c_int, c_void_p]),
+    "fm_selftest_wait_timeout": (c_int, [c_void_p, c_void_p, c_double, c_void_p]),
     "fm_autotune": (c_int, [c_void_p, POINTER(FmFrame), c_int, c_void_p, c_int, POINTER(c_int), POINTER(c_int),
                             POINTER(c_float)]),
     "fm_graph_create": (c_int, [c_void_p, POINTER(FmFrame), c_int, POINTER(c_void_p)]),
@@ -201,6 +202,10 @@ def fm_graph_launch(graph, stream) -> int:
 
 def fm_graph_destroy(graph) -> int:
     return load().fm_graph_destroy(graph)
+
+
+def fm_selftest_wait_timeout(ctx, status, limit_ms, stream) -> int:
+    return load().fm_selftest_wait_timeout(ctx, status, limit_ms, stream)
 
 
 def fm_run_host(ctx, frames, stream) -> int:

@@ -196,6 +196,7 @@ cudaError_t launch_sketch(const FrameDesc* d, int n_frames, int max_M, int max_l
 cudaError_t launch_orth(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, cudaStream_t s);
 cudaError_t launch_final(const FrameDesc* d, int n_frames, int max_M, int max_l, cudaStream_t s);
 cudaError_t launch_refine(const FrameDesc* d, int n_frames, int max_M, int max_T, cudaStream_t s);
+cudaError_t launch_wait_timeout(int* status, long long limit_cycles, cudaStream_t s);
 cudaError_t launch_sketch_tc(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, const void* tmA,
                              const void* tmB, cudaStream_t s);
 cudaError_t launch_scan(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s);

@@ -1036,6 +1036,21 @@ fm_status fm_graph_destroy(fm_graph* g) {
     return FM_OK;
 }
 
+fm_status fm_selftest_wait_timeout(fm_ctx* c, int* status, double limit_ms, fm_stream stream) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (!status || !(limit_ms > 0.0) || limit_ms > 10000.0)
+        return fail(c, FM_ERR_INVALID_ARG, "fm_selftest_wait_timeout: status NULL or limit_ms not in (0, 1e4]");
+    fm_status st = set_device(c);
+    if (st != FM_OK) return st;
+    int khz = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaDeviceGetAttribute(clock rate)");
+    const long long cycles = (long long)(limit_ms * (double)khz);
+    st = stage(c, kStGrid, reinterpret_cast<cudaStream_t>(stream),
+               [&] { return fm::launch_wait_timeout(status, cycles, reinterpret_cast<cudaStream_t>(stream)); });
+    return st;
+}
+
 fm_status fm_run_subspace(fm_ctx* c, int frame, void* U, fm_stream stream) {
     if (!c) return FM_ERR_INVALID_ARG;
     if (!U || frame < 0 || frame >= (int)c->last_us.size() || std::get<0>(c->last_us[frame]) == SIZE_MAX)

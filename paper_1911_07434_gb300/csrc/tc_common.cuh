@@ -34,19 +34,24 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false (and *abort set) if the phase did not complete in time.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
+// Bounded wait: false (and *abort set) if the phase did not complete within
+// limit_cycles SM clocks (or another thread of the CTA gave up first).
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t* b, uint32_t parity, volatile int* abort,
+                                                long long limit_cycles) {
     if (mbar_test(b, parity)) return true;
     const long long t0 = clock64();
     while (true) {
         if (mbar_test(b, parity)) return true;
         if (*abort) return false;
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > limit_cycles) {
             *abort = 1;
             return false;
         }
         __nanosleep(64);
     }
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
+    return mbar_wait_limit(b, parity, abort, kWaitCycles);
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {

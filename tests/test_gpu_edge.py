@@ -171,3 +171,17 @@ def test_smallest_array_grid_and_snapshot_count(lib, ctx):
     assert int(b.n.item()) == 1 and int(b.idx[0].item()) == 0
     Pc = c.P.cpu().numpy()
     assert int(c.n.item()) == 1 and int(c.idx[0].item()) == int(np.argmax(Pc))
+
+
+def test_bounded_wait_reports_timeout_and_context_stays_usable(lib, ctx):
+    """Failure detection without a GPU fault: a wait on a barrier nothing arrives on gives
+    up after its limit, the status word carries FM_ERR_TIMEOUT, and the next frame runs."""
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx._check(lib.fm_selftest_wait_timeout(ctx.h, st.data_ptr(), 2.0, None), "fm_selftest_wait_timeout")
+    torch.cuda.synchronize()
+    assert int(st.item()) == 1 << lib.FM_ERR_TIMEOUT
+    fr = synth.small_frame()
+    one = One(lib, fr.X, fr.K, fr.l, fr.t, 2, fr.theta0, fr.step, fr.L)
+    ctx.run([one.f])
+    torch.cuda.synchronize()
+    assert int(one.st.item()) == 0 and int(one.n.item()) == fr.K
