@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cstdarg>
@@ -27,6 +28,9 @@ constexpr size_t kAlign = 256;
 inline size_t aup(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 enum Stage { kStGrid = 0, kStCov, kStSketch, kStOrth, kStFinal, kStScan, kStPeaks, kStRefine };
+// NVTX range names of the stages (visible in a timeline profiler; no cost without one)
+const char* const kStageName[FM_N_STAGES] = {"fm grid",  "fm covariance", "fm sketch", "fm orth",
+                                              "fm final", "fm scan",       "fm peaks",  "fm refine"};
 
 struct TimedEvent {
     int stage;
@@ -120,6 +124,10 @@ cudaEvent_t get_event(fm_ctx* c) {
 // Run one stage launch, bracketed by events when timing is on.
 template <typename F>
 fm_status stage(fm_ctx* c, int st, cudaStream_t s, F&& launch) {
+    nvtxRangePushA(kStageName[st]);
+    struct Pop {
+        ~Pop() { nvtxRangePop(); }
+    } pop;
     cudaEvent_t a = nullptr, b = nullptr;
     if (c->timing) {
         a = get_event(c);
