@@ -504,7 +504,8 @@ def main():
     ctx.set_timing(False)
     launches = ctx.launch_count() - launches0
     paths = {"covariance": "tensor" if ctx.last_cov_path() == binding.FM_COV_TC else "cuda-core",
-             "scan": {binding.FM_COV_TC: "tensor", binding.FM_COV_SIMT: "cuda-core"}.get(ctx.last_scan_path(), "mixed")}
+             "scan": {binding.FM_COV_TC: "tensor", binding.FM_COV_SIMT: "cuda-core"}.get(ctx.last_scan_path(), "mixed"),
+             "sketch": {binding.FM_COV_TC: "tensor", binding.FM_COV_SIMT: "cuda-core"}.get(ctx.last_sketch_path(), "mixed")}
     step_ms = [step_ev[k].elapsed_time(step_ev[k + 1]) for k in range(args.steps)]
     total_ms = step_ev[0].elapsed_time(step_ev[-1])
     stages = ctx.stage_times(reset=True)

@@ -88,6 +88,8 @@ _SIGS = {
     "fm_last_cov_path": (c_int, [c_void_p]),
     "fm_set_scan_path": (c_int, [c_void_p, c_int]),
     "fm_last_scan_path": (c_int, [c_void_p]),
+    "fm_set_sketch_path": (c_int, [c_void_p, c_int]),
+    "fm_last_sketch_path": (c_int, [c_void_p]),
     "fm_spectrum_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_double, POINTER(FmGrid), c_void_p, c_void_p]),
     "fm_serve_submit": (c_int, [c_void_p, POINTER(FmFrame), POINTER(c_uint64)]),
     "fm_serve_poll": (c_int, [c_void_p, c_uint64, POINTER(c_int)]),
@@ -235,6 +237,14 @@ def fm_set_scan_path(ctx, path) -> int:
 
 def fm_last_scan_path(ctx) -> int:
     return load().fm_last_scan_path(ctx)
+
+
+def fm_set_sketch_path(ctx, path) -> int:
+    return load().fm_set_sketch_path(ctx, path)
+
+
+def fm_last_sketch_path(ctx) -> int:
+    return load().fm_last_sketch_path(ctx)
 
 
 def fm_spectrum_noalloc(U, n_frames, M, ncols, d_wl, grid: FmGrid, P, stream) -> int:
@@ -416,6 +426,12 @@ class Context:
 
     def last_scan_path(self) -> int:
         return fm_last_scan_path(self.h)
+
+    def set_sketch_path(self, path: int):
+        self._check(fm_set_sketch_path(self.h, path), "fm_set_sketch_path")
+
+    def last_sketch_path(self) -> int:
+        return fm_last_sketch_path(self.h)
 
     def serve_submit(self, frame: FmFrame) -> int:
         st, t = fm_serve_submit(self.h, frame)

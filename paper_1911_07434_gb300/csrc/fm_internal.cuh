@@ -30,7 +30,8 @@ struct FrameDesc {
     float2* V;         // M x l  basis (power steps) / Q
     float2* Us;        // M x kpad (zero-padded)
     float2* Y;         // T x l  X^H V of the refinement step (refine only)
-    float* Bsk;        // 2 l_pad x 2M  B rows of the tensor-core sketch (sketch_tc only)
+    float* Bsk;        // B rows of the tensor-core sketch (sketch_tc only): 2 l_pad x 2M, or
+                       // 2 l_pad x sketch_split_rowlen(M) for a split pass
     int* idx;          // l sampled indices
     float2* qtab;      // L entries (q_hi, q_lo): q = 2 d_wl sin(theta_i), split for exact m*q_hi
     float* P;          // L
@@ -165,15 +166,15 @@ __device__ __forceinline__ void set_status(int* status, int code) {
     if (status) atomicOr(status, 1 << code);
 }
 
-// Sketch passes that run on the tensor cores (sketch_tc.cu): every pass of a frame in
-// TF32 / BF16 mode; in FP32 mode every pass but the last, whose product the final
-// solve reads (sampling has no product at pass 0).
-__host__ __device__ inline bool sketch_on_tc(int method, int prec, int t, int pass) {
-    if (pass == 0 && method != FM_RAND_PROJECTION) return false;
-    if (prec != FM_PREC_FP32) return true;
-    return pass < t;
-}
+// Sketch products on the tensor cores (sketch_tc.cu, for frames prepared for it): every
+// product R V (sampling has none at pass 0).  The last product of an FP32 frame, which
+// the final solve reads, takes three TF32 MMAs per FP32 product (sketch_split); the
+// other products take one.
+__host__ __device__ inline bool sketch_on_tc(int method, int pass) { return pass > 0 || method == FM_RAND_PROJECTION; }
+__host__ __device__ inline bool sketch_split(int prec, int t, int pass) { return prec == FM_PREC_FP32 && pass == t; }
 __host__ __device__ inline int sketch_tc_lpad(int l) { return (l + 7) / 8 * 8; }
+// Floats per B row of the split layout: ceil(2M / 16) chunks of [hi 16 | lo 16].
+__host__ __device__ inline int64_t sketch_split_rowlen(int M) { return 32 * (int64_t)((2 * M + 15) / 16); }
 
 // ---------------------------------------------------------- launch wrappers --
 // Kernel launches issued by the calling host thread (every launch site bumps it),
@@ -192,13 +193,15 @@ int scan_tc_ncp(int ncols);
 cudaError_t launch_covariance(const FrameDesc* d, int n_frames, int max_M, cudaStream_t s);
 cudaError_t launch_repack(const FrameDesc* d, int n_frames, int max_M, int max_T, cudaStream_t s);
 cudaError_t launch_sketch(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, bool any_gather,
-                          bool any_dense, cudaStream_t s);
+                          bool any_omega, bool any_dense, cudaStream_t s);
 cudaError_t launch_orth(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, cudaStream_t s);
 cudaError_t launch_final(const FrameDesc* d, int n_frames, int max_M, int max_l, cudaStream_t s);
 cudaError_t launch_refine(const FrameDesc* d, int n_frames, int max_M, int max_T, cudaStream_t s);
 cudaError_t launch_wait_timeout(int* status, long long limit_cycles, cudaStream_t s);
-cudaError_t launch_sketch_tc(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, const void* tmA,
-                             const void* tmB, cudaStream_t s);
+cudaError_t launch_sketch_tc(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, bool any_plain,
+                             bool any_split, const void* tmA, const void* tmB, const void* tmA_split,
+                             const void* tmB_split, cudaStream_t s);
+size_t sketch_tc_smem_bytes(int max_l, bool split);
 cudaError_t launch_scan(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s);
 cudaError_t launch_scan_fixup(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s);
 cudaError_t launch_peaks(const FrameDesc* d, int n_frames, int max_K, cudaStream_t s);

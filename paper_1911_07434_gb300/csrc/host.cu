@@ -61,6 +61,8 @@ struct fm_ctx {
     int last_cov_path = 0;
     int scan_path = FM_COV_AUTO;
     int last_scan_path = 0;
+    int sketch_path = FM_COV_AUTO;
+    int last_sketch_path = 0;
     // serving state
     struct Slot;
     std::vector<Slot*> slots;
@@ -277,10 +279,10 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
     size_t off = 0;
     pl.desc_off = off;
     off = aup(off + sizeof(FrameDesc) * (size_t)n);
-    // TMA tensor maps: per frame X (covariance); per scan group B; per frame R and the
-    // B rows of the tensor-core sketch
+    // TMA tensor maps: per frame X (covariance); per scan group B; per frame the R and
+    // B-row maps of the tensor-core sketch, one-MMA and split layouts
     pl.tmap_off = off;
-    if (need_R) off = aup(off + sizeof(CUtensorMap) * (4 * (size_t)n));
+    if (need_R) off = aup(off + sizeof(CUtensorMap) * (6 * (size_t)n));
     std::map<GridKey, int> gmap;
     pl.grid_of.assign(n, -1);
     if (need_grid) {
@@ -323,11 +325,12 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
         if (need_sketch) off = aup(off + sizeof(float2) * M * l);
         pl.idx.push_back(need_sketch ? off : SIZE_MAX);
         if (need_sketch) off = aup(off + sizeof(int) * l);
-        bool tcsk = false;  // some pass of this frame runs on the tensor-core sketch
-        for (int pass = 0; need_R && pass <= f[b].p.t; ++pass)
-            tcsk |= fm::sketch_on_tc(f[b].p.method, f[b].p.prec, f[b].p.t, pass);
-        pl.Bsk.push_back(tcsk ? off : SIZE_MAX);
-        if (tcsk) off = aup(off + sizeof(float) * 2 * (size_t)fm::sketch_tc_lpad((int)l) * 2 * M);
+        bool tcsk = false;  // some pass of this frame can run on the tensor-core sketch
+        for (int pass = 0; need_R && pass <= f[b].p.t; ++pass) tcsk |= fm::sketch_on_tc(f[b].p.method, pass);
+        pl.Bsk.push_back(tcsk ? off : SIZE_MAX);  // sized for the split layout (the larger)
+        if (tcsk)
+            off = aup(off + sizeof(float) * 2 * (size_t)fm::sketch_tc_lpad((int)l) *
+                                (size_t)fm::sketch_split_rowlen((int)M));
         const bool y = need_sketch && f[b].p.refine;  // X^H V of the refinement step
         pl.Y.push_back(y ? off : SIZE_MAX);
         if (y) off = aup(off + sizeof(float2) * (size_t)f[b].T * l);
@@ -449,9 +452,11 @@ bool encode_tmap(const FrameDesc& d, CUtensorMap* out) {
     return r == CUDA_SUCCESS;
 }
 
-// The tensor-core sketch: R viewed as M x 2M FP32 (boxes of 128 rows x 32 floats) and
-// its B rows (2 l_pad x 2M FP32, one box of all 2 l_pad rows x 32 floats).
-bool encode_sketch_tmaps(const FrameDesc& d, CUtensorMap* a, CUtensorMap* b) {
+// The tensor-core sketch: R viewed as M x 2M FP32 (boxes of 128 rows x 32 floats,
+// 128-byte swizzle) and its B rows (2 l_pad x 2M FP32, one box of all 2 l_pad rows x
+// 32 floats); for the split kernel, R in raw boxes of 128 rows x 16 floats (no
+// swizzle) and the split B rows (2 l_pad x sketch_split_rowlen(M), boxes of 32 floats).
+bool encode_sketch_tmaps(const FrameDesc& d, CUtensorMap* a, CUtensorMap* b, CUtensorMap* a2, CUtensorMap* b2) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
     if (!enc) return false;
     const int nb = 2 * fm::sketch_tc_lpad(d.l);
@@ -465,6 +470,16 @@ bool encode_sketch_tmaps(const FrameDesc& d, CUtensorMap* a, CUtensorMap* b) {
     cuuint64_t dims_b[2] = {(cuuint64_t)(2 * (int64_t)d.M), (cuuint64_t)nb};
     cuuint32_t box_b[2] = {32, (cuuint32_t)nb};
     r = enc(b, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d.Bsk, dims_b, strides, box_b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    cuuint32_t box_raw[2] = {16, 128};
+    r = enc(a2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d.R, dims, strides, box_raw, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    const int64_t rl = fm::sketch_split_rowlen(d.M);
+    cuuint64_t dims_s[2] = {(cuuint64_t)rl, (cuuint64_t)nb};
+    cuuint64_t strides_s[1] = {(cuuint64_t)rl * 4};
+    r = enc(b2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d.Bsk, dims_s, strides_s, box_b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -520,7 +535,7 @@ fm_status upload_descs(fm_ctx* c, const Plan& pl, std::vector<FrameDesc>& ds, co
     if (group_maps && !group_maps->empty())
         memcpy(host + pl.tmap_off + sizeof(CUtensorMap) * ds.size(), group_maps->data(),
                sizeof(CUtensorMap) * group_maps->size());
-    if (sketch_maps && !sketch_maps->empty())  // [2n, 3n): R, [3n, 4n): B rows
+    if (sketch_maps && !sketch_maps->empty())  // [2n, 6n): sketch R, B rows, raw R, split B rows
         memcpy(host + pl.tmap_off + sizeof(CUtensorMap) * 2 * ds.size(), sketch_maps->data(),
                sizeof(CUtensorMap) * sketch_maps->size());
     std::vector<GridDesc> g = pl.grids;
@@ -533,23 +548,33 @@ fm_status upload_descs(fm_ctx* c, const Plan& pl, std::vector<FrameDesc>& ds, co
     return FM_OK;
 }
 
+// Which kernels a sketch pass needs (bits of RunPrep::tc_pass).
+enum : char { kPassPlain = 1, kPassSplit = 2, kPassDense = 4 };
+
 // The fast-MUSIC chain from R (already formed) to U_s.
-// tc_pass[p]: some frame takes the tensor-core sketch at pass p (sketch maps at
-// sk_maps: n maps over R, then n over the B rows).
+// tc_pass[p]: the kPass* bits of sketch pass p; sk_maps: n maps over R, n over the
+// B rows, n over R in raw boxes, n over the split B rows.  Without them every
+// product runs on the CUDA cores.
 fm_status run_subspace_chain(fm_ctx* c, FrameDesc* dd, int n, const Maxes& mx, cudaStream_t s,
                              const char* sk_maps = nullptr, const std::vector<char>* tc_pass = nullptr) {
-    auto sketch = [&](int p, bool gather, bool dense) {
-        cudaError_t e = fm::launch_sketch(dd, n, mx.M, mx.l, p, gather, dense, s);
-        if (e == cudaSuccess && sk_maps && tc_pass && (*tc_pass)[p])
-            e = fm::launch_sketch_tc(dd, n, mx.M, mx.l, p, sk_maps, sk_maps + sizeof(CUtensorMap) * (size_t)n, s);
+    auto sketch = [&](int p) {
+        const bool tc = sk_maps && tc_pass;
+        const char bits = tc ? (*tc_pass)[p] : (char)((p > 0 || mx.any_projection) ? kPassDense : 0);
+        cudaError_t e = fm::launch_sketch(dd, n, mx.M, mx.l, p, p == 0 && mx.any_sampling,
+                                          p == 0 && mx.any_projection, (bits & kPassDense) != 0, s);
+        if (e == cudaSuccess && (bits & (kPassPlain | kPassSplit))) {
+            const size_t m = sizeof(CUtensorMap) * (size_t)n;
+            e = fm::launch_sketch_tc(dd, n, mx.M, mx.l, p, (bits & kPassPlain) != 0, (bits & kPassSplit) != 0, sk_maps,
+                                     sk_maps + m, sk_maps + 2 * m, sk_maps + 3 * m, s);
+        }
         return e;
     };
-    fm_status st = stage(c, kStSketch, s, [&] { return sketch(0, mx.any_sampling, mx.any_projection); });
+    fm_status st = stage(c, kStSketch, s, [&] { return sketch(0); });
     if (st != FM_OK) return st;
     for (int p = 1; p <= mx.t; ++p) {
         st = stage(c, kStOrth, s, [&] { return fm::launch_orth(dd, n, mx.M, mx.l, p, s); });
         if (st != FM_OK) return st;
-        st = stage(c, kStSketch, s, [&] { return sketch(p, false, true); });
+        st = stage(c, kStSketch, s, [&] { return sketch(p); });
         if (st != FM_OK) return st;
     }
     if (mx.any_refine) {  // V = orth(C), then C = X (X^H V) / T in FP32 (frames with refine only)
@@ -647,7 +672,7 @@ struct RunPrep {
     Maxes mx;
     bool cov_tc = false, scan_tc = false, scan_simt = true, any_repack = false;
     std::vector<char> group_tc;  // per scan group: runs on the tensor cores
-    std::vector<char> tc_pass;   // per sketch pass: some frame takes the tensor-core sketch
+    std::vector<char> tc_pass;   // per sketch pass: kPass* bits of the kernels it needs
     FrameDesc* dd = nullptr;
     GridDesc* dg = nullptr;
 };
@@ -678,7 +703,7 @@ static fm_status prepare_run(fm_ctx* c, const fm_frame* frames, int n, cudaStrea
         d.idx = reinterpret_cast<int*>(c->arena + pl.idx[k]);
         d.Us = reinterpret_cast<float2*>(c->arena + pl.Us[k]);
         d.Y = pl.Y[k] != SIZE_MAX ? reinterpret_cast<float2*>(c->arena + pl.Y[k]) : nullptr;
-        if (pl.Bsk[k] != SIZE_MAX) {
+        if (pl.Bsk[k] != SIZE_MAX && c->sketch_path != FM_COV_SIMT) {
             d.Bsk = reinterpret_cast<float*>(c->arena + pl.Bsk[k]);
             d.sketch_tc = 1;
         }
@@ -697,18 +722,29 @@ static fm_status prepare_run(fm_ctx* c, const fm_frame* frames, int n, cudaStrea
     st = choose_cov_path(c, ds, maps, &rp.cov_tc);
     if (st != FM_OK) return st;
     // tensor-core sketch: maps over R and the B rows of every frame that takes it
-    std::vector<CUtensorMap> skmaps(2 * (size_t)n);
+    std::vector<CUtensorMap> skmaps(4 * (size_t)n);
     memset(skmaps.data(), 0, sizeof(CUtensorMap) * skmaps.size());
     rp.tc_pass.assign(9, 0);
+    int n_sk_tc = 0, n_sk_any = 0;
     for (int k = 0; k < n; ++k) {
-        if (!ds[k].sketch_tc) continue;
-        if (!encode_sketch_tmaps(ds[k], &skmaps[k], &skmaps[n + k])) {
-            ds[k].sketch_tc = 0;  // the CUDA-core sketch takes every pass of this frame
-            continue;
+        FrameDesc& d = ds[k];
+        if (d.sketch_tc && !encode_sketch_tmaps(d, &skmaps[k], &skmaps[n + k], &skmaps[2 * n + k], &skmaps[3 * n + k]))
+            d.sketch_tc = 0;  // the CUDA-core sketch takes every pass of this frame
+        bool has_product = false;
+        for (int p = 0; p <= d.t; ++p) {
+            if (!fm::sketch_on_tc(d.method, p)) continue;  // sampling, pass 0: a gather
+            has_product = true;
+            if (!d.sketch_tc)
+                rp.tc_pass[p] |= kPassDense;
+            else
+                rp.tc_pass[p] |= fm::sketch_split(d.prec, d.t, p) ? kPassSplit : kPassPlain;
         }
-        for (int p = 0; p <= ds[k].t; ++p)
-            if (fm::sketch_on_tc(ds[k].method, ds[k].prec, ds[k].t, p)) rp.tc_pass[p] = 1;
+        n_sk_any += has_product;
+        n_sk_tc += has_product && d.sketch_tc;
     }
+    if (c->sketch_path == FM_COV_TC && n_sk_tc < n_sk_any)
+        return fail(c, FM_ERR_INVALID_ARG, "tensor-core sketch needs an even M (16-byte aligned rows of R)");
+    c->last_sketch_path = n_sk_tc == n_sk_any ? FM_COV_TC : (n_sk_tc == 0 ? FM_COV_SIMT : FM_COV_AUTO);
     // scan: one batched tensor-core launch per scan group that fills at least a
     // quarter of the kernel's 512-row B tile (FM_COV_TC: every group), the CUDA-core
     // scan for the other frames, then the CUDA-core main-lobe recompute of the
@@ -997,6 +1033,7 @@ fm_status fm_graph_create(fm_ctx* c, const fm_frame* frames, int n, fm_graph** o
     if (fm_create(&g->sub, c->budget, c->device) != FM_OK) return bail(fail(c, FM_ERR_CUDA, "fm_graph_create: context"));
     g->sub->cov_path = c->cov_path;
     g->sub->scan_path = c->scan_path;
+    g->sub->sketch_path = c->sketch_path;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamCreate"));
     RunPrep rp;
@@ -1324,6 +1361,16 @@ fm_status fm_set_scan_path(fm_ctx* c, int path) {
 
 int fm_last_scan_path(const fm_ctx* c) { return c ? c->last_scan_path : 0; }
 
+fm_status fm_set_sketch_path(fm_ctx* c, int path) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (path != FM_COV_AUTO && path != FM_COV_SIMT && path != FM_COV_TC)
+        return fail(c, FM_ERR_INVALID_ARG, "unknown sketch path %d", path);
+    c->sketch_path = path;
+    return FM_OK;
+}
+
+int fm_last_sketch_path(const fm_ctx* c) { return c ? c->last_sketch_path : 0; }
+
 uint64_t fm_launch_count(const fm_ctx* c) { return c ? c->launches + c->serve_launches : 0; }
 
 // ------------------------------------------------------------ serving ----
@@ -1377,6 +1424,7 @@ static void serve_progress(fm_ctx* c) {
             sl->sub->arena_stream = sl->stream;
             sl->sub->cov_path = c->cov_path;
             sl->sub->scan_path = c->scan_path;
+            sl->sub->sketch_path = c->sketch_path;
             c->slots.push_back(sl);
             pick = sl;
         }

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kThreads) sketch_dense_kernel(const FrameDesc*
     const int M = dp->M, l = dp->l;
     if (pass > dp->t) return;
     if (pass == 0 && dp->method != FM_RAND_PROJECTION) return;
-    if (dp->sketch_tc && sketch_on_tc(dp->method, dp->prec, dp->t, pass)) return;  // sketch_tc.cu takes it
+    if (dp->sketch_tc && sketch_on_tc(dp->method, pass)) return;  // sketch_tc.cu takes it
     const int r0 = blockIdx.x * kRows;
     if (r0 >= M) return;
     const float2* __restrict__ R = dp->R;
@@ -187,7 +187,7 @@ cudaError_t launch_dense(const FrameDesc* d, int n_frames, int max_M, int max_l,
 }  // namespace
 
 cudaError_t launch_sketch(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, bool any_gather,
-                          bool any_dense, cudaStream_t s) {
+                          bool any_omega, bool any_dense, cudaStream_t s) {
     if (pass == 0 && any_gather) {
         const size_t gsm = sizeof(int) * (size_t)(max_M + max_l);
         count_launch();
@@ -195,13 +195,13 @@ cudaError_t launch_sketch(const FrameDesc* d, int n_frames, int max_M, int max_l
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (!any_dense) return cudaSuccess;
-    if (pass == 0) {
+    if (pass == 0 && any_omega) {
         count_launch();
         omega_kernel<<<dim3((max_M * max_l + 255) / 256, n_frames), 256, 0, s>>>(d);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    if (!any_dense) return cudaSuccess;
     const int nq = (max_l + kColG - 1) / kColG;
     if (nq <= 1) return launch_dense<1>(d, n_frames, max_M, max_l, pass, s);
     if (nq <= 2) return launch_dense<2>(d, n_frames, max_M, max_l, pass, s);

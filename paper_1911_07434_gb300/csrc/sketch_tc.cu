@@ -1,23 +1,28 @@
-// sketch_tc.cu -- the sketch product C = R V (Sec. III, Alg. 1 / Alg. 2, Eq. 11) on the
-// 5th-generation tensor cores with TF32 operands and FP32 accumulation.
+// sketch_tc.cu -- the sketch products C = R V (Sec. III, Alg. 1 / Alg. 2, Eq. 11) on
+// the 5th-generation tensor cores, FP32 accumulation.
 //
 // Real formulation on interleaved complex rows: a row of R is read as 2M FP32
 // values [Rr_0, Ri_0, Rr_1, Ri_1, ...], and every column j of V becomes two B rows
 //   [Vr_0, -Vi_0, Vr_1, -Vi_1, ...] -> Re C[., j],   [Vi_0, Vr_0, Vi_1, Vr_1, ...] -> Im C[., j],
-// so one real GEMM D = R_rows B^T (K = 2M, N = 2 l_pad) gives C with no operand
-// conversion: R streams from HBM by TMA straight into the 128-byte-swizzled
-// K-major layout the MMA reads (the tensor core takes the TF32 part of each FP32
-// value), and the B rows come from sketch_bprep_kernel (rounded to TF32).
+// so one real GEMM D = R_rows B^T (K = 2M, N = 2 l_pad) gives C.
 //
-// Which passes run here (sketch_on_tc): every pass of a frame in TF32 / BF16 mode,
-// and in FP32 mode every pass but the last (pass 0 = R Omega when power steps
-// follow, and the power steps before the last one): those products only select the
-// subspace that the next power step refines, while the final solve reads the last
-// product, which stays FP32 (sketch.cu).
+// Two kernels (sketch_bprep_kernel writes the B rows of both):
+// * sketch_tc_kernel, TF32 operands, one MMA per product: R streams from HBM by
+//   TMA straight into the 128-byte-swizzled K-major layout the MMA reads (the tensor
+//   core takes the TF32 part of each FP32 value), B rows rounded to TF32.  It takes
+//   every product of a TF32 / BF16 frame and the products of an FP32 frame before
+//   its last power step, which only choose the subspace the next step refines.
+// * sketch_split_kernel, FP32 accuracy, three TF32 MMAs per product (hi*hi + hi*lo
+//   + lo*hi, as the covariance does): the last product of an FP32 frame, which the
+//   final solve reads.  R arrives raw (128 rows x 16 FP32 per chunk); four converter
+//   warps split it into [hi 16 | lo 16] TF32 rows of the swizzled A tile, and the B
+//   rows come pre-split in the same [hi 16 | lo 16] chunk layout.
 //
-// One CTA per 128 rows of R of one frame: warp 0 issues TMA loads (4-stage ring),
-// warp 1 allocates TMEM and issues the MMAs (one thread), warps 2-5 run the
-// epilogue.  Every mbarrier wait is bounded and records FM_ERR_TIMEOUT on expiry.
+// One CTA per 128 rows of R of one frame: warp 0 issues TMA loads (ring of stages),
+// warp 1 allocates TMEM and issues the MMAs (one thread), warps 2-5 convert (split
+// kernel) and run the epilogue.  Shared memory is sized for the launch's largest l
+// so that two CTAs fit on an SM.  Every mbarrier wait is bounded and records
+// FM_ERR_TIMEOUT on expiry.
 #include "tc_common.cuh"
 
 namespace fm {
@@ -26,64 +31,256 @@ namespace {
 using namespace tc;
 
 constexpr int kRows = 128;
-constexpr int kStageA = kRows * 128;   // 16 KB: 128 rows x 32 FP32 (16 complex)
-constexpr int kMaxNB = 2 * kLMax;      // B rows (2 l_pad <= 96)
-constexpr int kStageB = kMaxNB * 128;  // 12 KB
-constexpr int kStage = kStageA + kStageB;
-constexpr int kNStages = 4;
+constexpr int kTileA = kRows * 128;    // 16 KB: 128 rows x 128 B (32 FP32, or [hi 16 | lo 16] TF32)
+constexpr int kRawA = kRows * 64;      // 8 KB: 128 raw rows x 16 FP32 (split kernel)
 constexpr int kThreads = 192;
-constexpr int kTiles = kNStages * kStage;
-constexpr int kSmemBytes = kTiles + 1024 + 256;
+constexpr int kSmemPerCta = 113 * 1024;  // two CTAs per SM (228 KB, 1 KB reserved per CTA)
+constexpr int kSmemExtra = 1024 + 256;   // 1024-B alignment slack + barriers
 constexpr uint32_t kTmemCols = 128;
 
-__global__ void sketch_bprep_kernel(const FrameDesc* __restrict__ descs, int pass, int max_M) {
+// Ring geometry for B tiles of nb_max rows (nb_max = 2 l_pad of the launch's largest l).
+__host__ __device__ constexpr int plain_stage(int nb_max) { return kTileA + nb_max * 128; }
+__host__ __device__ constexpr int plain_nstages(int nb_max) {
+    return 4 * plain_stage(nb_max) + kSmemExtra <= kSmemPerCta ? 4 : 3;
+}
+__host__ __device__ constexpr int split_stage(int nb_max) { return kTileA + nb_max * 128 + kRawA; }
+constexpr int kSplitStages = 3;
+static_assert(kSplitStages * split_stage(2 * kLMax) + kSmemExtra <= kSmemPerCta, "split ring too large");
+static_assert(plain_nstages(2 * kLMax) * plain_stage(2 * kLMax) + kSmemExtra <= kSmemPerCta, "ring too large");
+
+// B rows of pass `pass`, element (j, m) per thread.  Plain layout (2 l_pad rows x 2M):
+// TF32-rounded [Vr, -Vi] and [Vi, Vr] rows.  Split layout (2 l_pad rows x 32 ceil(2M/16)):
+// chunk c of 16 values stored as [hi 16 | lo 16], hi = rn_tf32(v), lo = rn_tf32(v - hi);
+// m runs over M rounded up to 8 so the last chunk's padding is written as zeros.
+__global__ void sketch_bprep_kernel(const FrameDesc* __restrict__ descs, int pass) {
     const FrameDesc* dp = descs + blockIdx.y;
-    if (!dp->sketch_tc || !sketch_on_tc(dp->method, dp->prec, dp->t, pass)) return;
+    if (!dp->sketch_tc || pass > dp->t || !sketch_on_tc(dp->method, pass)) return;
     const int M = dp->M, l = dp->l, lp = sketch_tc_lpad(l);
-    const int64_t rowlen = 2 * (int64_t)M;
+    const bool split = sketch_split(dp->prec, dp->t, pass);
+    const int Mq = split ? (M + 7) / 8 * 8 : M;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;  // (j, m)
-    if (e >= lp * M) return;
-    const int j = e / M, m = e % M;
+    if (e >= lp * Mq) return;
+    const int j = e / Mq, m = e % Mq;
     float2 v = make_float2(0.f, 0.f);
-    if (j < l) v = dp->V[(int64_t)m * l + j];
-    float* re = dp->Bsk + (2 * (int64_t)j) * rowlen;
-    float* im = re + rowlen;
-    re[2 * m] = __uint_as_float(tf32_rn(v.x));
-    re[2 * m + 1] = __uint_as_float(tf32_rn(-v.y));
-    im[2 * m] = __uint_as_float(tf32_rn(v.y));
-    im[2 * m + 1] = __uint_as_float(tf32_rn(v.x));
-    (void)max_M;
+    if (j < l && m < M) v = dp->V[(int64_t)m * l + j];
+    const float val[4] = {v.x, -v.y, v.y, v.x};  // re row (2m, 2m+1), im row (2m, 2m+1)
+    if (!split) {
+        const int64_t rowlen = 2 * (int64_t)M;
+        float* re = dp->Bsk + (2 * (int64_t)j) * rowlen;
+        float* im = re + rowlen;
+        re[2 * m] = __uint_as_float(tf32_rn(val[0]));
+        re[2 * m + 1] = __uint_as_float(tf32_rn(val[1]));
+        im[2 * m] = __uint_as_float(tf32_rn(val[2]));
+        im[2 * m + 1] = __uint_as_float(tf32_rn(val[3]));
+        return;
+    }
+    const int64_t rowlen = sketch_split_rowlen(M);
+    const int f = 2 * m, c = f >> 4, w = f & 15;  // chunk c, position w (even) of the value pair
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float* row = dp->Bsk + (2 * (int64_t)j + h) * rowlen + 32 * (int64_t)c;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float x = val[2 * h + u];
+            const uint32_t hi = tf32_rn(x);
+            row[w + u] = __uint_as_float(hi);
+            row[16 + w + u] = __uint_as_float(tf32_rn(x - __uint_as_float(hi)));
+        }
+    }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+struct Ring {
+    uint64_t* full;   // [ns] TMA (+ converters) -> MMA
+    uint64_t* empty;  // [ns] MMA -> TMA
+    uint64_t* raw;    // [ns] raw A landed (split kernel)
+    uint64_t* acc_full;
+    uint32_t* tmem_slot;
+    volatile int* abort_flag;
+};
+
+__device__ __forceinline__ Ring ring_at(unsigned char* p, int ns) {
+    Ring r;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(p);
+    r.full = bars;
+    r.empty = bars + ns;
+    r.raw = bars + 2 * ns;
+    r.acc_full = bars + 3 * ns;
+    r.tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * ns + 1);
+    r.abort_flag = reinterpret_cast<volatile int*>(bars + 3 * ns + 2);
+    return r;
+}
+
+// Epilogue of warps 2-5: TMEM lane quadrant warp % 4 = rows 32 q + lane of the tile;
+// accumulator column 2j = Re C[., j], 2j + 1 = Im C[., j].
+__device__ __forceinline__ void store_c(const FrameDesc* dp, const Ring& rg, uint32_t tmem, int r0, int nb, int warp,
+                                        int lane) {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(rg.acc_full, 0u, rg.abort_flag));
+    tc_fence_after();
+    if (ok) {
+        const int M = dp->M, l = dp->l;
+        const int q = warp & 3;
+        const int gr = r0 + 32 * q + lane;
+        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+        float2* __restrict__ C = dp->C;
+        for (int c0 = 0; c0 < nb; c0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(tl + c0, v);
+            tmem_wait_ld();
+            if (gr >= M) continue;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = c0 / 2 + u;
+                if (j < l) C[(int64_t)gr * l + j] = make_float2(__uint_as_float(v[2 * u]), __uint_as_float(v[2 * u + 1]));
+            }
+        }
+    }
+    tc_fence_before();
+}
+
+__device__ __forceinline__ uint32_t tmem_setup(const Ring& rg, int ns, const CUtensorMap* ta, const CUtensorMap* tb,
+                                               int full_count) {
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ns; ++s) {
+            mbar_init(&rg.full[s], (uint32_t)full_count);
+            mbar_init(&rg.empty[s], 1);
+            mbar_init(&rg.raw[s], 1);
+        }
+        mbar_init(rg.acc_full, 1);
+        *rg.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(ta)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tb)) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(rg.tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    return *rg.tmem_slot;
+}
+
+__device__ __forceinline__ void tmem_teardown(const FrameDesc* dp, const Ring& rg, uint32_t tmem) {
+    __syncthreads();
+    if (*rg.abort_flag && threadIdx.x == 0) set_status(dp->status, FM_ERR_TIMEOUT);
+    if ((threadIdx.x >> 5) == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
     sketch_tc_kernel(const FrameDesc* __restrict__ descs, const CUtensorMap* __restrict__ tmA,
-                     const CUtensorMap* __restrict__ tmB, int pass) {
+                     const CUtensorMap* __restrict__ tmB, int pass, int nb_max) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(base + kTiles);
-    uint64_t* full = bars;                  // [kNStages] TMA -> MMA
-    uint64_t* empty = bars + kNStages;      // [kNStages] MMA -> TMA
-    uint64_t* acc_full = bars + 2 * kNStages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kNStages + 1);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * kNStages + 2);
-
+    const int ns = plain_nstages(nb_max), stage = plain_stage(nb_max);
     const FrameDesc* dp = descs + blockIdx.y;
-    if (!dp->sketch_tc || !sketch_on_tc(dp->method, dp->prec, dp->t, pass)) return;
-    const int M = dp->M, l = dp->l, lp = sketch_tc_lpad(l), nb = 2 * lp;
+    // frames whose last product is done (pass > t) keep their C
+    if (!dp->sketch_tc || pass > dp->t || !sketch_on_tc(dp->method, pass) || sketch_split(dp->prec, dp->t, pass))
+        return;
+    const int M = dp->M, nb = 2 * sketch_tc_lpad(dp->l);
     const int r0 = blockIdx.x * kRows;
     if (r0 >= M) return;
     const int nstages = (2 * M + 31) / 32;
     const CUtensorMap* ta = tmA + blockIdx.y;
     const CUtensorMap* tb = tmB + blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Ring rg = ring_at(base + ns * stage, ns);
+    const uint32_t tmem = tmem_setup(rg, ns, ta, tb, 1);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)kTileA + (uint32_t)nb * 128u;
+            for (int s = 0; s < nstages; ++s) {
+                const int slot = s % ns;
+                if (!mbar_wait(&rg.empty[slot], ((uint32_t)(s / ns) & 1u) ^ 1u, rg.abort_flag)) break;
+                unsigned char* dst = base + slot * stage;
+                mbar_expect_tx(&rg.full[slot], bytes);
+                tma_load_2d(dst, ta, s * 32, r0, &rg.full[slot]);
+                tma_load_2d(dst + kTileA, tb, s * 32, 0, &rg.full[slot]);
+            }
+            for (int s = max(0, nstages - ns); s < nstages; ++s)
+                mbar_wait(&rg.full[s % ns], (uint32_t)(s / ns) & 1u, rg.abort_flag);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(128, (uint32_t)nb);
+            for (int s = 0; s < nstages; ++s) {
+                const int slot = s % ns;
+                if (!mbar_wait(&rg.full[slot], (uint32_t)(s / ns) & 1u, rg.abort_flag)) break;
+                tc_fence_after();
+                const uint32_t a = sa(base + slot * stage), b = a + kTileA;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)  // 32 values per row = four K = 8 steps of 32 bytes
+                    mma_tf32(tmem, desc_sw128(a + 32 * kk), desc_sw128(b + 32 * kk), idesc, (s > 0 || kk > 0) ? 1u : 0u);
+                mma_commit(&rg.empty[slot]);
+            }
+            mma_commit(rg.acc_full);
+            mbar_wait(rg.acc_full, 0u, rg.abort_flag);
+        }
+    } else {
+        store_c(dp, rg, tmem, r0, nb, warp, lane);
+    }
+    tmem_teardown(dp, rg, tmem);
+}
+
+// Split kernel, two-level sum: the MMAs of each group of kGroup chunks accumulate in
+// one of two TMEM buffers (columns 0 and 128), and warps 2-5 add every finished group
+// into FP32 registers, as the CUDA-core sketch sums per chunk and then across chunks.
+// A single accumulator over all 6 M / 16 MMAs of a row would carry the tensor core's
+// accumulation error of every step (measured: 2.4x the projector error at M = 1024).
+constexpr int kGroup = 8;                 // chunks per group (48 MMAs)
+constexpr int kDrainLag = 2;              // drain a group once conversion is this far past it
+static_assert(kDrainLag <= kGroup + 1, "the MMA waits for group g - 2 before group g");
+constexpr uint32_t kSplitTmemCols = 256;  // two accumulators of up to 128 columns
+
+template <int NB>
+__global__ void __launch_bounds__(kThreads, 2)
+    sketch_split_kernel(const FrameDesc* __restrict__ descs, const CUtensorMap* __restrict__ tmA,
+                        const CUtensorMap* __restrict__ tmB, int pass) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    constexpr int ns = kSplitStages;
+    constexpr int stage = split_stage(NB);
+    const FrameDesc* dp = descs + blockIdx.y;
+    if (!dp->sketch_tc || !sketch_on_tc(dp->method, pass) || !sketch_split(dp->prec, dp->t, pass)) return;
+    const int M = dp->M, l = dp->l, nb = 2 * sketch_tc_lpad(l);
+    const int r0 = blockIdx.x * kRows;
+    if (r0 >= M) return;
+    const int nchunks = (2 * M + 15) / 16;  // 16 FP32 of K per chunk
+    const int ngroups = (nchunks + kGroup - 1) / kGroup;
+    const CUtensorMap* ta = tmA + blockIdx.y;
+    const CUtensorMap* tb = tmB + blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + ns * stage);
+    uint64_t* full = bars;                // [ns] B rows landed + 128 converter arrivals -> MMA
+    uint64_t* empty = bars + ns;          // [ns] MMA -> TMA
+    uint64_t* rawb = bars + 2 * ns;       // [ns] raw A landed -> converters
+    uint64_t* acc_ready = bars + 3 * ns;  // [2] group committed -> drain
+    uint64_t* acc_free = bars + 3 * ns + 2;  // [2] group drained (128 arrivals) -> MMA
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * ns + 4);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 3 * ns + 5);
+    // stage layout: [A tile 16 KB | B rows NB x 128 B | raw A 8 KB]
+    constexpr int b_off = kTileA, raw_off = kTileA + NB * 128;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kNStages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+        for (int i = 0; i < ns; ++i) {
+            mbar_init(&full[i], 1 + 128);  // the producer's expect_tx arrival + one per converter thread
+            mbar_init(&empty[i], 1);
+            mbar_init(&rawb[i], 1);
         }
-        mbar_init(acc_full, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&acc_ready[i], 1);
+            mbar_init(&acc_free[i], 128);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(ta)) : "memory");
@@ -91,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(tmem_slot)),
-                     "r"(kTmemCols)
+                     "r"(kSplitTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -102,81 +299,175 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            const uint32_t bytes = (uint32_t)kStageA + (uint32_t)nb * 128u;
-            for (int s = 0; s < nstages; ++s) {
-                const int slot = s % kNStages;
-                if (!mbar_wait(&empty[slot], ((uint32_t)(s / kNStages) & 1u) ^ 1u, abort_flag)) break;
-                unsigned char* dst = base + slot * kStage;
-                mbar_expect_tx(&full[slot], bytes);
-                tma_load_2d(dst, ta, s * 32, r0, &full[slot]);
-                tma_load_2d(dst + kStageA, tb, s * 32, 0, &full[slot]);
+            for (int s = 0; s < nchunks; ++s) {
+                const int slot = s % ns;
+                if (!mbar_wait(&empty[slot], ((uint32_t)(s / ns) & 1u) ^ 1u, abort_flag)) break;
+                unsigned char* st = base + slot * stage;
+                mbar_expect_tx(&rawb[slot], (uint32_t)kRawA);
+                tma_load_2d(st + raw_off, ta, s * 16, r0, &rawb[slot]);
+                mbar_expect_tx(&full[slot], (uint32_t)nb * 128u);
+                tma_load_2d(st + b_off, tb, s * 32, 0, &full[slot]);
             }
-            for (int s = max(0, nstages - kNStages); s < nstages; ++s)
-                mbar_wait(&full[s % kNStages], (uint32_t)(s / kNStages) & 1u, abort_flag);
+            for (int s = max(0, nchunks - ns); s < nchunks; ++s) {
+                mbar_wait(&rawb[s % ns], (uint32_t)(s / ns) & 1u, abort_flag);
+                mbar_wait(&full[s % ns], (uint32_t)(s / ns) & 1u, abort_flag);
+            }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = idesc_tf32(128, (uint32_t)nb);
-            for (int s = 0; s < nstages; ++s) {
-                const int slot = s % kNStages;
-                if (!mbar_wait(&full[slot], (uint32_t)(s / kNStages) & 1u, abort_flag)) break;
+            for (int s = 0; s < nchunks; ++s) {
+                const int slot = s % ns, g = s / kGroup, buf = g & 1, sg = s % kGroup;
+                const uint32_t d = tmem + 128u * (uint32_t)buf;
+                if (sg == 0 && g >= 2) {  // buffer buf still holds group g - 2 until it is drained
+                    if (!mbar_wait(&acc_free[buf], (uint32_t)((g >> 1) + 1) & 1u, abort_flag)) break;
+                    tc_fence_after();
+                }
+                if (!mbar_wait(&full[slot], (uint32_t)(s / ns) & 1u, abort_flag)) break;
                 tc_fence_after();
-                const uint32_t a = sa(base + slot * kStage), b = a + kStageA;
+                const uint32_t a = sa(base + slot * stage), b = a + b_off;
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)  // 32 values per row = four K = 8 steps of 32 bytes
-                    mma_tf32(tmem, desc_sw128(a + 32 * kk), desc_sw128(b + 32 * kk), idesc, (s > 0 || kk > 0) ? 1u : 0u);
+                for (int kk = 0; kk < 2; ++kk) {  // 16 values per chunk = two K = 8 steps
+                    const uint64_t a_hi = desc_sw128(a + 32 * kk), a_lo = desc_sw128(a + 64 + 32 * kk);
+                    const uint64_t b_hi = desc_sw128(b + 32 * kk), b_lo = desc_sw128(b + 64 + 32 * kk);
+                    mma_tf32(d, a_hi, b_hi, idesc, (sg > 0 || kk > 0) ? 1u : 0u);
+                    mma_tf32(d, a_hi, b_lo, idesc, 1u);
+                    mma_tf32(d, a_lo, b_hi, idesc, 1u);
+                }
                 mma_commit(&empty[slot]);
+                if (sg == kGroup - 1 || s == nchunks - 1) mma_commit(&acc_ready[buf]);
             }
-            mma_commit(acc_full);
-            mbar_wait(acc_full, 0u, abort_flag);
+            // all MMAs retired before dealloc: the last group's commit tracks every earlier MMA
+            mbar_wait(&acc_ready[(ngroups - 1) & 1], (uint32_t)((ngroups - 1) >> 1) & 1u, abort_flag);
         }
     } else {
-        // epilogue: warps 2-5, TMEM lane quadrant warp % 4 = rows 32 q + lane
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full, 0u, abort_flag));
-        tc_fence_after();
-        if (ok) {
-            const int q = warp & 3;
-            const int row = 32 * q + lane;
-            const int gr = r0 + row;
-            const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
-            float2* __restrict__ C = dp->C;
-            for (int c0 = 0; c0 < nb; c0 += 16) {
-                uint32_t v[16];
-                tmem_ld16(tl + c0, v);
-                tmem_wait_ld();
-                if (gr >= M) continue;
+        // converters + two-level sum.  Conversion: raw chunk (128 rows x 64 B, float4 i =
+        // row i >> 2, quarter i & 3) -> A tile row with hi in 16-byte chunk q, lo in 4 + q
+        // (128-byte swizzle).  Sum: thread (warp % 4, lane) owns row 32 (warp % 4) + lane
+        // (its TMEM lane quadrant) and keeps the row's NB accumulator columns in registers.
+        const int c = threadIdx.x - 64;
+        const int q4 = warp & 3;
+        const uint32_t tl = tmem + ((uint32_t)(32 * q4) << 16);
+        float sum[NB];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int j = c0 / 2 + u;
-                    if (j < l) C[(int64_t)gr * l + j] = make_float2(__uint_as_float(v[2 * u]), __uint_as_float(v[2 * u + 1]));
-                }
+        for (int j = 0; j < NB; ++j) sum[j] = 0.f;
+        bool ok = true;
+        int gd = 0;  // next group to drain
+        auto drain = [&](int g) {
+            const int buf = g & 1;
+            ok = ok && __all_sync(0xffffffffu, mbar_wait(&acc_ready[buf], (uint32_t)(g >> 1) & 1u, abort_flag));
+            if (!ok) return;
+            tc_fence_after();
+#pragma unroll
+            for (int c0 = 0; c0 < NB; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(tl + 128u * (uint32_t)buf + (uint32_t)c0, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int u = 0; u < 16; ++u) sum[c0 + u] += __uint_as_float(v[u]);
             }
+            tc_fence_before();
+            mbar_arrive(&acc_free[buf]);
+        };
+        for (int s = 0; s < nchunks && ok; ++s) {
+            const int slot = s % ns;
+            if (!__all_sync(0xffffffffu, mbar_wait(&rawb[slot], (uint32_t)(s / ns) & 1u, abort_flag))) {
+                ok = false;
+                break;
+            }
+            unsigned char* st = base + slot * stage;
+            const unsigned char* raw = st + raw_off;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = c + 128 * u;
+                const int r = i >> 2, q = i & 3;
+                const float4 v = *reinterpret_cast<const float4*>(raw + 16 * i);
+                uint4 hi, lo;
+                hi.x = tf32_rn(v.x);
+                hi.y = tf32_rn(v.y);
+                hi.z = tf32_rn(v.z);
+                hi.w = tf32_rn(v.w);
+                lo.x = tf32_rn(v.x - __uint_as_float(hi.x));
+                lo.y = tf32_rn(v.y - __uint_as_float(hi.y));
+                lo.z = tf32_rn(v.z - __uint_as_float(hi.z));
+                lo.w = tf32_rn(v.w - __uint_as_float(hi.w));
+                *reinterpret_cast<uint4*>(st + swz(r, q)) = hi;
+                *reinterpret_cast<uint4*>(st + swz(r, 4 + q)) = lo;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&full[slot]);
+            // groups whose chunks are all converted and kDrainLag behind are drained here
+            while (ok && gd < ngroups && min(gd * kGroup + kGroup - 1, nchunks - 1) + kDrainLag <= s) drain(gd++);
         }
-        tc_fence_before();
+        while (ok && gd < ngroups) drain(gd++);
+        const int gr = r0 + 32 * q4 + lane;
+        if (ok && gr < M) {
+            float2* __restrict__ C = dp->C + (int64_t)gr * l;
+#pragma unroll
+            for (int j = 0; j < NB / 2; ++j)
+                if (j < l) C[j] = make_float2(sum[2 * j], sum[2 * j + 1]);
+        }
     }
     __syncthreads();
     if (*abort_flag && threadIdx.x == 0) set_status(dp->status, FM_ERR_TIMEOUT);
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kSplitTmemCols)
+                     : "memory");
     }
 }
 
 }  // namespace
 
-cudaError_t launch_sketch_tc(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, const void* tmA,
-                             const void* tmB, cudaStream_t s) {
-    const int lp = sketch_tc_lpad(max_l);
+template <int NB>
+cudaError_t launch_split(const FrameDesc* d, dim3 grid, int pass, const void* tmA, const void* tmB, cudaStream_t s) {
+    static_assert(NB % 16 == 0 && NB <= 2 * kLMax, "B rows: 2 l_pad");
+    const int smem = kSplitStages * split_stage(NB) + kSmemExtra;
+    cudaError_t e = cudaFuncSetAttribute(sketch_split_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
     count_launch();
-    sketch_bprep_kernel<<<dim3((unsigned)((lp * max_M + 255) / 256), n_frames), 256, 0, s>>>(d, pass, max_M);
+    sketch_split_kernel<NB><<<grid, kThreads, smem, s>>>(d, reinterpret_cast<const CUtensorMap*>(tmA),
+                                                         reinterpret_cast<const CUtensorMap*>(tmB), pass);
+    return cudaGetLastError();
+}
+
+size_t sketch_tc_smem_bytes(int max_l, bool split) {
+    const int nb_max = 2 * sketch_tc_lpad(max_l);
+    return split ? (size_t)kSplitStages * split_stage(nb_max) + kSmemExtra
+                 : (size_t)plain_nstages(nb_max) * plain_stage(nb_max) + kSmemExtra;
+}
+
+cudaError_t launch_sketch_tc(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, bool any_plain,
+                             bool any_split, const void* tmA, const void* tmB, const void* tmA_split,
+                             const void* tmB_split, cudaStream_t s) {
+    const int lp = sketch_tc_lpad(max_l), nb_max = 2 * lp;
+    const int Mq = any_split ? (max_M + 7) / 8 * 8 : max_M;
+    count_launch();
+    sketch_bprep_kernel<<<dim3((unsigned)((lp * Mq + 255) / 256), n_frames), 256, 0, s>>>(d, pass);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (e != cudaSuccess) return e;
-    count_launch();
-    sketch_tc_kernel<<<dim3((unsigned)((max_M + kRows - 1) / kRows), n_frames), kThreads, kSmemBytes, s>>>(
-        d, reinterpret_cast<const CUtensorMap*>(tmA), reinterpret_cast<const CUtensorMap*>(tmB), pass);
-    return cudaGetLastError();
+    const dim3 grid((unsigned)((max_M + kRows - 1) / kRows), n_frames);
+    if (any_plain) {
+        const int smem = (int)sketch_tc_smem_bytes(max_l, false);
+        e = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        count_launch();
+        sketch_tc_kernel<<<grid, kThreads, smem, s>>>(d, reinterpret_cast<const CUtensorMap*>(tmA),
+                                                      reinterpret_cast<const CUtensorMap*>(tmB), pass, nb_max);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (any_split) {
+        switch (nb_max) {  // 2 l_pad, l_pad a multiple of 8 up to kLMax
+            case 16: return launch_split<16>(d, grid, pass, tmA_split, tmB_split, s);
+            case 32: return launch_split<32>(d, grid, pass, tmA_split, tmB_split, s);
+            case 48: return launch_split<48>(d, grid, pass, tmA_split, tmB_split, s);
+            case 64: return launch_split<64>(d, grid, pass, tmA_split, tmB_split, s);
+            case 80: return launch_split<80>(d, grid, pass, tmA_split, tmB_split, s);
+            default: return launch_split<96>(d, grid, pass, tmA_split, tmB_split, s);
+        }
+    }
+    return e;
 }
 
 }  // namespace fm
