@@ -6,7 +6,7 @@
 //                     or H = C(I, :) = R(I, I) (sampling, t = 0)       (Eq. 8)
 //         C = Q R_c                         (QR in place of SVD(C): Q = U_c Z, Z unitary)
 //         B = R_c W R_c^H, W = H^+          (rank restriction)
-//         eig(B) = U_B L_B U_B^H, U_s = Q U_B[:, :ncols]
+//         eig(B) = U_B L_B U_B^H, U_s = Q U_B[:, :ncols] = C (R_c^{-1} U_B[:, :ncols])
 //
 // One thread-block cluster per frame: CTA r of the cluster keeps rows
 // [r*Mr, (r+1)*Mr) of C (and V) in shared memory for the whole kernel, so
@@ -16,19 +16,21 @@
 // CTA holds the same l x l matrix and runs the same l x l algorithms.
 //
 // Precision (no FP64 -- its rate on GB300 is a small fraction of FP32):
-//   - QR: CholeskyQR2.  Pass 1 accumulates C^H C in double-float arithmetic
-//     (FP32 products split exactly with an FMA, sums kept as hi + lo pairs),
-//     factors and inverts it in double-float, and applies the inverse with
-//     double-float accumulation, so the pass survives cond(C) up to ~1/u_fp32
-//     without amplifying rounding into the range of Q.  Pass 2 (cond ~ 1) is
-//     double-float for the final Q (its orthonormality feeds U_s directly) and
-//     FP32 for the power-step basis V.
+//   - QR: R_c from C^H C accumulated in double-float arithmetic (FP32 products split
+//     exactly with an FMA, sums kept as hi + lo pairs), factored and inverted in
+//     double-float, which survives cond(C) up to ~1/u_fp32.  ORTH applies R_c^{-1}
+//     to the rows (double-float accumulation) to give the power-step basis V.
+//     FINAL never forms Q: it keeps R_c^{-1} in double-float and forms U_s =
+//     C (R_c^{-1} U_B) at the end with double-float sums, so U_s^H U_s = U_B^H U_B
+//     up to double-float rounding and the one FP32 rounding of U_s (the
+//     orthonormality a second CholeskyQR pass would give, without the two M-long
+//     passes over the rows).
 //   - W: H is Hermitian positive definite in exact arithmetic, so
 //     B = R_c H^{-1} R_c^H = F F^H with F = R_c R_h^{-1}, H = R_h^H R_h (FP32
 //     Cholesky).  If the Cholesky breaks down, W is the eigenvalue pseudo-inverse
 //     of H (pivots with |lambda| <= l eps max|lambda| dropped).
-//   - eig(B): two-sided complex Jacobi in FP32, round-robin parallel ordering,
-//     relative stopping test |b_pq| <= tol sqrt(|b_pp b_qq|), followed by one
+//   - eig(B): one-sided Jacobi SVD of F in FP32 (two-sided complex Jacobi on B for
+//     the pseudo-inverse branch), round-robin parallel ordering, followed by one
 //     Rayleigh-Ritz correction of the leading eigenspace with double-float sums
 //     (see refine_subspace) and a double-float re-orthonormalisation of the
 //     selected eigenvectors.
@@ -124,7 +126,7 @@ __device__ __forceinline__ zd zneg(zd a) { return zd{dd_neg(a.re), dd_neg(a.im)}
 
 // ------------------------------------------------------------------ layout --
 struct Sm {
-    float2* Cs;    // Mr x l   rows of C (Q after the QR)
+    float2* Cs;    // Mr x l   rows of C (ORTH: Q after the QR)
     float2* Vs;    // Mr x l   rows of V (FINAL, until H is formed)
     float4* Gd;    // l x l    double-float Gram / Cholesky factor   (aliases Vs)
     float4* Xd;    // l x l    double-float inverse                  (aliases Vs)
@@ -504,47 +506,6 @@ __device__ void apply_upper_d(float2* A, int rows, int l, const float4* X) {
     __syncthreads();
 }
 
-// dst rows (rows x ncols, row stride ld) = A rows (rows x l) * T (l x ncols, row
-// stride ldt), FP32; upper: T upper triangular.  dst may equal A (row-local).
-__device__ void apply_f(const float2* A, float2* dst, int rows, int l, const float2* T, int ldt, int ncols, int ld,
-                        bool upper) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int r = warp; r < rows; r += kWarps) {
-        float2 out[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int c = lane + 32 * h;
-            out[h] = make_float2(0.f, 0.f);
-            if (c >= ncols) continue;
-            const int kend = upper ? c : l - 1;
-            float2 acc = make_float2(0.f, 0.f);
-            for (int k = 0; k <= kend; ++k) cfma(acc, A[r * l + k], T[k * ldt + c]);
-            out[h] = acc;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int c = lane + 32 * h;
-            if (c < ncols) dst[(int64_t)r * ld + c] = out[h];
-        }
-        __syncwarp();
-    }
-    __syncthreads();
-}
-
-// Rc <- R * Rc for upper triangular R, Rc (tmp: scratch).
-__device__ void upper_mul(const float2* R, float2* Rc, float2* tmp, int l) {
-    for (int e = threadIdx.x; e < l * l; e += kThreads) {
-        const int i = e / l, j = e % l;
-        float2 s = make_float2(0.f, 0.f);
-        for (int k = i; k <= j; ++k) cfma(s, R[i * l + k], Rc[k * l + j]);
-        tmp[e] = s;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < l * l; e += kThreads) Rc[e] = tmp[e];
-    __syncthreads();
-}
-
 // One double-float CholeskyQR pass on the cluster-distributed rows A (in place):
 // G = A^H A (double-float sums), G = R^H R (double-float Cholesky),
 // A <- A R^{-1} (double-float accumulation).  Rk receives R rounded to FP32.
@@ -558,28 +519,6 @@ __device__ bool cholqr_pass_d(cg::cluster_group& cl, float2* A, int rows, int l,
         Rk[e] = make_float2(g.x + g.y, g.z + g.w);
     }
     apply_upper_d(A, rows, l, sm.Xd);
-    return ok;
-}
-
-// CholeskyQR2 of the cluster-distributed rows A (rows x l, in place -> Q); Rc
-// receives the R factor (the same on every CTA).  Pass 1 is double-float (it
-// must survive cond(A) up to ~1/u_fp32); pass 2 starts from cond ~ 1 and is
-// double-float as well when exact_pass2 (then ||Q^H Q - I|| is set by the final
-// FP32 rounding of Q alone, not by an FP32 Gram summed over M rows), FP32
-// otherwise.  Returns false on a Cholesky breakdown.
-__device__ bool cholqr2(cg::cluster_group& cl, float2* A, int rows, int l, const Sm& sm, bool exact_pass2) {
-    bool ok = cholqr_pass_d(cl, A, rows, l, sm, sm.Rc);
-    if (exact_pass2) {
-        ok = cholqr_pass_d(cl, A, rows, l, sm, sm.Z) && ok;  // Z: R2 (scratch until the eigensolve)
-        upper_mul(sm.Z, sm.Rc, sm.T, l);
-        return ok;
-    }
-    gram_part_f(A, A, rows, l, true, reinterpret_cast<float2*>(sm.part));
-    reduce_f(cl, reinterpret_cast<float2*>(sm.part), sm.Gf, l, true);
-    ok = chol_f(sm.Gf, l, sm, 0x1p-20f) && ok;
-    trinv_f(sm.Gf, sm.Xf, l);
-    apply_f(A, A, rows, l, sm.Xf, l, l, l, true);
-    upper_mul(sm.Gf, sm.Rc, sm.T, l);
     return ok;
 }
 
@@ -956,8 +895,8 @@ __device__ void refine_subspace(const Sm& sm, int l, int nc) {
 
 // Re-orthonormalise the k columns of Z (n x k, row stride k, every CTA holds the
 // same copy) by one double-float CholeskyQR pass: the accumulated FP32 Jacobi
-// rotations leave them orthonormal only to ~sqrt(rounds) u, and U_s = Q Z
-// inherits that; the pass keeps their span.
+// rotations leave them orthonormal only to ~sqrt(rounds) u, and U_s inherits
+// that; the pass keeps their span.  Scratch: part and Gd (Xd is left alone).
 __device__ void orthonormalize_cols_d(float2* Z, int n, int k, const Sm& sm) {
     gram_part_d(Z, n, k, sm.part);
     __syncthreads();
@@ -971,8 +910,44 @@ __device__ void orthonormalize_cols_d(float2* Z, int n, int k, const Sm& sm) {
     }
     __syncthreads();
     chol_d(sm.Gd, k, sm);
-    trinv_d(sm.Gd, sm.Xd, k, sm);
-    apply_upper_d(Z, n, k, sm.Xd);
+    trinv_d(sm.Gd, sm.part, k, sm);
+    apply_upper_d(Z, n, k, sm.part);
+}
+
+// Zt = X W (l x nc, double-float, row stride nc) for X upper triangular l x l in
+// double-float and W l x nc FP32 (row stride nc).
+__device__ void upper_times_d(const float4* X, const float2* W, float4* Zt, int l, int nc) {
+    for (int e = threadIdx.x; e < l * nc; e += kThreads) {
+        const int i = e / nc, k = e % nc;
+        zd s{df{0.f, 0.f}, df{0.f, 0.f}};
+        for (int m = i; m < l; ++m) {
+            const float2 w = W[m * nc + k];
+            s = zadd(s, zmul(zload(X[i * l + m]), zd{df{w.x, 0.f}, df{w.y, 0.f}}));
+        }
+        Zt[e] = zpack(s);
+    }
+    __syncthreads();
+}
+
+// dst rows (rows x nc, row stride ld, global) = A rows (rows x l, FP32) * Zt (l x nc,
+// double-float): FP32 products split exactly, double-float sums, one final rounding.
+__device__ void apply_d(const float2* A, float2* __restrict__ dst, int rows, int l, const float4* Zt, int nc,
+                        int64_t ld) {
+    for (int e = threadIdx.x; e < rows * nc; e += kThreads) {
+        const int r = e / nc, c = e % nc;
+        df re{0.f, 0.f}, im{0.f, 0.f};
+        for (int k = 0; k < l; ++k) {
+            const float2 a = A[r * l + k];
+            const float4 x = Zt[k * nc + c];  // (re.hi, re.lo, im.hi, im.lo)
+            dd_acc(re, a.x, x.x);
+            dd_acc(re, -a.y, x.z);
+            dd_acc(im, a.x, x.z);
+            dd_acc(im, a.y, x.x);
+            re.lo = fmaf(a.x, x.y, fmaf(-a.y, x.w, re.lo));
+            im.lo = fmaf(a.x, x.w, fmaf(a.y, x.y, im.lo));
+        }
+        dst[(int64_t)r * ld + c] = make_float2(re.hi + re.lo, im.hi + im.lo);
+    }
 }
 
 // ---------------------------------------------------------------- kernel ----
@@ -997,7 +972,7 @@ __global__ void __launch_bounds__(kThreads, 3) small_cluster_kernel(const FrameD
         // The power step only needs a well-conditioned basis of range(C): the core
         // matrix H = V^H C and the Nystrom form C H^+ C^H do not depend on which
         // basis V is.  One double-float CholeskyQR pass leaves V orthonormal to about
-        // u cond(C) (cond(V) ~ 1), so the second pass of CholeskyQR2 is not taken.
+        // u cond(C) (cond(V) ~ 1), so a second CholeskyQR pass is not taken.
         __syncthreads();
         const bool ok = cholqr_pass_d(cl, sm.Cs, rows, l, sm, sm.Rc);
         store_rows(sm.Cs, dp->V, r0, rows, l);
@@ -1035,8 +1010,20 @@ __global__ void __launch_bounds__(kThreads, 3) small_cluster_kernel(const FrameD
     }
     __syncthreads();
 
-    // C = Q R_c (Q in place of the C rows); V rows are dead from here on
-    bool ok = cholqr2(cl, sm.Cs, rows, l, sm, true);
+    // C = Q R_c with Q = C R_c^{-1} left implicit: R_c from the double-float Gram of C
+    // (Cholesky, pivot floor as in CholeskyQR), X = R_c^{-1} kept in Xd until U_s = C (X W)
+    // is formed at the end for the ncols selected eigenvectors W only.  U_s^H U_s =
+    // W^H X^H (C^H C) X W = W^H W up to double-float rounding, so one pass gives the
+    // orthonormality of a second CholeskyQR pass without forming Q.  V rows are dead
+    // from here on.
+    gram_part_d(sm.Cs, rows, l, sm.part);
+    reduce_d(cl, sm.part, sm.Gd, l);
+    bool ok = chol_d(sm.Gd, l, sm);
+    trinv_d(sm.Gd, sm.Xd, l, sm);
+    for (int e = threadIdx.x; e < l * l; e += kThreads) {
+        const float4 g = sm.Gd[e];
+        sm.Rc[e] = make_float2(g.x + g.y, g.z + g.w);
+    }
 
     // B = R_c H^+ R_c^H
     for (int e = threadIdx.x; e < l * l; e += kThreads) sm.Gf[e] = sm.H[e];
@@ -1109,8 +1096,9 @@ __global__ void __launch_bounds__(kThreads, 3) small_cluster_kernel(const FrameD
     const int nc_out = dp->ncols;
     refine_subspace(sm, l, nc_out);
     orthonormalize_cols_d(sm.Rc, l, nc_out, sm);
-    // U_s rows = Q rows * U_B[:, :ncols] (refined, in Rc: l x ncols)
-    apply_f(sm.Cs, dp->Us + (int64_t)r0 * dp->kpad, rows, l, sm.Rc, nc_out, nc_out, dp->kpad, false);
+    // U_s rows = C rows * (R_c^{-1} U_B[:, :ncols]) (U_B refined, in Rc: l x ncols)
+    upper_times_d(sm.Xd, sm.Rc, sm.Gd, l, nc_out);
+    apply_d(sm.Cs, dp->Us + (int64_t)r0 * dp->kpad, rows, l, sm.Gd, nc_out, dp->kpad);
     if (rank == 0 && threadIdx.x == 0 && (s2 < 0 || !ok)) set_status(dp->status, FM_ERR_NO_CONVERGENCE);
 }
 
