@@ -689,7 +689,14 @@ __device__ int jacobi(float2* A, float2* Z, float* w, int* perm, int n, const Sm
 __device__ int eig_onesided(const float2* Frm, float2* Wc, float2* Z, float* w, int* perm, int n, const Sm& sm) {
     const int ne = n + (n & 1), np = ne / 2, nr = ne - 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int kPW = 3;  // pairs per warp: np <= 24 = 3 x kWarps
+    // one pair per half-warp and slot: 16 lanes hold the pair's two columns (up to kE
+    // entries each) and reduce over 16 lanes; every half-warp evaluates the same
+    // rotation formulas for its own pair
+    constexpr int kHW = kThreads / 16;
+    constexpr int kPH = (kLMax / 2 + kHW - 1) / kHW;  // pair slots per half-warp (2 at l = 48)
+    constexpr int kE = (kLMax + 15) / 16;             // column entries per lane (3 at l = 48)
+    const int hw = threadIdx.x >> 4, hl = threadIdx.x & 15;
+    const int nslot = (np + kHW - 1) / kHW, nent = (n + 15) / 16;  // block-uniform
     for (int e = threadIdx.x; e < n * n; e += kThreads) {
         const int i = e / n, p = e % n;
         Wc[p * n + i] = Frm[e];
@@ -710,24 +717,27 @@ __device__ int eig_onesided(const float2* Frm, float2* Wc, float2* Z, float* w, 
             if (lane == 0) w[k] = a;
         }
         // round-robin positions, advanced by one each round
-        int ia[kPW], ib[kPW];
+        int ia[kPH], ib[kPH];
 #pragma unroll
-        for (int j = 0; j < kPW; ++j) {
-            const int k = warp + kWarps * j;
+        for (int j = 0; j < kPH; ++j) {
+            const int k = hw + kHW * j;
             ia[j] = (k == 0 || nr == 0) ? 0 : (k - 1) % nr;
             ib[j] = nr ? (ne - 2 - k + nr) % nr : 0;
         }
+        float ratio = 0.f;  // this thread's largest pair ratio in the sweep
+        bool any = false;
         __syncthreads();
         for (int r = 0; r < nr; ++r) {
-            float2* fp[kPW];
-            float2* fq[kPW];
-            float2 xp[kPW][2], xq[kPW][2];
-            float g[kPW][2], na[kPW], nb[kPW];
-            int pi[kPW], qi[kPW];
-            bool live[kPW];
+            float2* fp[kPH];
+            float2* fq[kPH];
+            float2 xp[kPH][kE], xq[kPH][kE];
+            float g[kPH][2], na[kPH], nb[kPH];
+            int pi[kPH], qi[kPH];
+            bool live[kPH];
 #pragma unroll
-            for (int j = 0; j < kPW; ++j) {
-                const int k = warp + kWarps * j;
+            for (int j = 0; j < kPH; ++j) {
+                if (j >= nslot) break;
+                const int k = hw + kHW * j;
                 const int pa = (k == 0) ? 0 : 1 + ia[j];
                 const int pb = 1 + ib[j];
                 const int p = min(pa, pb), q = max(pa, pb);
@@ -740,8 +750,9 @@ __device__ int eig_onesided(const float2* Frm, float2* Wc, float2* Z, float* w, 
                 nb[j] = live[j] ? w[q] : 1.f;
                 float gr = 0.f, gi = 0.f;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int i = lane + 32 * h;
+                for (int h = 0; h < kE; ++h) {
+                    if (h >= nent) break;
+                    const int i = hl + 16 * h;
                     xp[j][h] = (live[j] && i < n) ? fp[j][i] : make_float2(0.f, 0.f);
                     xq[j][h] = (live[j] && i < n) ? fq[j][i] : make_float2(0.f, 0.f);
                     gr = fmaf(xp[j][h].x, xq[j][h].x, fmaf(xp[j][h].y, xq[j][h].y, gr));  // conj(f_p) f_q
@@ -753,24 +764,22 @@ __device__ int eig_onesided(const float2* Frm, float2* Wc, float2* Z, float* w, 
                 if (++ib[j] == nr) ib[j] = 0;
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
+            for (int o = 8; o > 0; o >>= 1)
 #pragma unroll
-                for (int j = 0; j < kPW; ++j) {
-                    g[j][0] += __shfl_xor_sync(0xffffffffu, g[j][0], o);
-                    g[j][1] += __shfl_xor_sync(0xffffffffu, g[j][1], o);
+                for (int j = 0; j < kPH; ++j) {
+                    if (j >= nslot) break;
+                    g[j][0] += __shfl_xor_sync(0xffffffffu, g[j][0], o, 16);
+                    g[j][1] += __shfl_xor_sync(0xffffffffu, g[j][1], o, 16);
                 }
-            // rotation parameters of every pair in straight-line code (identity where the
-            // pair is already orthogonal to the tolerance), then the column updates
-            bool any = false;
-            float ratio = 0.f;
-            float cc[kPW], ss[kPW], tm[kPW];
-            float2 u10[kPW], u11[kPW];
+            // rotation of every pair (identity where the pair is already orthogonal to the
+            // tolerance), then the column updates
 #pragma unroll
-            for (int j = 0; j < kPW; ++j) {
+            for (int j = 0; j < kPH; ++j) {
+                if (j >= nslot) break;
                 const float gr = g[j][0], gi = g[j][1];
                 const float mag2 = fmaf(gr, gr, gi * gi);
                 const float ab = na[j] * nb[j];
-                const bool rot = live[j] && mag2 > FLT_MIN && mag2 > tol2 * ab;  // warp-uniform
+                const bool rot = live[j] && mag2 > FLT_MIN && mag2 > tol2 * ab;  // uniform over the half-warp
                 if (live[j] && ab > 0.f) ratio = fmaxf(ratio, __fdividef(mag2, ab));
                 const float inv = rsqrtf(fmaxf(mag2, FLT_MIN));
                 const float mag = mag2 * inv;
@@ -779,37 +788,33 @@ __device__ int eig_onesided(const float2* Frm, float2* Wc, float2* Z, float* w, 
                 const float q1 = fmaf(tau, tau, 1.f);
                 const float t = rot ? copysignf(__fdividef(1.f, fabsf(tau) + q1 * rsqrtf(q1)), tau) : 0.f;
                 const float c = rsqrtf(fmaf(t, t, 1.f));
-                cc[j] = c;
-                ss[j] = t * c;
-                tm[j] = t * mag;
+                const float sn = t * c;
                 // F <- F U, U = [[c, s], [-s conj(ph), c conj(ph)]], ph = g / |g| (1 if no rotation)
                 const float2 phc = rot ? make_float2(gr * inv, -gi * inv) : make_float2(1.f, 0.f);
-                u10[j] = cscale(phc, -ss[j]);
-                u11[j] = cscale(phc, c);
+                const float2 u10 = cscale(phc, -sn), u11 = cscale(phc, c);
                 any |= rot;
-            }
-#pragma unroll
-            for (int j = 0; j < kPW; ++j) {
                 if (!live[j]) continue;  // a dead pair's pointers alias column 0 of a live one
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int i = lane + 32 * h;
+                for (int h = 0; h < kE; ++h) {
+                    if (h >= nent) break;
+                    const int i = hl + 16 * h;
                     if (i < n) {
-                        fp[j][i] = cadd(cscale(xp[j][h], cc[j]), cmul(xq[j][h], u10[j]));
-                        fq[j][i] = cadd(cscale(xp[j][h], ss[j]), cmul(xq[j][h], u11[j]));
+                        fp[j][i] = cadd(cscale(xp[j][h], c), cmul(xq[j][h], u10));
+                        fq[j][i] = cadd(cscale(xp[j][h], sn), cmul(xq[j][h], u11));
                     }
                 }
-                if (lane == 0) {
-                    w[pi[j]] = na[j] - tm[j];
-                    w[qi[j]] = nb[j] + tm[j];
+                if (hl == 0) {
+                    w[pi[j]] = na[j] - t * mag;
+                    w[qi[j]] = nb[j] + t * mag;
                 }
-            }
-            if (lane == 0) {
-                if (any) sm.flags[sweep] = 1;
-                atomicMax(sweep_max, __float_as_int(ratio));
             }
             __syncthreads();
         }
+        if (hl == 0) {
+            if (any) sm.flags[sweep] = 1;
+            atomicMax(sweep_max, __float_as_int(ratio));
+        }
+        __syncthreads();
         // converged: no rotation in this sweep, or every pair of it was within 1e-4 before its
         // rotation, so after it (quadratic convergence) within 1e-8 < the tolerance
         if (!sm.flags[sweep] || __int_as_float(*sweep_max) < 1e-8f) {
