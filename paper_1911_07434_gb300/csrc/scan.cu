@@ -92,12 +92,38 @@ __device__ __forceinline__ void store_spectrum(const FrameDesc* dp, int i, int M
 // angle away from every source).  The tensor-core accumulator's error grows like
 // u M ||U_s^H a||^2 and is biased, while the sums here stay far below that, so
 // near a peak, where M - ||U_s^H a||^2 cancels, the CUDA-core value is kept.
-// The flagged angles of a 256-angle chunk are compacted; each is shared by
-// fix_groups(KP) warps, warp g taking the m0 residue class g (all lanes of a warp
-// read the same U_s row: a shared-memory broadcast), and the partial c_k are
-// summed in shared memory in a fixed order.  Chunks with no flagged angle exit
-// before loading U_s.
+// The flagged angles of kFixChunks 256-angle chunks are compacted (one U_s load
+// serves them all); each is shared by fix_groups(KP) warps, warp g taking the m0
+// residue class g (all lanes of a warp read the same U_s row: a shared-memory
+// broadcast), and the partial c_k are summed in shared memory in a fixed order.
+// CTAs with no flagged angle exit before loading U_s.
 __host__ __device__ constexpr int fix_groups(int kp) { return kp <= 8 ? 8 : (kp == 16 ? 4 : 2); }
+constexpr int kFixChunks = 4;
+
+// Usm (M x KP, zero-padded columns) <- U_s (M x kp): float4 copies issued four at a
+// time when the layouts agree, else element by element.
+template <int KP>
+__device__ __forceinline__ void load_us(const float2* __restrict__ Us, float2* Usm, int M, int kp) {
+    if (kp == KP && (reinterpret_cast<uintptr_t>(Us) & 15) == 0) {
+        const int n4 = M * KP / 2;  // KP is even
+        const float4* __restrict__ src = reinterpret_cast<const float4*>(Us);
+        float4* dst = reinterpret_cast<float4*>(Usm);
+        for (int e = threadIdx.x; e < n4; e += 4 * kThreads) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (e + u * kThreads < n4) v[u] = src[e + u * kThreads];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (e + u * kThreads < n4) dst[e + u * kThreads] = v[u];
+        }
+        return;
+    }
+    for (int e = threadIdx.x; e < M * KP; e += kThreads) {
+        const int m = e / KP, k = e % KP;
+        Usm[e] = (k < kp) ? Us[(int64_t)m * kp + k] : make_float2(0.f, 0.f);
+    }
+}
 
 template <int KP, int NB, bool FIXUP>
 __global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restrict__ descs) {
@@ -106,36 +132,47 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restr
     const FrameDesc* dp = descs + blockIdx.y;
     if ((dp->scan_tc != 0) != FIXUP) return;  // the plain scan skips tensor-core frames, the fixup the others
     const int M = dp->M, L = dp->L, kp = dp->kpad;
-    const int i0 = blockIdx.x * kThreads;
+    const int i0 = blockIdx.x * kThreads * (FIXUP ? kFixChunks : 1);
     if (i0 >= L) return;
     const float2* __restrict__ Us = dp->Us;
     constexpr int kWarps = kThreads / 32;
-    __shared__ int s_list[FIXUP ? kThreads : 1];
-    __shared__ int s_wcount[kWarps];
+    constexpr int kCh = FIXUP ? kFixChunks : 1;
+    __shared__ int s_list[FIXUP ? kThreads * kFixChunks : 1];
+    __shared__ int s_wcount[kCh * kWarps];
     __shared__ float2 s_red[FIXUP ? kThreads * 8 : 1];  // [warp][k % 8][lane]
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int n_fix = 0;
     if (FIXUP) {
-        const int ii = i0 + threadIdx.x;
-        bool f = false;
-        if (ii < L) f = !(1.0f / dp->P[ii] >= (float)(M - 4 * dp->ncols));  // NaN is recomputed too
-        const unsigned bal = __ballot_sync(0xffffffffu, f);
-        if (lane == 0) s_wcount[w] = __popc(bal);
-        __syncthreads();
+        // flags of the CTA's kFixChunks chunks (loads issued together), compacted in
+        // (chunk, warp, lane) order
+        const float thr = (float)(M - 4 * dp->ncols);
+        float pv[kFixChunks];
 #pragma unroll
-        for (int j = 0; j < kWarps; ++j) n_fix += s_wcount[j];
+        for (int c = 0; c < kFixChunks; ++c) {
+            const int ii = i0 + c * kThreads + threadIdx.x;
+            pv[c] = ii < L ? dp->P[ii] : 0.f;
+        }
+        unsigned bal[kFixChunks];
+#pragma unroll
+        for (int c = 0; c < kFixChunks; ++c) {
+            const int ii = i0 + c * kThreads + threadIdx.x;
+            const bool f = ii < L && !(1.0f / pv[c] >= thr);  // NaN is recomputed too
+            bal[c] = __ballot_sync(0xffffffffu, f);
+            if (lane == 0) s_wcount[c * kWarps + w] = __popc(bal[c]);
+        }
+        __syncthreads();
+        for (int j = 0; j < kCh * kWarps; ++j) n_fix += s_wcount[j];
         if (n_fix == 0) return;
-        if (f) {
+#pragma unroll
+        for (int c = 0; c < kFixChunks; ++c) {
+            if (!((bal[c] >> lane) & 1u)) continue;
             int base = 0;
-            for (int j = 0; j < w; ++j) base += s_wcount[j];
-            s_list[base + __popc(bal & ((1u << lane) - 1u))] = ii;
+            for (int j = 0; j < c * kWarps + w; ++j) base += s_wcount[j];
+            s_list[base + __popc(bal[c] & ((1u << lane) - 1u))] = i0 + c * kThreads + threadIdx.x;
         }
         // s_list is ordered by the __syncthreads after the U_s load
     }
-    for (int e = threadIdx.x; e < M * KP; e += kThreads) {
-        const int m = e / KP, k = e % KP;
-        Usm[e] = (k < kp) ? Us[(int64_t)m * kp + k] : make_float2(0.f, 0.f);
-    }
+    load_us<KP>(Us, Usm, M, kp);
     __syncthreads();
     float2 acc[KP];
     if (!FIXUP) {
@@ -188,14 +225,16 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restr
 template <int KP, int NB, bool FIXUP>
 cudaError_t launch_kp(const FrameDesc* d, int n_frames, int max_L, int max_M, cudaStream_t s) {
     const size_t smem = sizeof(float2) * (size_t)max_M * KP;
-    const size_t static_smem = FIXUP ? sizeof(int) * (kThreads + kThreads / 32) + sizeof(float2) * kThreads * 8
+    const size_t static_smem = FIXUP ? sizeof(int) * (kThreads * kFixChunks + kFixChunks * kThreads / 32) +
+                                           sizeof(float2) * kThreads * 8
                                      : sizeof(int) * (1 + kThreads / 32) + sizeof(float2);
     if (smem + static_smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(scan_kernel<KP, NB, FIXUP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    dim3 grid((max_L + kThreads - 1) / kThreads, n_frames);
+    const int per_cta = kThreads * (FIXUP ? kFixChunks : 1);
+    dim3 grid((max_L + per_cta - 1) / per_cta, n_frames);
     count_launch();
     scan_kernel<KP, NB, FIXUP><<<grid, kThreads, smem, s>>>(d);
     return cudaGetLastError();

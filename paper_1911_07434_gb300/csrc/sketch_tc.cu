@@ -43,9 +43,18 @@ __host__ __device__ constexpr int plain_stage(int nb_max) { return kTileA + nb_m
 __host__ __device__ constexpr int plain_nstages(int nb_max) {
     return 4 * plain_stage(nb_max) + kSmemExtra <= kSmemPerCta ? 4 : 3;
 }
-__host__ __device__ constexpr int split_stage(int nb_max) { return kTileA + nb_max * 128 + kRawA; }
-constexpr int kSplitStages = 3;
-static_assert(kSplitStages * split_stage(2 * kLMax) + kSmemExtra <= kSmemPerCta, "split ring too large");
+// Split kernel: a ring of raw stages [B rows nb_max x 128 B | raw A 8 KB] as deep as two
+// CTAs per SM allow (at most 6), and two converted A tiles.
+__host__ __device__ constexpr int split_stage(int nb_max) { return nb_max * 128 + kRawA; }
+__host__ __device__ constexpr int split_nraw(int nb_max) {
+    int n = 6;
+    while (n > 2 && n * split_stage(nb_max) + 2 * kTileA + kSmemExtra > kSmemPerCta) --n;
+    return n;
+}
+__host__ __device__ constexpr int split_smem(int nb_max) {
+    return split_nraw(nb_max) * split_stage(nb_max) + 2 * kTileA + kSmemExtra;
+}
+static_assert(split_nraw(2 * kLMax) >= 3 && split_smem(2 * kLMax) <= kSmemPerCta, "split ring too large");
 static_assert(plain_nstages(2 * kLMax) * plain_stage(2 * kLMax) + kSmemExtra <= kSmemPerCta, "ring too large");
 
 // B rows of pass `pass`, element (j, m) per thread.  Plain layout (2 l_pad rows x 2M):
@@ -149,8 +158,8 @@ __device__ __forceinline__ uint32_t tmem_setup(const Ring& rg, int ns, const CUt
         mbar_init(rg.acc_full, 1);
         *rg.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(ta)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tb)) : "memory");
+        tmap_acquire(ta);
+        tmap_acquire(tb);
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(rg.tmem_slot)),
@@ -247,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    constexpr int ns = kSplitStages;
+    constexpr int nr = split_nraw(NB);
     constexpr int stage = split_stage(NB);
     const FrameDesc* dp = descs + blockIdx.y;
     if (!dp->sketch_tc || !sketch_on_tc(dp->method, pass) || !sketch_split(dp->prec, dp->t, pass)) return;
@@ -260,31 +269,34 @@ __global__ void __launch_bounds__(kThreads, 2)
     const CUtensorMap* tb = tmB + blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    uint64_t* bars = reinterpret_cast<uint64_t*>(base + ns * stage);
-    uint64_t* full = bars;                // [ns] B rows landed + 128 converter arrivals -> MMA
-    uint64_t* empty = bars + ns;          // [ns] MMA -> TMA
-    uint64_t* rawb = bars + 2 * ns;       // [ns] raw A landed -> converters
-    uint64_t* acc_ready = bars + 3 * ns;  // [2] group committed -> drain
-    uint64_t* acc_free = bars + 3 * ns + 2;  // [2] group drained (128 arrivals) -> MMA
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * ns + 4);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 3 * ns + 5);
-    // stage layout: [A tile 16 KB | B rows NB x 128 B | raw A 8 KB]
-    constexpr int b_off = kTileA, raw_off = kTileA + NB * 128;
+    // layout: nr raw stages [B rows NB x 128 B | raw A 8 KB], two A tiles, barriers
+    unsigned char* conv = base + nr * stage;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(conv + 2 * kTileA);
+    uint64_t* full = bars;                    // [nr] raw A + B rows landed (TMA)
+    uint64_t* empty = bars + nr;              // [nr] MMA done with the stage's B rows
+    uint64_t* conv_full = bars + 2 * nr;      // [2] A tile written (128 converter arrivals)
+    uint64_t* conv_empty = bars + 2 * nr + 2;  // [2] MMA done with the A tile
+    uint64_t* acc_ready = bars + 2 * nr + 4;  // [2] group committed -> drain
+    uint64_t* acc_free = bars + 2 * nr + 6;   // [2] group drained (128 arrivals) -> MMA
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * nr + 8);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * nr + 9);
+    constexpr int raw_off = NB * 128;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < ns; ++i) {
-            mbar_init(&full[i], 1 + 128);  // the producer's expect_tx arrival + one per converter thread
+        for (int i = 0; i < nr; ++i) {
+            mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
-            mbar_init(&rawb[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
+            mbar_init(&conv_full[i], 128);
+            mbar_init(&conv_empty[i], 1);
             mbar_init(&acc_ready[i], 1);
             mbar_init(&acc_free[i], 128);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(ta)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tb)) : "memory");
+        tmap_acquire(ta);
+        tmap_acquire(tb);
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(tmem_slot)),
@@ -299,33 +311,31 @@ __global__ void __launch_bounds__(kThreads, 2)
 
     if (warp == 0) {
         if (lane == 0) {
+            const uint32_t bytes = (uint32_t)kRawA + (uint32_t)nb * 128u;
             for (int s = 0; s < nchunks; ++s) {
-                const int slot = s % ns;
-                if (!mbar_wait(&empty[slot], ((uint32_t)(s / ns) & 1u) ^ 1u, abort_flag)) break;
+                const int slot = s % nr;
+                if (!mbar_wait(&empty[slot], ((uint32_t)(s / nr) & 1u) ^ 1u, abort_flag)) break;
                 unsigned char* st = base + slot * stage;
-                mbar_expect_tx(&rawb[slot], (uint32_t)kRawA);
-                tma_load_2d(st + raw_off, ta, s * 16, r0, &rawb[slot]);
-                mbar_expect_tx(&full[slot], (uint32_t)nb * 128u);
-                tma_load_2d(st + b_off, tb, s * 32, 0, &full[slot]);
+                mbar_expect_tx(&full[slot], bytes);
+                tma_load_2d(st + raw_off, ta, s * 16, r0, &full[slot]);
+                tma_load_2d(st, tb, s * 32, 0, &full[slot]);
             }
-            for (int s = max(0, nchunks - ns); s < nchunks; ++s) {
-                mbar_wait(&rawb[s % ns], (uint32_t)(s / ns) & 1u, abort_flag);
-                mbar_wait(&full[s % ns], (uint32_t)(s / ns) & 1u, abort_flag);
-            }
+            for (int s = max(0, nchunks - nr); s < nchunks; ++s)
+                mbar_wait(&full[s % nr], (uint32_t)(s / nr) & 1u, abort_flag);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = idesc_tf32(128, (uint32_t)nb);
             for (int s = 0; s < nchunks; ++s) {
-                const int slot = s % ns, g = s / kGroup, buf = g & 1, sg = s % kGroup;
+                const int slot = s % nr, cs = s & 1, g = s / kGroup, buf = g & 1, sg = s % kGroup;
                 const uint32_t d = tmem + 128u * (uint32_t)buf;
                 if (sg == 0 && g >= 2) {  // buffer buf still holds group g - 2 until it is drained
                     if (!mbar_wait(&acc_free[buf], (uint32_t)((g >> 1) + 1) & 1u, abort_flag)) break;
-                    tc_fence_after();
                 }
-                if (!mbar_wait(&full[slot], (uint32_t)(s / ns) & 1u, abort_flag)) break;
+                if (!mbar_wait(&full[slot], (uint32_t)(s / nr) & 1u, abort_flag)) break;
+                if (!mbar_wait(&conv_full[cs], (uint32_t)(s >> 1) & 1u, abort_flag)) break;
                 tc_fence_after();
-                const uint32_t a = sa(base + slot * stage), b = a + b_off;
+                const uint32_t a = sa(conv + cs * kTileA), b = sa(base + slot * stage);
 #pragma unroll
                 for (int kk = 0; kk < 2; ++kk) {  // 16 values per chunk = two K = 8 steps
                     const uint64_t a_hi = desc_sw128(a + 32 * kk), a_lo = desc_sw128(a + 64 + 32 * kk);
@@ -334,6 +344,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     mma_tf32(d, a_hi, b_lo, idesc, 1u);
                     mma_tf32(d, a_lo, b_hi, idesc, 1u);
                 }
+                mma_commit(&conv_empty[cs]);
                 mma_commit(&empty[slot]);
                 if (sg == kGroup - 1 || s == nchunks - 1) mma_commit(&acc_ready[buf]);
             }
@@ -341,11 +352,14 @@ __global__ void __launch_bounds__(kThreads, 2)
             mbar_wait(&acc_ready[(ngroups - 1) & 1], (uint32_t)((ngroups - 1) >> 1) & 1u, abort_flag);
         }
     } else {
-        // converters + two-level sum.  Conversion: raw chunk (128 rows x 64 B, float4 i =
-        // row i >> 2, quarter i & 3) -> A tile row with hi in 16-byte chunk q, lo in 4 + q
-        // (128-byte swizzle).  Sum: thread (warp % 4, lane) owns row 32 (warp % 4) + lane
-        // (its TMEM lane quadrant) and keeps the row's NB accumulator columns in registers.
-        const int c = threadIdx.x - 64;
+        // converters + two-level sum.  Conversion of a raw chunk (128 rows x 16 FP32 in
+        // 64-byte rows) into the A tile: hi in 16-byte chunk q of the row, lo in 4 + q
+        // (128-byte swizzle).  Lane (j = lane >> 3, k = lane & 7) of converter warp w takes
+        // row 32 u + 8 w + k, quarter q = (k >> 1) ^ j: every 8-lane phase then reads and
+        // writes eight distinct 16-byte bank groups.  Sum: thread (warp % 4, lane) owns row
+        // 32 (warp % 4) + lane (its TMEM lane quadrant) and keeps the row's NB accumulator
+        // columns in registers.
+        const int w = warp - 2, kq = lane & 7, q = (kq >> 1) ^ (lane >> 3);
         const int q4 = warp & 3;
         const uint32_t tl = tmem + ((uint32_t)(32 * q4) << 16);
         float sum[NB];
@@ -370,18 +384,18 @@ __global__ void __launch_bounds__(kThreads, 2)
             mbar_arrive(&acc_free[buf]);
         };
         for (int s = 0; s < nchunks && ok; ++s) {
-            const int slot = s % ns;
-            if (!__all_sync(0xffffffffu, mbar_wait(&rawb[slot], (uint32_t)(s / ns) & 1u, abort_flag))) {
+            const int slot = s % nr, cs = s & 1;
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], (uint32_t)(s / nr) & 1u, abort_flag) &&
+                                             mbar_wait(&conv_empty[cs], ((uint32_t)(s >> 1) & 1u) ^ 1u, abort_flag))) {
                 ok = false;
                 break;
             }
-            unsigned char* st = base + slot * stage;
-            const unsigned char* raw = st + raw_off;
+            const unsigned char* raw = base + slot * stage + raw_off;
+            unsigned char* at = conv + cs * kTileA;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int i = c + 128 * u;
-                const int r = i >> 2, q = i & 3;
-                const float4 v = *reinterpret_cast<const float4*>(raw + 16 * i);
+                const int r = 32 * u + 8 * w + kq;
+                const float4 v = *reinterpret_cast<const float4*>(raw + 64 * r + 16 * q);
                 uint4 hi, lo;
                 hi.x = tf32_rn(v.x);
                 hi.y = tf32_rn(v.y);
@@ -391,11 +405,11 @@ __global__ void __launch_bounds__(kThreads, 2)
                 lo.y = tf32_rn(v.y - __uint_as_float(hi.y));
                 lo.z = tf32_rn(v.z - __uint_as_float(hi.z));
                 lo.w = tf32_rn(v.w - __uint_as_float(hi.w));
-                *reinterpret_cast<uint4*>(st + swz(r, q)) = hi;
-                *reinterpret_cast<uint4*>(st + swz(r, 4 + q)) = lo;
+                *reinterpret_cast<uint4*>(at + swz(r, q)) = hi;
+                *reinterpret_cast<uint4*>(at + swz(r, 4 + q)) = lo;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(&full[slot]);
+            mbar_arrive(&conv_full[cs]);
             // groups whose chunks are all converted and kDrainLag behind are drained here
             while (ok && gd < ngroups && min(gd * kGroup + kGroup - 1, nchunks - 1) + kDrainLag <= s) drain(gd++);
         }
@@ -422,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 template <int NB>
 cudaError_t launch_split(const FrameDesc* d, dim3 grid, int pass, const void* tmA, const void* tmB, cudaStream_t s) {
     static_assert(NB % 16 == 0 && NB <= 2 * kLMax, "B rows: 2 l_pad");
-    const int smem = kSplitStages * split_stage(NB) + kSmemExtra;
+    const int smem = split_smem(NB);
     cudaError_t e = cudaFuncSetAttribute(sketch_split_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     count_launch();
@@ -433,7 +447,7 @@ cudaError_t launch_split(const FrameDesc* d, dim3 grid, int pass, const void* tm
 
 size_t sketch_tc_smem_bytes(int max_l, bool split) {
     const int nb_max = 2 * sketch_tc_lpad(max_l);
-    return split ? (size_t)kSplitStages * split_stage(nb_max) + kSmemExtra
+    return split ? (size_t)split_smem(nb_max)
                  : (size_t)plain_nstages(nb_max) * plain_stage(nb_max) + kSmemExtra;
 }
 

@@ -1029,6 +1029,7 @@ __global__ void __launch_bounds__(kThreads, 3) small_cluster_kernel(const FrameD
         const float4 g = sm.Gd[e];
         sm.Rc[e] = make_float2(g.x + g.y, g.z + g.w);
     }
+    __syncthreads();  // Gf (next) aliases Gd
 
     // B = R_c H^+ R_c^H
     for (int e = threadIdx.x; e < l * l; e += kThreads) sm.Gf[e] = sm.H[e];

@@ -54,6 +54,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
     return mbar_wait_limit(b, parity, abort, kWaitCycles);
 }
 
+// Tensor maps live in global memory, where the host rewrites them between launches
+// (each call uploads its descriptors into a reused workspace): the issuing thread
+// orders its tensor-map reads after those generic-proxy writes, then warms the
+// tensor-map cache.
+__device__ __forceinline__ void tmap_acquire(const void* tm) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(tm))
+                 : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tm)) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::

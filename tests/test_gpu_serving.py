@@ -69,7 +69,9 @@ def check_same(alone, mixed, fr):
     M = fr.X.shape[0]
     tol = 16 * U32 * M * nc
     da, dm = 1.0 / Pa, 1.0 / Pm
-    assert np.max(np.abs(da - dm)) <= tol, np.max(np.abs(da - dm))
+    j = int(np.argmax(np.abs(da - dm)))
+    assert np.max(np.abs(da - dm)) <= tol, (np.max(np.abs(da - dm)), "M", M, "K", fr.K, "l", fr.l, "angle", j,
+                                            da[j], dm[j], "first", da[0], dm[0], "peaks", sorted(ia), sorted(im))
     for a, b in zip(sorted(ia), sorted(im)):
         if a != b:  # only a near-tie of adjacent grid points may move a peak
             assert abs(int(a) - int(b)) == 1 and abs(da[a] - da[b]) <= 2 * tol
