@@ -485,8 +485,10 @@ def main():
         ctx.run(frames)
     torch.cuda.synchronize()
     assert int(status.abs().sum()) == 0, "a frame reported a non-zero status"
+    # the timed region brackets the covariance stage only (its events give the roofline's
+    # kernel duration); the per-stage breakdown comes from a short loop after it
     ctx.stage_times(reset=True)
-    ctx.set_timing(True)
+    ctx.set_timing_mask(1 << binding.STAGES.index("covariance"))
     launches0 = ctx.launch_count()
     step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     clocks = ClockSampler(local)
@@ -508,9 +510,32 @@ def main():
              "sketch": {binding.FM_COV_TC: "tensor", binding.FM_COV_SIMT: "cuda-core"}.get(ctx.last_sketch_path(), "mixed")}
     step_ms = [step_ev[k].elapsed_time(step_ev[k + 1]) for k in range(args.steps)]
     total_ms = step_ev[0].elapsed_time(step_ev[-1])
-    stages = ctx.stage_times(reset=True)
+    cov_timed = ctx.stage_times(reset=True)["covariance"]
     total_ms = max_over_ranks(total_ms, dev)
     value = job_rate(world, B, args.steps, total_ms / 1e3)
+    # per-stage breakdown (every stage bracketed), outside the timed region
+    ctx.set_timing(True)
+    for _ in range(max(5, min(args.steps, 20))):
+        ctx.run(frames)
+    torch.cuda.synchronize()
+    ctx.set_timing(False)
+    stages = ctx.stage_times(reset=True)
+    stages_cov_breakdown = stages["covariance"]
+    stages["covariance"] = cov_timed  # the roofline uses the timed region's launches
+    # the same step replayed through the library's CUDA graph of the chain (fm_graph_*)
+    graph = ctx.graph(frames)
+    for _ in range(3):
+        graph.launch(stream)
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.steps):
+        graph.launch(stream)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = g0.elapsed_time(g1) / args.steps
+    graph.close()
+    assert int(status.abs().sum()) == 0, "a frame reported a non-zero status"
 
     # ---- end-to-end through the C ABI with host buffers (fm_run_host) ----------
     # Every step copies its X from pinned host memory and its P and peaks back;
@@ -542,11 +567,16 @@ def main():
     # ---- roofline of the dominant kernel ----------------------------------------
     pk, pk_kind = peaks_json()
     names = list(stages.keys())
-    dom = max(names, key=lambda n: stages[n][0])
     roof = roofline(stages, ctx, pk, pk_kind, B, M, T, K, L)
     tot = max(1e-9, sum(v[0] for v in stages.values()))
     stage_summary = {n: {"ms_per_launch": (stages[n][0] / stages[n][1]) if stages[n][1] else 0.0,
                          "launches": stages[n][1], "share": stages[n][0] / tot} for n in names}
+    if stages_cov_breakdown[1]:  # covariance share from the same breakdown loop as the others
+        tot_b = tot - stages["covariance"][0] + stages_cov_breakdown[0]
+        for n in names:
+            own = stages_cov_breakdown if n == "covariance" else stages[n]
+            stage_summary[n]["share"] = own[0] / max(1e-9, tot_b)
+    dom = max(names, key=lambda n: stage_summary[n]["share"])
 
     # ---- single-frame latency (one fm_run per frame, device-resident) ----------
     lat = []
@@ -623,6 +653,8 @@ def main():
         "latency_ms": {"p50_step": srt[len(srt) // 2], "p99_step": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
                        "single_frame": single},
         "kernel_paths": paths,
+        "cuda_graph": {"value": job_rate(world, B, 1, graph_ms / 1e3), "unit": UNIT, "ms_per_step": graph_ms,
+                       "launch": "fm_graph_launch: the same chain replayed from one CUDA graph"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": roof, "dominant_stage": dom, "stages": stage_summary,

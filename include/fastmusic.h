@@ -252,9 +252,13 @@ fm_status fm_sample_indices(fm_ctx* ctx, uint64_t seed, uint64_t frame_id, int M
  * events.  fm_stage_times synchronises on them and returns, per stage, the
  * summed milliseconds and the number of launches since the last reset.
  * Stage order: 0 grid table, 1 covariance, 2 sketch, 3 orth, 4 final small
- * solve, 5 scan, 6 peaks, 7 FP32 refinement step. */
+ * solve, 5 scan, 6 peaks, 7 FP32 refinement step.  fm_set_timing(ctx, 1) times
+ * every stage, 0 none; fm_set_timing_mask times the stages whose bit
+ * (1 << stage) is set in mask (each timed launch adds two event records to its
+ * stream, so timing one stage perturbs a step less than timing all of them). */
 #define FM_N_STAGES 8
 fm_status fm_set_timing(fm_ctx* ctx, int enable);
+fm_status fm_set_timing_mask(fm_ctx* ctx, unsigned mask);
 fm_status fm_stage_times(fm_ctx* ctx, double* total_ms, int* launches, int reset);
 /* Number of kernel launches issued by this context since creation. */
 uint64_t fm_launch_count(const fm_ctx* ctx);

@@ -12,7 +12,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, byref, c_double, c_float, c_int, c_int64, c_size_t, c_uint64, c_void_p
+from ctypes import POINTER, byref, c_double, c_float, c_int, c_int64, c_size_t, c_uint, c_uint64, c_void_p
 
 from . import build as _build
 
@@ -74,6 +74,7 @@ _SIGS = {
     "fm_test_matrix": (c_int, [c_void_p, c_uint64, c_uint64, c_int, c_int, c_void_p, c_void_p]),
     "fm_sample_indices": (c_int, [c_void_p, c_uint64, c_uint64, c_int, c_int, c_void_p, c_void_p]),
     "fm_set_timing": (c_int, [c_void_p, c_int]),
+    "fm_set_timing_mask": (c_int, [c_void_p, c_uint]),
     "fm_stage_times": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int), c_int]),
     "fm_launch_count": (c_uint64, [c_void_p]),
     "fm_run_subspace": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
@@ -175,6 +176,10 @@ def fm_sample_indices(ctx, seed, frame_id, M, l, idx, stream) -> int:
 
 def fm_set_timing(ctx, enable) -> int:
     return load().fm_set_timing(ctx, int(enable))
+
+
+def fm_set_timing_mask(ctx, mask) -> int:
+    return load().fm_set_timing_mask(ctx, int(mask))
 
 
 def fm_stage_times(ctx, reset=False):
@@ -406,6 +411,10 @@ class Context:
 
     def set_timing(self, on: bool):
         self._check(fm_set_timing(self.h, on), "fm_set_timing")
+
+    def set_timing_mask(self, mask: int):
+        """Time only the stages whose bit (1 << stage) is set."""
+        self._check(fm_set_timing_mask(self.h, mask), "fm_set_timing_mask")
 
     def stage_times(self, reset=False):
         st, ms, n = fm_stage_times(self.h, reset)

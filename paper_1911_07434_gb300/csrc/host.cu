@@ -51,7 +51,7 @@ struct fm_ctx {
     cudaEvent_t staging_done = nullptr;
     bool staging_pending = false;
     std::string err;
-    bool timing = false;
+    unsigned timing = 0;  // bit s: stage s is bracketed by events
     std::vector<TimedEvent> pending;
     std::vector<cudaEvent_t> pool;
     double stage_ms[FM_N_STAGES] = {};
@@ -131,7 +131,8 @@ fm_status stage(fm_ctx* c, int st, cudaStream_t s, F&& launch) {
         ~Pop() { nvtxRangePop(); }
     } pop;
     cudaEvent_t a = nullptr, b = nullptr;
-    if (c->timing) {
+    const bool timed = (c->timing >> st) & 1u;
+    if (timed) {
         a = get_event(c);
         b = get_event(c);
         cudaEventRecord(a, s);
@@ -140,7 +141,7 @@ fm_status stage(fm_ctx* c, int st, cudaStream_t s, F&& launch) {
     cudaError_t e = launch();
     c->launches += fm::g_kernel_launches - k0;
     if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
-    if (c->timing) {
+    if (timed) {
         cudaEventRecord(b, s);
         c->pending.push_back({st, a, b});
     }
@@ -951,8 +952,8 @@ fm_status fm_autotune(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream
     if (st != FM_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int saved_cov = c->cov_path, saved_scan = c->scan_path;
-    const bool saved_timing = c->timing;
-    c->timing = false;
+    const unsigned saved_timing = c->timing;
+    c->timing = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1311,7 +1312,13 @@ fm_status fm_sample_indices(fm_ctx* c, uint64_t seed, uint64_t frame_id, int M, 
 
 fm_status fm_set_timing(fm_ctx* c, int enable) {
     if (!c) return FM_ERR_INVALID_ARG;
-    c->timing = enable != 0;
+    c->timing = enable != 0 ? (1u << FM_N_STAGES) - 1u : 0u;
+    return FM_OK;
+}
+
+fm_status fm_set_timing_mask(fm_ctx* c, unsigned mask) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    c->timing = mask & ((1u << FM_N_STAGES) - 1u);
     return FM_OK;
 }
 
