@@ -196,9 +196,13 @@ fm_status fm_run_subspace(fm_ctx* ctx, int frame, void* U, fm_stream stream);
  * but the copies then block the host).  Asynchronous: the call enqueues, on
  * streams of the context, the host -> device copies of every X (rows of T
  * complex elements taken with stride ldx) into one of two device staging
- * slots, the whole chain, and the device -> host copies of every output, and
- * makes `stream` wait for the last copy, so once `stream` has passed the call
- * the host outputs are written.  Consecutive calls overlap: the copies of one
+ * slots (frames adjacent in host memory in one copy), the whole chain, and the
+ * device -> host transfer of every output, and makes `stream` wait for it, so
+ * once `stream` has passed the call the host outputs are written.  Where the
+ * device addresses host memory through host pointers
+ * (cudaDevAttrPageableMemoryAccess) and every output is 4-byte aligned, one
+ * kernel writes all outputs into the host buffers; otherwise each output buffer
+ * is copied (one cudaMemcpyAsync each).  Consecutive calls overlap: the copies of one
  * call run while the previous call computes.  The host X must hold its data
  * when the call is made (the copies in do not wait for earlier work on
  * `stream`), and the caller keeps the host buffers of a call untouched until

@@ -176,6 +176,13 @@ __host__ __device__ inline int sketch_tc_lpad(int l) { return (l + 7) / 8 * 8; }
 // Floats per B row of the split layout: ceil(2M / 16) chunks of [hi 16 | lo 16].
 __host__ __device__ inline int64_t sketch_split_rowlen(int M) { return 32 * (int64_t)((2 * M + 15) / 16); }
 
+// One device -> host output copy of fm_run_host (dst: a host address the device can write).
+struct CopyEntry {
+    const void* src;
+    void* dst;
+    int64_t bytes;
+};
+
 // ---------------------------------------------------------- launch wrappers --
 // Kernel launches issued by the calling host thread (every launch site bumps it),
 // so the host side can report exactly how many kernels a call launched.
@@ -198,6 +205,7 @@ cudaError_t launch_orth(const FrameDesc* d, int n_frames, int max_M, int max_l, 
 cudaError_t launch_final(const FrameDesc* d, int n_frames, int max_M, int max_l, cudaStream_t s);
 cudaError_t launch_refine(const FrameDesc* d, int n_frames, int max_M, int max_T, cudaStream_t s);
 cudaError_t launch_wait_timeout(int* status, long long limit_cycles, cudaStream_t s);
+cudaError_t launch_scatter(const CopyEntry* tab, int n, cudaStream_t s);
 cudaError_t launch_sketch_tc(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, bool any_plain,
                              bool any_split, const void* tmA, const void* tmB, const void* tmA_split,
                              const void* tmB_split, cudaStream_t s);

@@ -79,7 +79,10 @@ struct fm_ctx {
         size_t bytes = 0;
         cudaEvent_t h2d = nullptr, comp = nullptr, d2h = nullptr;
         bool used = false;
+        fm::CopyEntry* tab = nullptr;  // pinned: the output copies of the slot's call
+        size_t tab_cap = 0;
     };
+    int host_direct = -1;  // the device writes host memory through its host address (-1: not yet asked)
     HostSlot hslot[2];
     int hnext = 0;
     cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
@@ -622,6 +625,7 @@ fm_status fm_destroy(fm_ctx* c) {
     for (fm_ctx::HostSlot& h : c->hslot) {
         if (h.d2h) cudaEventSynchronize(h.d2h);
         if (h.buf) cudaFree(h.buf);
+        if (h.tab) cudaFreeHost(h.tab);
         if (h.h2d) cudaEventDestroy(h.h2d);
         if (h.comp) cudaEventDestroy(h.comp);
         if (h.d2h) cudaEventDestroy(h.d2h);
@@ -854,14 +858,21 @@ fm_status fm_run_host(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream
     for (cudaEvent_t* ev : {&h.h2d, &h.comp, &h.d2h})
         if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
             return cuda_fail(c, e, "cudaEventCreate");
-    // device staging layout: per frame packed X (M x T), then every output
+    // device staging layout: every frame's packed X (M x T, rows padded to an even
+    // length) back to back, so that frames adjacent in host memory arrive in one copy;
+    // then every output; then the table of output copies
     std::vector<size_t> xo(n), po(n), dbo(n), io(n), dgo(n), no(n), so(n);
     size_t off = 0;
     for (int b = 0; b < n; ++b) {
         const fm_frame& f = frames[b];
-        const size_t M = (size_t)f.arr.M, K = (size_t)f.p.K, L = (size_t)f.grid.L;
         xo[b] = off;
-        off = aup(off + 8 * M * (size_t)(f.T + (f.T & 1)));  // rows padded to an even length
+        off += 8 * (size_t)f.arr.M * (size_t)(f.T + (f.T & 1));  // a multiple of 16 bytes
+    }
+    off = aup(off);
+    int n_out = 0;
+    for (int b = 0; b < n; ++b) {
+        const fm_frame& f = frames[b];
+        const size_t K = (size_t)f.p.K, L = (size_t)f.grid.L;
         po[b] = off;
         off = aup(off + 4 * L);
         dbo[b] = off;
@@ -874,7 +885,10 @@ fm_status fm_run_host(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream
         off = aup(off + 4);
         so[b] = off;
         off = aup(off + 4);
+        n_out += 4 + (f.P_db_out ? 1 : 0) + (f.status ? 1 : 0);
     }
+    const size_t tab_off = off;
+    off = aup(off + sizeof(fm::CopyEntry) * (size_t)n_out);
     if (off > h.bytes) {
         if (h.used) cudaEventSynchronize(h.d2h);  // the slot's previous call is done with it
         if (h.buf) cudaFree(h.buf);
@@ -890,16 +904,37 @@ fm_status fm_run_host(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream
     // previous call's copies out, which `stream` is made to wait for, and serialise)
     if (h.used) cudaStreamWaitEvent(c->s_h2d, h.d2h, 0);
     std::vector<fm_frame> dev(frames, frames + n);
+    // one copy per run of frames that are contiguous both in host memory and here
+    const char* run_src = nullptr;
+    size_t run_dst = 0, run_bytes = 0;
+    auto flush = [&]() -> cudaError_t {
+        if (!run_bytes) return cudaSuccess;
+        const cudaError_t r = cudaMemcpyAsync(h.buf + run_dst, run_src, run_bytes, cudaMemcpyHostToDevice, c->s_h2d);
+        run_bytes = 0;
+        return r;
+    };
     for (int b = 0; b < n; ++b) {
         const fm_frame& f = frames[b];
         const size_t row = 8 * (size_t)f.T;
         const int64_t ldd = f.T + (f.T & 1);
-        if (f.ldx == f.T && ldd == f.T)  // one contiguous block
-            e = cudaMemcpyAsync(h.buf + xo[b], f.X, row * (size_t)f.arr.M, cudaMemcpyHostToDevice, c->s_h2d);
-        else
-            e = cudaMemcpy2DAsync(h.buf + xo[b], 8 * (size_t)ldd, f.X, 8 * (size_t)f.ldx, row, (size_t)f.arr.M,
-                                  cudaMemcpyHostToDevice, c->s_h2d);
-        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy2DAsync(X)");
+        if (f.ldx == f.T && ldd == f.T) {  // one contiguous block
+            const char* src = reinterpret_cast<const char*>(f.X);
+            const size_t bytes = row * (size_t)f.arr.M;
+            if (run_bytes && src == run_src + run_bytes && xo[b] == run_dst + run_bytes) {
+                run_bytes += bytes;
+            } else {
+                e = flush();
+                run_src = src;
+                run_dst = xo[b];
+                run_bytes = bytes;
+            }
+        } else {
+            e = flush();
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(h.buf + xo[b], 8 * (size_t)ldd, f.X, 8 * (size_t)f.ldx, row, (size_t)f.arr.M,
+                                      cudaMemcpyHostToDevice, c->s_h2d);
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync(X)");
         dev[b].X = h.buf + xo[b];
         dev[b].ldx = ldd;
         dev[b].P_out = reinterpret_cast<float*>(h.buf + po[b]);
@@ -909,6 +944,8 @@ fm_status fm_run_host(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream
         dev[b].n_peaks = reinterpret_cast<int*>(h.buf + no[b]);
         dev[b].status = reinterpret_cast<int*>(h.buf + so[b]);
     }
+    e = flush();
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync(X)");
     cudaEventRecord(h.h2d, c->s_h2d);
     // the chain
     cudaStreamWaitEvent(c->s_comp, h.h2d, 0);
@@ -918,20 +955,50 @@ fm_status fm_run_host(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream
     st = enqueue_run(c, rp, c->s_comp);
     if (st != FM_OK) return st;
     cudaEventRecord(h.comp, c->s_comp);
-    // copies out
+    // copies out: where the device writes host memory through its host address, one
+    // kernel scatters every output (after one upload of the copy table); else one
+    // copy per output buffer
     cudaStreamWaitEvent(c->s_d2h, h.comp, 0);
+    if (c->host_direct < 0) {
+        int pageable = 0;
+        cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, c->device);
+        c->host_direct = pageable ? 1 : 0;
+    }
+    std::vector<fm::CopyEntry> tab;
+    tab.reserve((size_t)n_out);
     for (int b = 0; b < n; ++b) {
         const fm_frame& f = frames[b];
-        const size_t L = (size_t)f.grid.L, K = (size_t)f.p.K;
-        e = cudaMemcpyAsync(f.P_out, h.buf + po[b], 4 * L, cudaMemcpyDeviceToHost, c->s_d2h);
-        if (e == cudaSuccess && f.P_db_out)
-            e = cudaMemcpyAsync(f.P_db_out, h.buf + dbo[b], 4 * L, cudaMemcpyDeviceToHost, c->s_d2h);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(f.peak_idx, h.buf + io[b], 4 * K, cudaMemcpyDeviceToHost, c->s_d2h);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(f.peak_deg, h.buf + dgo[b], 4 * K, cudaMemcpyDeviceToHost, c->s_d2h);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(f.n_peaks, h.buf + no[b], 4, cudaMemcpyDeviceToHost, c->s_d2h);
-        if (e == cudaSuccess && f.status)
-            e = cudaMemcpyAsync(f.status, h.buf + so[b], 4, cudaMemcpyDeviceToHost, c->s_d2h);
-        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync(outputs)");
+        const int64_t L = f.grid.L, K = f.p.K;
+        tab.push_back({h.buf + po[b], f.P_out, 4 * L});
+        if (f.P_db_out) tab.push_back({h.buf + dbo[b], f.P_db_out, 4 * L});
+        tab.push_back({h.buf + io[b], f.peak_idx, 4 * K});
+        tab.push_back({h.buf + dgo[b], f.peak_deg, 4 * K});
+        tab.push_back({h.buf + no[b], f.n_peaks, 4});
+        if (f.status) tab.push_back({h.buf + so[b], f.status, 4});
+    }
+    bool direct = c->host_direct == 1;
+    for (const fm::CopyEntry& t : tab) direct = direct && (reinterpret_cast<uintptr_t>(t.dst) % 4) == 0;
+    if (direct) {
+        if (h.used) cudaEventSynchronize(h.d2h);  // the slot's previous table upload is done
+        if (h.tab_cap < tab.size()) {
+            if (h.tab) cudaFreeHost(h.tab);
+            h.tab = nullptr;
+            h.tab_cap = 0;
+            e = cudaMallocHost(reinterpret_cast<void**>(&h.tab), sizeof(fm::CopyEntry) * tab.size());
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaMallocHost(copy table)");
+            h.tab_cap = tab.size();
+        }
+        memcpy(h.tab, tab.data(), sizeof(fm::CopyEntry) * tab.size());
+        fm::CopyEntry* dtab = reinterpret_cast<fm::CopyEntry*>(h.buf + tab_off);
+        e = cudaMemcpyAsync(dtab, h.tab, sizeof(fm::CopyEntry) * tab.size(), cudaMemcpyHostToDevice, c->s_d2h);
+        if (e == cudaSuccess) e = fm::launch_scatter(dtab, (int)tab.size(), c->s_d2h);
+        if (e != cudaSuccess) return cuda_fail(c, e, "output scatter");
+        c->launches += 1;
+    } else {
+        for (const fm::CopyEntry& t : tab) {
+            e = cudaMemcpyAsync(t.dst, t.src, (size_t)t.bytes, cudaMemcpyDeviceToHost, c->s_d2h);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync(outputs)");
+        }
     }
     cudaEventRecord(h.d2h, c->s_d2h);
     h.used = true;
