@@ -8,11 +8,14 @@
 //                        Fisher-Yates index set; rows of R are read coalesced.
 //   pass p >= 1        : C = R V with V the basis from the previous orth step.
 //
-// Dense form: each CTA owns 64 rows of R and all l columns of C.  Threads hold a
-// 4-row x ceil(l/8)-column register tile; R and V stream through double-buffered
-// shared memory in 32-column chunks (cp.async: the next chunk arrives while the
-// current one is consumed).  FP32 products, two-level accumulation (per chunk,
-// then into the running sum).  R is read from HBM exactly once per pass.
+// Dense form (the CUDA-core product, for frames the tensor-core sketch of
+// sketch_tc.cu cannot read, i.e. odd M, and for fm_set_sketch_path(FM_COV_SIMT)):
+// each CTA owns 64 rows of R and all l columns of C.  Threads hold a 4-row x
+// ceil(l/8)-column register tile; R and V stream through double-buffered shared
+// memory in 32-column chunks (cp.async: the next chunk arrives while the current
+// one is consumed).  FP32 products, two-level accumulation (per chunk, then into
+// the running sum).  R is read from HBM exactly once per pass.  Omega and the
+// sampling gather run here for every frame.
 #include "fm_internal.cuh"
 
 namespace fm {
