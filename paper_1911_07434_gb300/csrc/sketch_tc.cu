@@ -99,9 +99,8 @@ __global__ void sketch_bprep_kernel(const FrameDesc* __restrict__ descs, int pas
 }
 
 struct Ring {
-    uint64_t* full;   // [ns] TMA (+ converters) -> MMA
+    uint64_t* full;   // [ns] TMA -> MMA
     uint64_t* empty;  // [ns] MMA -> TMA
-    uint64_t* raw;    // [ns] raw A landed (split kernel)
     uint64_t* acc_full;
     uint32_t* tmem_slot;
     volatile int* abort_flag;
@@ -112,10 +111,9 @@ __device__ __forceinline__ Ring ring_at(unsigned char* p, int ns) {
     uint64_t* bars = reinterpret_cast<uint64_t*>(p);
     r.full = bars;
     r.empty = bars + ns;
-    r.raw = bars + 2 * ns;
-    r.acc_full = bars + 3 * ns;
-    r.tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * ns + 1);
-    r.abort_flag = reinterpret_cast<volatile int*>(bars + 3 * ns + 2);
+    r.acc_full = bars + 2 * ns;
+    r.tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * ns + 1);
+    r.abort_flag = reinterpret_cast<volatile int*>(bars + 2 * ns + 2);
     return r;
 }
 
@@ -153,7 +151,6 @@ __device__ __forceinline__ uint32_t tmem_setup(const Ring& rg, int ns, const CUt
         for (int s = 0; s < ns; ++s) {
             mbar_init(&rg.full[s], (uint32_t)full_count);
             mbar_init(&rg.empty[s], 1);
-            mbar_init(&rg.raw[s], 1);
         }
         mbar_init(rg.acc_full, 1);
         *rg.abort_flag = 0;

@@ -251,36 +251,51 @@ __device__ void gram_part_f(const float2* A, const float2* B, int rows, int l, b
 }
 
 // part <- A^H A over this CTA's rows in double-float (upper triangle, float4 entries).
+// Each entry is shared by a lane pair (rows of one parity each, four interleaved
+// partial sums per lane) and combined across the pair in a fixed order, so the
+// l(l+1)/2 entries spread evenly over the block.
 __device__ void gram_part_d(const float2* A, int rows, int l, float4* part) {
     const int n = l * (l + 1) / 2;
-    for (int e = threadIdx.x; e < n; e += kThreads) {
+    const int ntask = 2 * n;
+    const int rounds = (ntask + kThreads - 1) / kThreads;  // block-uniform: every lane reaches every shuffle
+    for (int u = 0; u < rounds; ++u) {
+        const int task = threadIdx.x + u * kThreads;
+        const bool act = task < ntask;
+        const int e = act ? task >> 1 : 0, h = task & 1;
         int i, j;
         tri_coords(e, l, i, j);
-        // four interleaved double-float partial sums (rows r = 4 u + v) shorten the
-        // dependent chain; they are combined in a fixed order at the end
         df re[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         df im[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        int r = 0;
-        for (; r + 4 <= rows; r += 4) {
+        if (act) {
+            int r = h;
+            for (; r + 6 < rows; r += 8) {  // rows r, r + 2, r + 4, r + 6 of this lane's parity
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const float2 a = A[(r + v) * l + i], b = A[(r + v) * l + j];
-                dd_acc(re[v], a.x, b.x);
-                dd_acc(re[v], a.y, b.y);
-                dd_acc(im[v], a.x, b.y);
-                dd_acc(im[v], -a.y, b.x);
+                for (int v = 0; v < 4; ++v) {
+                    const float2 a = A[(r + 2 * v) * l + i], b = A[(r + 2 * v) * l + j];
+                    dd_acc(re[v], a.x, b.x);
+                    dd_acc(re[v], a.y, b.y);
+                    dd_acc(im[v], a.x, b.y);
+                    dd_acc(im[v], -a.y, b.x);
+                }
+            }
+            for (; r < rows; r += 2) {
+                const float2 a = A[r * l + i], b = A[r * l + j];
+                dd_acc(re[0], a.x, b.x);
+                dd_acc(re[0], a.y, b.y);
+                dd_acc(im[0], a.x, b.y);
+                dd_acc(im[0], -a.y, b.x);
             }
         }
-        for (; r < rows; ++r) {
-            const float2 a = A[r * l + i], b = A[r * l + j];
-            dd_acc(re[0], a.x, b.x);
-            dd_acc(re[0], a.y, b.y);
-            dd_acc(im[0], a.x, b.y);
-            dd_acc(im[0], -a.y, b.x);
+        df sr = dd_add(dd_add(re[0], re[1]), dd_add(re[2], re[3]));
+        df si = dd_add(dd_add(im[0], im[1]), dd_add(im[2], im[3]));
+        // the even-row lane adds its odd-row partner's sums
+        const df pr{__shfl_xor_sync(0xffffffffu, sr.hi, 1), __shfl_xor_sync(0xffffffffu, sr.lo, 1)};
+        const df pi{__shfl_xor_sync(0xffffffffu, si.hi, 1), __shfl_xor_sync(0xffffffffu, si.lo, 1)};
+        if (act && h == 0) {
+            sr = dd_add(sr, pr);
+            si = dd_add(si, pi);
+            part[e] = zpack(zd{quick_two_sum(sr.hi, sr.lo), quick_two_sum(si.hi, si.lo)});
         }
-        const df sr = dd_add(dd_add(re[0], re[1]), dd_add(re[2], re[3]));
-        const df si = dd_add(dd_add(im[0], im[1]), dd_add(im[2], im[3]));
-        part[e] = zpack(zd{quick_two_sum(sr.hi, sr.lo), quick_two_sum(si.hi, si.lo)});
     }
 }
 
