@@ -533,7 +533,7 @@ def main():
         graph.launch(stream)
     g1.record(stream)
     torch.cuda.synchronize()
-    graph_ms = g0.elapsed_time(g1) / args.steps
+    graph_ms = max_over_ranks(g0.elapsed_time(g1) / args.steps, dev)
     graph.close()
     assert int(status.abs().sum()) == 0, "a frame reported a non-zero status"
 
