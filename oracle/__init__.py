@@ -9,7 +9,7 @@ with gcc and marshals numpy arrays through ctypes.
 Function map (paper section / equation / algorithm each one follows):
   covariance          Eq. 2              S = Y Y^H / N
   eigh_jacobi         Eq. 4              cyclic complex Jacobi EVD of a Hermitian matrix
-  svd_jacobi          Alg. 1 line "SVD of C"   one-sided Jacobi thin SVD
+  svd_jacobi          Alg. 1 (SVD of C)  one-sided Jacobi thin SVD
   householder_qr      Sec. III-B qr()/orth()
   pinv_hermitian      Eq. 8              pseudo-inverse by EVD
   philox4x32_10       counter-based generator used for Pi (Salmon et al., SC'11)
