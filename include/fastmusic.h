@@ -202,7 +202,9 @@ fm_status fm_run_subspace(fm_ctx* ctx, int frame, void* U, fm_stream stream);
  * device addresses host memory through host pointers
  * (cudaDevAttrPageableMemoryAccess) and every output is 4-byte aligned, one
  * kernel writes all outputs into the host buffers; otherwise each output buffer
- * is copied (one cudaMemcpyAsync each).  Consecutive calls overlap: the copies of one
+ * is copied (one cudaMemcpyAsync each).  The two staging slots alternate, so a call
+ * may block the host until the call two before it has written its outputs.
+ * Consecutive calls overlap: the copies of one
  * call run while the previous call computes.  The host X must hold its data
  * when the call is made (the copies in do not wait for earlier work on
  * `stream`), and the caller keeps the host buffers of a call untouched until
