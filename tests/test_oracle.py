@@ -239,6 +239,69 @@ def test_nystrom_identity_and_forms(method, t):
     assert np.linalg.norm(proj(U0) - proj(U1)) < 1e-9
 
 
+def _nystrom_reference(R, method, l, t, seed, frame_id=0):
+    """S~ = C pinv(P^H C) C^H written from Eq. 8 with a general Pi (Sec. III-B) and the
+    power steps of Eq. 11, with numpy/LAPACK primitives only: C = R Pi (Pi the pinned
+    Gaussian test matrix, or the columns R(:, I) for Alg. 1), then t times
+    {P = orth(C) by LAPACK QR; C = R P}.  Also returns the two plausible wrong cores
+    (W = I, and W built from Pi instead of the last P after power steps)."""
+    M = R.shape[0]
+    if method == 1:
+        idx = oracle.sample_indices(seed, frame_id, M, l)
+        Pi = np.zeros((M, l), dtype=complex)
+        Pi[idx, np.arange(l)] = 1.0
+    else:
+        Pi = oracle.gaussian_test_matrix(seed, frame_id, M, l)
+    C = R @ Pi
+    P = Pi
+    for _ in range(t):
+        P, _r = np.linalg.qr(C)
+        C = R @ P
+    H = P.conj().T @ C
+    H = (H + H.conj().T) / 2
+    S_tilde = C @ np.linalg.pinv(H, hermitian=True) @ C.conj().T
+    wrong_identity = C @ C.conj().T
+    Hp = Pi.conj().T @ C
+    wrong_pi = C @ np.linalg.pinv((Hp + Hp.conj().T) / 2, hermitian=True) @ C.conj().T
+    return S_tilde, wrong_identity, wrong_pi
+
+
+def _top_eig(S, n):
+    w, V = np.linalg.eigh((S + S.conj().T) / 2)
+    order = np.argsort(w)[::-1][:n]
+    return w[order], V[:, order]
+
+
+@pytest.mark.parametrize("case,method,t", [
+    ("small", 2, 0), ("small", 2, 1), ("small", 2, 2), ("small", 1, 1), ("small", 1, 0),
+    ("m96", 2, 0), ("m96", 2, 1), ("m96", 2, 2), ("m96", 1, 1)])
+def test_core_matrix_is_nystrom_pinv(case, method, t):
+    """The core matrix W of Alg. 1/2 is pinv(P^H S P) = pinv(P^H C) (Eq. 8 with a general
+    Pi; Alg. 2 with P = the last orth(C)), so B's eigenvalues are the l nonzero eigenvalues
+    of the Nystrom approximation S~ = C W C^H and U spans S~'s top-K eigenspace.
+    Noisy frames with l > K, where the choice of W decides the result; the two plausible
+    slips (W = I; Pi in place of the last P) are shown to miss the check by a wide margin."""
+    if case == "small":
+        fr = synth.small_frame()
+        K, l = fr.K, fr.l
+    else:
+        fr = synth.massive_mimo_frames(1, seed=4, M=96, T=300, K=4, extra=16, snr_lo=0.0,
+                                       snr_hi=12.0).frames[0]
+        K, l = fr.K, fr.l
+    R = oracle.covariance(fr.X)
+    U, lamB, _ = oracle.fast_music(R, K, l, t, method, seed=21)
+    S_tilde, wrong_identity, wrong_pi = _nystrom_reference(R, method, l, t, seed=21)
+    w_ref, V_ref = _top_eig(S_tilde, l)
+    scale = w_ref[0]
+    assert np.max(np.abs(lamB - w_ref)) <= 1e-9 * scale, np.max(np.abs(lamB - w_ref)) / scale
+    assert np.linalg.norm(proj(U) - proj(V_ref[:, :K])) <= 1e-9
+    w_id, _ = _top_eig(wrong_identity, l)
+    assert np.max(np.abs(lamB - w_id)) > 1.0 * scale
+    if t > 0:
+        w_pi, _ = _top_eig(wrong_pi, l)
+        assert np.max(np.abs(lamB - w_pi)) > 0.1 * scale
+
+
 def test_power_iterations_converge():
     """Theorem 2/3: the error decays like (sigma_{K+1}/sigma_K)^{t+1}."""
     fr = synth.massive_mimo_frames(1, seed=3, M=96, T=200, K=4, extra=0, snr_lo=-6, snr_hi=-3).frames[0]
