@@ -25,10 +25,13 @@
  *     launch; an invalid call launches nothing and returns FM_ERR_INVALID_ARG.
  *   - Errors are returned as fm_status; a readable message is available from
  *     fm_last_error(ctx).  No exception crosses the ABI.
- *   - Steering vectors are those of a uniform linear array with element
- *     spacing d_wl wavelengths (0.5 = lambda/2, Sec. II-A):
- *       a_m(theta) = exp(j 2 pi d_wl m sin theta),  m = 0..M-1,
+ *   - Steering vectors follow the far-field signal model of Sec. II-A for a
+ *     linear array with element m at position x_m wavelengths along its axis:
+ *       a_m(theta) = exp(j 2 pi x_m sin theta),  m = 0..M-1,
  *     theta measured from broadside, grid theta_i = theta0_deg + i * step_deg.
+ *     x_m = d_wl * m for a uniform linear array of spacing d_wl (0.5 = lambda/2),
+ *     or any positions (a sparse or cascaded MIMO virtual array) given by
+ *     fm_array.pos_wl.
  *   - The Gaussian test matrix Pi of Sec. III-B is drawn from Philox4x32-10
  *     (Salmon et al., SC'11) with key (seed_lo, seed_hi) and counter
  *     (column j, row m, frame_id_lo, frame_id_hi); outputs x0, x1 give
@@ -82,10 +85,20 @@ typedef enum {
     FM_PREC_BF16 = 2  /* BF16 operands (7-bit mantissa), one kind::f16 MMA per 16 elements */
 } fm_precision;
 
-/* Uniform linear array (Sec. II-A): M elements, spacing d_wl wavelengths (0 => 0.5). */
+/* Array geometry (Sec. II-A): M elements on a line.  pos_wl == NULL: a uniform
+ * linear array, x_m = d_wl * m with d_wl in (0, 1] wavelengths (0 => 0.5).
+ * pos_wl != NULL: a HOST array of M element positions x_m in wavelengths (any
+ * order and spacing, |x_m| <= 4096, all finite; d_wl is then ignored).  The
+ * library reads pos_wl during the call that takes the frame (fm_run,
+ * fm_run_host, fm_graph_create, fm_workspace_bytes) and copies what it needs
+ * into its workspace; a frame given to fm_serve_submit is read when its batch
+ * starts, so its positions must stay valid until fm_serve_poll reports it done.
+ * Frames whose positions are equal element by element share their steering
+ * vectors in the scan. */
 typedef struct {
     int M;
     double d_wl;
+    const double* pos_wl;
 } fm_array;
 
 /* Angle grid (Sec. II-B): theta_i = theta0_deg + i * step_deg, i = 0..L-1. */
@@ -236,9 +249,14 @@ fm_status fm_subspace(fm_ctx* ctx, const void* R, int n_frames, int M, const fm_
                       uint64_t frame_id0, void* U, int* status, fm_stream stream);
 
 /* fm_spectrum (Eq. 5 / Eq. 10): P_b[i] = 1/(M - ||U_b^H a(theta_i)||^2) for
- * U_b = U + b*M*ncols (complex64 M x ncols, orthonormal columns), P_b = P + b*L. */
+ * U_b = U + b*M*ncols (complex64 M x ncols, orthonormal columns), P_b = P + b*L,
+ * on a uniform linear array of spacing d_wl. */
 fm_status fm_spectrum(fm_ctx* ctx, const void* U, int n_frames, int M, int ncols, double d_wl,
                       const fm_grid* grid, float* P, fm_stream stream);
+/* fm_spectrum_array: fm_spectrum for the array `arr` (uniform or given by
+ * arr->pos_wl, read during the call); M = arr->M. */
+fm_status fm_spectrum_array(fm_ctx* ctx, const void* U, int n_frames, const fm_array* arr, int ncols,
+                            const fm_grid* grid, float* P, fm_stream stream);
 
 /* fm_peaks (Eq. 6): K largest local maxima of each P_b (P + b*L); a local
  * maximum is i with P[i] > P[i-1] and P[i] >= P[i+1] (missing neighbours at the
@@ -313,6 +331,17 @@ int fm_last_scan_path(const fm_ctx* ctx);
 fm_status fm_set_sketch_path(fm_ctx* ctx, int path);
 int fm_last_sketch_path(const fm_ctx* ctx);
 
+/* ---- eigensolver sweep cap (failure detection) -----------------------------------
+ * The paper's SVD / eigendecomposition steps (Alg. 1 / Alg. 2) run here as cyclic
+ * Jacobi iterations on l x l matrices with a cap of 30 sweeps; a frame whose
+ * solve does not converge within the cap (or meets a non-finite pivot) still
+ * gets outputs, and its status word carries the FM_ERR_NO_CONVERGENCE bit.
+ * fm_set_sweep_cap lowers the cap for the later fm_run calls of this context
+ * (and for the graphs and serving slots created after it): cap in [1, 30], 0
+ * restores 30.  A cap of 1 makes an ordinary frame report FM_ERR_NO_CONVERGENCE,
+ * which is how failure detection is exercised without faulting anything. */
+fm_status fm_set_sweep_cap(fm_ctx* ctx, int cap);
+
 /* ---- allocation-free spectrum --------------------------------------------------
  * The paper has no counterpart to this call; it exists for callers that cannot
  * let the library allocate device memory: a radar front end that fixes its
@@ -324,9 +353,10 @@ int fm_last_sketch_path(const fm_ctx* ctx);
  * library, about 524 KB, which every GPU that loads the library holds until the
  * process exits.  Limits: n_frames <= 64 and grid->L <= 65536 (larger requests
  * return FM_ERR_INVALID_ARG before any work), plus fm_spectrum's own limits.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call shares the one array and overwrites it: calls that
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, which also loads the module there on the first call of
+ * a process), so a device reset between calls is harmless; make the first call
+ * on a device before any stream capture.  Every call shares the one array and overwrites it: calls that
  * overlap on the GPU (different streams, or different host threads on one
  * device) race, so serialise them on one stream.  The descriptors are copied
  * from host stack memory with a pageable cudaMemcpyAsync, which has taken its

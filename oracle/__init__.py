@@ -17,7 +17,7 @@ Function map (paper section / equation / algorithm each one follows):
   sample_indices      Alg. 1             index set I
   music_subspace      Eq. 4              U_K of standard MUSIC
   fast_music          Alg. 1 / Alg. 2    randomized signal subspace
-  spectrum            Eq. 5 / Eq. 10     pseudo-spectrum on an angle grid
+  spectrum            Eq. 5 / Eq. 10     pseudo-spectrum on an angle grid (uniform or given positions)
   peaks               Eq. 6              K largest local maxima
   frame               whole frame X -> P, peaks
 """
@@ -75,10 +75,10 @@ def _load():
             "orc_music_subspace": (c_int, [vp, c_int, c_int, vp, vp]),
             "orc_fast_music": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, c_u64, c_u64,
                                        c_int, c_int, vp, vp, vp]),
-            "orc_spectrum": (c_int, [vp, c_int, c_int, c_dbl, c_dbl, c_dbl, c_int, c_int, vp]),
+            "orc_spectrum": (c_int, [vp, c_int, c_int, c_dbl, vp, c_dbl, c_dbl, c_int, c_int, vp]),
             "orc_peaks": (c_int, [vp, c_int, c_int, vp, vp]),
             "orc_frame": (c_int, [vp, c_int, c_int, c_i64, c_int, c_int, c_int, c_int, c_u64,
-                                  c_u64, c_dbl, c_dbl, c_dbl, c_int, vp, vp, vp]),
+                                  c_u64, c_dbl, vp, c_dbl, c_dbl, c_int, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -193,13 +193,25 @@ def fast_music(R: np.ndarray, K: int, l: int, t: int, method: int, seed: int, fr
     return U, lamB, idx
 
 
+def _positions(pos, M):
+    """float64 copy of the element positions (wavelengths), or None for a uniform array."""
+    if pos is None:
+        return None
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    if pos.shape != (M,):
+        raise ValueError(f"pos must hold M = {M} element positions")
+    return pos
+
+
 def spectrum(U: np.ndarray, theta0_deg: float, step_deg: float, L: int, d: float = 0.5,
-             residual_form: bool = False) -> np.ndarray:
+             residual_form: bool = False, pos=None) -> np.ndarray:
+    """Pseudo-spectrum on the grid; pos = element positions in wavelengths (None: d * m)."""
     U = _c128(U)
     M, nc = U.shape
     P = np.zeros(L)
-    _check(_load().orc_spectrum(_p(U), M, nc, d, theta0_deg, step_deg, L, int(residual_form), _p(P)),
-           "spectrum")
+    pp = _positions(pos, M)
+    _check(_load().orc_spectrum(_p(U), M, nc, d, None if pp is None else _p(pp), theta0_deg, step_deg, L,
+                                int(residual_form), _p(P)), "spectrum")
     return P
 
 
@@ -212,13 +224,16 @@ def peaks(P: np.ndarray, K: int):
 
 
 def frame(X: np.ndarray, K: int, l: int, t: int, method: int, seed: int, frame_id: int,
-          theta0_deg: float, step_deg: float, L: int, d: float = 0.5):
-    """Whole frame: X (complex64 M x T) -> (P, peak_idx, n_peaks)."""
+          theta0_deg: float, step_deg: float, L: int, d: float = 0.5, pos=None):
+    """Whole frame: X (complex64 M x T) -> (P, peak_idx, n_peaks); pos = element positions
+    in wavelengths (None: a uniform array of spacing d)."""
     X = np.ascontiguousarray(X, dtype=np.complex64)
     M, T = X.shape
     P = np.zeros(L)
     idx = np.zeros(K, dtype=np.int32)
     n = ctypes.c_int(0)
-    _check(_load().orc_frame(_p(X), M, T, T, K, l, t, method, seed, frame_id, d, theta0_deg,
-                             step_deg, L, _p(P), _p(idx), ctypes.byref(n)), "frame")
+    pp = _positions(pos, M)
+    _check(_load().orc_frame(_p(X), M, T, T, K, l, t, method, seed, frame_id, d,
+                             None if pp is None else _p(pp), theta0_deg, step_deg, L, _p(P), _p(idx),
+                             ctypes.byref(n)), "frame")
     return P, idx, n.value

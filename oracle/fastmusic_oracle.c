@@ -20,8 +20,10 @@
  *
  * Readings of places where the paper is silent or ambiguous (the same list
  * is kept with the design notes):
- *   - steering vector a_m(theta) = exp(+j 2 pi d m sin(theta)) with d in
- *     wavelengths (the trailing ^H in Sec. II-B is read as a transpose);
+ *   - steering vector a_m(theta) = exp(+j 2 pi x_m sin(theta)) with x_m = d m
+ *     for the uniform array of Sec. II-A (d in wavelengths) or the given
+ *     element positions x_m of a non-uniform virtual array (the trailing ^H in
+ *     Sec. II-B is read as a transpose);
  *   - theta is measured from broadside in degrees, grid theta_i = theta0 + i*step;
  *   - sampling draws l DISTINCT indices from {0..M-1}, sorted ascending; the
  *     sqrt(M/p) scale of the sampling matrix cancels in C W C^H and is omitted;
@@ -568,12 +570,14 @@ done:
 
 /* ------------------------------------------------------------------------ */
 /* Pseudo-spectrum (Eq. 5 / Eq. 10) on the grid theta_i = theta0 + i*step    */
-/* (degrees):  P_i = 1 / (||a||^2 - ||U^H a||^2) with                         */
-/* a_m = exp(j 2 pi d m sin theta_i).  residual_form = 1 evaluates the same   */
+/* (degrees):  P_i = 1 / (||a||^2 - ||U^H a||^2) with the far-field steering   */
+/* vector of Sec. II-A, a_m = exp(j 2 pi x_m sin theta_i), x_m the position   */
+/* of element m in wavelengths: x_m = d m for a uniform linear array        */
+/* (pos == NULL), else x_m = pos[m].  residual_form = 1 evaluates the same    */
 /* quantity as 1 / ||a - U U^H a||^2 (no cancellation).                      */
 /* ------------------------------------------------------------------------ */
-int orc_spectrum(const zc* U, int M, int ncols, double d, double theta0_deg, double step_deg,
-                 int L, int residual_form, double* P)
+int orc_spectrum(const zc* U, int M, int ncols, double d, const double* pos, double theta0_deg,
+                 double step_deg, int L, int residual_form, double* P)
 {
     if (M < 1 || ncols < 1 || L < 1) return ORC_ERR_ARG;
     zc* a = (zc*)malloc(sizeof(zc) * (size_t)M);
@@ -584,7 +588,7 @@ int orc_spectrum(const zc* U, int M, int ncols, double d, double theta0_deg, dou
         double s = sin(th);
         double an = 0.0;
         for (int m = 0; m < M; ++m) {
-            double ph = 2.0 * M_PI * d * (double)m * s;
+            double ph = pos ? 2.0 * M_PI * pos[m] * s : 2.0 * M_PI * d * (double)m * s;
             a[m] = cos(ph) + I * sin(ph);
             an += creal(a[m] * conj(a[m]));
         }
@@ -645,8 +649,8 @@ int orc_peaks(const double* P, int L, int K, int* idx, int* n_found)
 /* P (length L) and peak_idx (length K) are outputs.                          */
 /* ------------------------------------------------------------------------ */
 int orc_frame(const float* X, int M, int T, int64_t ldx, int K, int l, int t, int method,
-              uint64_t seed, uint64_t frame_id, double d, double theta0_deg, double step_deg,
-              int L, double* P, int* peak_idx, int* n_peaks)
+              uint64_t seed, uint64_t frame_id, double d, const double* pos, double theta0_deg,
+              double step_deg, int L, double* P, int* peak_idx, int* n_peaks)
 {
     zc* R = (zc*)malloc(sizeof(zc) * (size_t)M * M);
     zc* U = (zc*)malloc(sizeof(zc) * (size_t)M * K);
@@ -658,7 +662,7 @@ int orc_frame(const float* X, int M, int T, int64_t ldx, int K, int l, int t, in
         else
             rc = orc_fast_music(R, M, K, l, t, method, seed, frame_id, K, 0, U, NULL, NULL);
     }
-    if (rc == ORC_OK) rc = orc_spectrum(U, M, K, d, theta0_deg, step_deg, L, 0, P);
+    if (rc == ORC_OK) rc = orc_spectrum(U, M, K, d, pos, theta0_deg, step_deg, L, 0, P);
     if (rc == ORC_OK) rc = orc_peaks(P, L, K, peak_idx, n_peaks);
     free(R); free(U);
     return rc;

@@ -39,7 +39,7 @@ STAGES = ("grid", "covariance", "sketch", "orth", "final", "scan", "peaks", "ref
 
 
 class FmArray(ctypes.Structure):
-    _fields_ = [("M", c_int), ("d_wl", c_double)]
+    _fields_ = [("M", c_int), ("d_wl", c_double), ("pos_wl", c_void_p)]
 
 
 class FmGrid(ctypes.Structure):
@@ -69,6 +69,8 @@ _SIGS = {
     "fm_subspace": (c_int, [c_void_p, c_void_p, c_int, c_int, POINTER(FmParams), c_uint64, c_void_p, c_void_p,
                             c_void_p]),
     "fm_spectrum": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_double, POINTER(FmGrid), c_void_p, c_void_p]),
+    "fm_spectrum_array": (c_int, [c_void_p, c_void_p, c_int, POINTER(FmArray), c_int, POINTER(FmGrid), c_void_p,
+                                  c_void_p]),
     "fm_peaks": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, POINTER(FmGrid), c_void_p, c_void_p, c_void_p,
                          c_void_p]),
     "fm_test_matrix": (c_int, [c_void_p, c_uint64, c_uint64, c_int, c_int, c_void_p, c_void_p]),
@@ -91,6 +93,7 @@ _SIGS = {
     "fm_last_scan_path": (c_int, [c_void_p]),
     "fm_set_sketch_path": (c_int, [c_void_p, c_int]),
     "fm_last_sketch_path": (c_int, [c_void_p]),
+    "fm_set_sweep_cap": (c_int, [c_void_p, c_int]),
     "fm_spectrum_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_double, POINTER(FmGrid), c_void_p, c_void_p]),
     "fm_serve_submit": (c_int, [c_void_p, POINTER(FmFrame), POINTER(c_uint64)]),
     "fm_serve_poll": (c_int, [c_void_p, c_uint64, POINTER(c_int)]),
@@ -160,6 +163,10 @@ def fm_subspace(ctx, R, n_frames, M, params: FmParams, frame_id0, U, status, str
 
 def fm_spectrum(ctx, U, n_frames, M, ncols, d_wl, grid: FmGrid, P, stream) -> int:
     return load().fm_spectrum(ctx, U, n_frames, M, ncols, d_wl, byref(grid), P, stream)
+
+
+def fm_spectrum_array(ctx, U, n_frames, arr: FmArray, ncols, grid: FmGrid, P, stream) -> int:
+    return load().fm_spectrum_array(ctx, U, n_frames, byref(arr), ncols, byref(grid), P, stream)
 
 
 def fm_peaks(ctx, P, n_frames, L, K, grid: FmGrid, peak_idx, peak_deg, n_peaks, stream) -> int:
@@ -252,6 +259,10 @@ def fm_last_sketch_path(ctx) -> int:
     return load().fm_last_sketch_path(ctx)
 
 
+def fm_set_sweep_cap(ctx, cap) -> int:
+    return load().fm_set_sweep_cap(ctx, cap)
+
+
 def fm_spectrum_noalloc(U, n_frames, M, ncols, d_wl, grid: FmGrid, P, stream) -> int:
     """Same result as fm_spectrum without any device allocation (see fastmusic.h)."""
     return load().fm_spectrum_noalloc(U, n_frames, M, ncols, d_wl, byref(grid), P, stream)
@@ -270,6 +281,19 @@ def fm_serve_poll(ctx, ticket):
 
 
 # ---- torch convenience ------------------------------------------------------
+def _array(M, d_wl, pos_wl, owner) -> FmArray:
+    """FmArray of M elements; with positions, a float64 copy is kept alive on `owner`."""
+    if pos_wl is None:
+        return FmArray(M, d_wl, None)
+    import numpy as np
+    pos = np.ascontiguousarray(pos_wl, dtype=np.float64)
+    if pos.shape != (M,):
+        raise ValueError(f"pos_wl must hold M = {M} positions")
+    owner._pos_keep = pos
+    return FmArray(M, d_wl, pos.ctypes.data)
+
+
+
 def _stream_handle(stream=None) -> int:
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
@@ -305,14 +329,16 @@ class Context:
     # frames -----------------------------------------------------------------
     @staticmethod
     def frame(X, K, l, t, method, theta0, step, L, P, peak_idx, peak_deg, n_peaks, seed=0, frame_id=0,
-              d_wl=0.5, status=None, P_db=None, rank_restrict=0, prec=0, refine=0) -> FmFrame:
-        """FmFrame for a complex64 CUDA tensor X (M x T, row stride >= T)."""
+              d_wl=0.5, status=None, P_db=None, rank_restrict=0, prec=0, refine=0, pos_wl=None) -> FmFrame:
+        """FmFrame for a complex64 CUDA tensor X (M x T, row stride >= T).  pos_wl: element
+        positions in wavelengths (M floats; None = uniform spacing d_wl); the frame keeps
+        a float64 copy alive for the library to read."""
         M, T = X.shape
         f = FmFrame()
         f.X = X.data_ptr()
         f.T = T
         f.ldx = X.stride(0)
-        f.arr = FmArray(M, d_wl)
+        f.arr = _array(M, d_wl, pos_wl, f)
         f.grid = FmGrid(theta0, step, L)
         f.p = FmParams(method, K, l, t, prec, rank_restrict, refine, 0, seed)
         f.frame_id = frame_id
@@ -383,6 +409,21 @@ class Context:
         self._check(fm_spectrum(self.h, Ub.data_ptr(), B, M, nc, d_wl, FmGrid(theta0, step, L), P.data_ptr(),
                                 _stream_handle(stream)), "fm_spectrum")
         return P
+
+    def spectrum_array(self, U, theta0, step, L, pos_wl=None, d_wl=0.5, stream=None):
+        """fm_spectrum_array: the scan for element positions pos_wl (None: uniform d_wl)."""
+        import torch
+        Ub = (U if U.dim() == 3 else U.unsqueeze(0)).contiguous()
+        B, M, nc = Ub.shape
+        P = torch.empty((B, L), dtype=torch.float32, device=U.device)
+        arr = _array(M, d_wl, pos_wl, self)
+        self._check(fm_spectrum_array(self.h, Ub.data_ptr(), B, arr, nc, FmGrid(theta0, step, L), P.data_ptr(),
+                                      _stream_handle(stream)), "fm_spectrum_array")
+        return P
+
+    def set_sweep_cap(self, cap: int):
+        """Jacobi sweeps allowed in the l x l eigensolves of later runs (0: the default 30)."""
+        self._check(fm_set_sweep_cap(self.h, cap), "fm_set_sweep_cap")
 
     def peaks(self, P, K, theta0, step, stream=None):
         import torch

@@ -24,7 +24,7 @@ struct FrameDesc {
     int refine;        // 1: one more power step C = X (X^H V) / T in FP32 before the final solve
     int scan_tc;       // 1: scanned by the tensor-core kernel (then main lobes by the fixup scan)
     int sketch_tc;     // 1: the tensor-core sketch is prepared for this frame (Bsk, tensor maps)
-    int pad2_;
+    int sweep_cap;     // Jacobi sweeps allowed in the l x l eigensolves (0: the solver's own cap)
     float2* R;         // M x M
     float2* C;         // M x l  sketch
     float2* V;         // M x l  basis (power steps) / Q
@@ -34,6 +34,7 @@ struct FrameDesc {
                        // 2 l_pad x sketch_split_rowlen(M) for a split pass
     int* idx;          // l sampled indices
     float2* qtab;      // L entries (q_hi, q_lo): q = 2 d_wl sin(theta_i), split for exact m*q_hi
+    const float2* pos; // M element positions (x_hi, x_lo) in wavelengths, or null for a uniform array
     float* P;          // L
     float* Pdb;        // L (nullable)
     int* peak_idx;     // K
@@ -161,6 +162,20 @@ __device__ __forceinline__ float2 steer_exact(int m, float qh, float ql) {
     return make_float2(c, s);
 }
 
+// e^{j pi x q} for an element at x = x_hi + x_lo wavelengths (x_hi with at most 11
+// significant bits) and q = q_hi + q_lo = 2 sin(theta) (q_hi a multiple of 2^-11,
+// |q| <= 2): x_hi*q_hi has at most 23 significant bits, so it is exact in FP32 and is
+// reduced mod 2 without error; the small terms x_hi*q_lo + x_lo*q are added after the
+// reduction.  For x = m (x_lo = 0) this is steer_exact(m, q_hi, q_lo) bit for bit.
+__device__ __forceinline__ float2 steer_pos(float2 x, float qh, float ql) {
+    const float p = x.x * qh;                    // exact
+    const float r = p - 2.0f * rintf(0.5f * p);  // exact, in [-1, 1]
+    const float ph = fmaf(x.x, ql, fmaf(x.y, qh + ql, r));
+    float s, c;
+    sincospif(ph, &s, &c);
+    return make_float2(c, s);
+}
+
 // Per-frame status bits.
 __device__ __forceinline__ void set_status(int* status, int code) {
     if (status) atomicOr(status, 1 << code);
@@ -194,8 +209,8 @@ cudaError_t launch_grid_table(const GridDesc* g, int n_grids, int max_L, const F
                               cudaStream_t s);
 cudaError_t launch_covariance_tc(const FrameDesc* d, const void* tmaps, int n_frames, int max_M, cudaStream_t s);
 size_t cov_tc_smem_bytes();
-cudaError_t launch_scan_tc(const FrameDesc* d, int n_frames, int M, int ncols, int L, int prec, float* bprep, const void* tmB,
-                           cudaStream_t s);
+cudaError_t launch_scan_tc(const FrameDesc* d, int n_frames, int M, int ncols, int L, int prec, bool pos, float* bprep,
+                           const void* tmB, cudaStream_t s);
 int scan_tc_ncp(int ncols);
 cudaError_t launch_covariance(const FrameDesc* d, int n_frames, int max_M, cudaStream_t s);
 cudaError_t launch_repack(const FrameDesc* d, int n_frames, int max_M, int max_T, cudaStream_t s);
@@ -210,8 +225,13 @@ cudaError_t launch_sketch_tc(const FrameDesc* d, int n_frames, int max_M, int ma
                              bool any_split, const void* tmA, const void* tmB, const void* tmA_split,
                              const void* tmB_split, cudaStream_t s);
 size_t sketch_tc_smem_bytes(int max_l, bool split);
-cudaError_t launch_scan(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s);
-cudaError_t launch_scan_fixup(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s);
+// smem_elems: the largest M * (ceil4(kpad) + (positions ? 1 : 0)) over the frames (float2
+// elements of shared memory per CTA: U_s rows and the element positions)
+cudaError_t launch_scan(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, size_t smem_elems,
+                        cudaStream_t s);
+cudaError_t launch_scan_fixup(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, size_t smem_elems,
+                              cudaStream_t s);
+inline size_t scan_smem_elems(int M, int kpad, bool pos) { return (size_t)M * (size_t)(((kpad + 3) & ~3) + (pos ? 1 : 0)); }
 cudaError_t launch_peaks(const FrameDesc* d, int n_frames, int max_K, cudaStream_t s);
 cudaError_t launch_test_matrix(uint64_t seed, uint64_t frame_id, int M, int l, float2* out, cudaStream_t s);
 cudaError_t launch_sample_indices(uint64_t seed, uint64_t frame_id, int M, int l, int* out, cudaStream_t s);

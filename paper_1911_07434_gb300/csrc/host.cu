@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cstdarg>
+#include <cstddef>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -21,6 +22,12 @@
 
 using fm::FrameDesc;
 using fm::GridDesc;
+
+// The struct layouts the ctypes binding mirrors (LP64).
+static_assert(sizeof(fm_array) == 24 && sizeof(fm_grid) == 24 && sizeof(fm_params) == 40, "ABI struct size");
+static_assert(offsetof(fm_frame, arr) == 24 && offsetof(fm_frame, grid) == 48 && offsetof(fm_frame, p) == 72 &&
+                  sizeof(fm_frame) == 168,
+              "fm_frame layout");
 
 namespace {
 
@@ -63,6 +70,7 @@ struct fm_ctx {
     int last_scan_path = 0;
     int sketch_path = FM_COV_AUTO;
     int last_sketch_path = 0;
+    int sweep_cap = 0;  // Jacobi sweeps allowed in the l x l eigensolves (0: the solver's own cap)
     // serving state
     struct Slot;
     std::vector<Slot*> slots;
@@ -241,7 +249,12 @@ const char* check_frame(const fm_frame& f) {
     if (M < 2 || M > fm::kMMax) return "M must be in [2, 1024]";
     if (f.T < 1) return "T must be >= 1";
     if (f.ldx < f.T) return "ldx must be >= T";
-    if (!(f.arr.d_wl >= 0.0 && f.arr.d_wl <= 1.0)) return "d_wl must be in (0, 1] (0 selects 0.5)";
+    if (f.arr.pos_wl) {
+        for (int m = 0; m < M; ++m)
+            if (!(std::fabs(f.arr.pos_wl[m]) <= 4096.0)) return "pos_wl: positions must be finite with |x| <= 4096";
+    } else if (!(f.arr.d_wl >= 0.0 && f.arr.d_wl <= 1.0)) {
+        return "d_wl must be in (0, 1] (0 selects 0.5)";
+    }
     if (f.grid.L < 1 || f.grid.L > 65536) return "grid L must be in [1, 65536]";
     if (!std::isfinite(f.grid.theta0_deg) || !std::isfinite(f.grid.step_deg)) return "grid is not finite";
     if (p.method != FM_RAND_SAMPLING && p.method != FM_RAND_PROJECTION) return "method must be 1 or 2";
@@ -258,8 +271,49 @@ const char* check_frame(const fm_frame& f) {
     return nullptr;
 }
 
+// Spacing that enters the grid's phase table q = 2 d sin(theta): the ULA spacing, or
+// 1 for explicit positions (the element phase is then pi x_m q = 2 pi x_m sin(theta)).
+double grid_spacing(const fm_frame& f) {
+    if (f.arr.pos_wl) return 1.0;
+    return f.arr.d_wl > 0.0 ? f.arr.d_wl : 0.5;
+}
+
+// x = hi + lo with hi carrying at most 11 significant bits, so that hi * q_hi is exact in
+// FP32 for any q_hi that is a multiple of 2^-11 with |q_hi| <= 2 (at most 23 bits).
+float2 split_position(double x) {
+    if (x == 0.0) return make_float2(0.f, 0.f);
+    int e = 0;
+    std::frexp(x, &e);  // |x| in [2^(e-1), 2^e)
+    const double scale = std::ldexp(1.0, 11 - e);
+    const double hi = std::nearbyint(x * scale) / scale;
+    return make_float2((float)hi, (float)(x - hi));
+}
+
+// Geometry id per frame: 0 for a uniform array, k >= 1 for the k-th distinct set of
+// element positions (compared element by element), in order of first appearance.
+std::vector<int> geometry_ids(const fm_frame* f, int n, std::vector<const fm_frame*>* firsts = nullptr) {
+    std::vector<int> id(n, 0);
+    std::vector<const fm_frame*> reps;
+    for (int b = 0; b < n; ++b) {
+        if (!f[b].arr.pos_wl) continue;
+        int k = 0;
+        for (size_t r = 0; r < reps.size() && !k; ++r)
+            if (reps[r]->arr.M == f[b].arr.M &&
+                (reps[r]->arr.pos_wl == f[b].arr.pos_wl ||
+                 std::memcmp(reps[r]->arr.pos_wl, f[b].arr.pos_wl, sizeof(double) * (size_t)f[b].arr.M) == 0))
+                k = (int)r + 1;
+        if (!k) {
+            reps.push_back(&f[b]);
+            k = (int)reps.size();
+        }
+        id[b] = k;
+    }
+    if (firsts) *firsts = reps;
+    return id;
+}
+
 struct Plan {
-    size_t desc_off, tmap_off, grid_off, total;
+    size_t desc_off, tmap_off, grid_off, pos_off, upload_bytes, total;
     // tensor-core scan groups: maximal runs of consecutive frames sharing M, ncols,
     // grid and prec (fm_run orders the frames so that each group is one run)
     struct ScanGroup {
@@ -273,6 +327,12 @@ struct Plan {
     std::vector<int> grid_of;
     std::vector<GridDesc> grids;
     std::vector<size_t> qtab;
+    // element positions (split as (hi, lo) floats), one table per distinct geometry,
+    // uploaded with the descriptors; geom_of[b] = 0 for a uniform array
+    std::vector<int> geom_of;
+    std::vector<size_t> pos_tab;        // offset of geometry k's table (index k - 1)
+    std::vector<float2> pos_host;       // every table back to back
+    std::vector<size_t> pos_host_at;    // start of table k - 1 in pos_host
 };
 
 typedef std::tuple<double, double, double, int> GridKey;
@@ -291,7 +351,7 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
     pl.grid_of.assign(n, -1);
     if (need_grid) {
         for (int b = 0; b < n; ++b) {
-            const double d = f[b].arr.d_wl > 0.0 ? f[b].arr.d_wl : 0.5;
+            const double d = grid_spacing(f[b]);
             GridKey k(f[b].grid.theta0_deg, f[b].grid.step_deg, d, f[b].grid.L);
             auto it = gmap.find(k);
             if (it == gmap.end()) {
@@ -311,6 +371,19 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
     }
     pl.grid_off = off;
     off = aup(off + sizeof(GridDesc) * pl.grids.size());
+    pl.pos_off = off;
+    pl.geom_of.assign(n, 0);
+    if (need_grid) {
+        std::vector<const fm_frame*> reps;
+        pl.geom_of = geometry_ids(f, n, &reps);
+        for (const fm_frame* r : reps) {
+            pl.pos_tab.push_back(off);
+            pl.pos_host_at.push_back(pl.pos_host.size());
+            for (int m = 0; m < r->arr.M; ++m) pl.pos_host.push_back(split_position(r->arr.pos_wl[m]));
+            off = aup(off + sizeof(float2) * (size_t)r->arr.M);
+        }
+    }
+    pl.upload_bytes = off;
     for (size_t g = 0; g < pl.grids.size(); ++g) {
         pl.qtab.push_back(off);
         off = aup(off + sizeof(float2) * (size_t)pl.grids[g].L);
@@ -346,7 +419,10 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
         for (int b = 0; b < n;) {
             const int M0 = f[b].arr.M, nc0 = ncols_of(f[b].p), pr0 = f[b].p.prec, g0 = pl.grid_of[b];
             int e = b + 1;
-            while (e < n && f[e].arr.M == M0 && ncols_of(f[e].p) == nc0 && f[e].p.prec == pr0 && pl.grid_of[e] == g0) ++e;
+            const int geo0 = pl.geom_of[b];
+            while (e < n && f[e].arr.M == M0 && ncols_of(f[e].p) == nc0 && f[e].p.prec == pr0 &&
+                   pl.grid_of[e] == g0 && pl.geom_of[e] == geo0)
+                ++e;
             Plan::ScanGroup sg{};
             sg.f0 = b;
             sg.nf = e - b;
@@ -392,13 +468,14 @@ FrameDesc make_desc(const fm_frame& f) {
     d.frame_id = f.frame_id;
     d.theta0 = f.grid.theta0_deg;
     d.step = f.grid.step_deg;
-    d.d_wl = f.arr.d_wl > 0.0 ? f.arr.d_wl : 0.5;
+    d.d_wl = grid_spacing(f);
     return d;
 }
 
 struct Maxes {
     int M = 0, l = 0, L = 0, K = 0, kpad = 0, t = 0, T = 0;
-    bool any_sampling = false, any_projection = false, any_status = false, any_refine = false;
+    bool any_sampling = false, any_projection = false, any_status = false, any_refine = false, any_pos = false;
+    size_t scan_smem = 0;  // float2 elements of shared memory the CUDA-core scan needs
 };
 
 Maxes maxes_of(const std::vector<FrameDesc>& ds) {
@@ -415,6 +492,8 @@ Maxes maxes_of(const std::vector<FrameDesc>& ds) {
         m.any_sampling |= d.method == FM_RAND_SAMPLING;
         m.any_projection |= d.method == FM_RAND_PROJECTION;
         m.any_status |= d.status != nullptr;
+        m.any_pos |= d.pos != nullptr;
+        m.scan_smem = std::max(m.scan_smem, fm::scan_smem_elems(d.M, d.kpad, d.pos != nullptr));
     }
     return m;
 }
@@ -530,7 +609,7 @@ fm_status upload_descs(fm_ctx* c, const Plan& pl, std::vector<FrameDesc>& ds, co
                        cudaStream_t s, FrameDesc** dd, GridDesc** dg,
                        const std::vector<CUtensorMap>* group_maps = nullptr,
                        const std::vector<CUtensorMap>* sketch_maps = nullptr) {
-    const size_t bytes = pl.grid_off + sizeof(GridDesc) * pl.grids.size();
+    const size_t bytes = pl.upload_bytes;
     char* host = nullptr;
     fm_status st = staging(c, bytes, &host);
     if (st != FM_OK) return st;
@@ -545,6 +624,10 @@ fm_status upload_descs(fm_ctx* c, const Plan& pl, std::vector<FrameDesc>& ds, co
     std::vector<GridDesc> g = pl.grids;
     for (size_t i = 0; i < g.size(); ++i) g[i].qtab = reinterpret_cast<float2*>(c->arena + pl.qtab[i]);
     if (!g.empty()) memcpy(host + pl.grid_off, g.data(), sizeof(GridDesc) * g.size());
+    for (size_t k = 0; k < pl.pos_tab.size(); ++k) {
+        const size_t end = k + 1 < pl.pos_host_at.size() ? pl.pos_host_at[k + 1] : pl.pos_host.size();
+        memcpy(host + pl.pos_tab[k], pl.pos_host.data() + pl.pos_host_at[k], sizeof(float2) * (end - pl.pos_host_at[k]));
+    }
     st = upload(c, host, c->arena, bytes, s);
     if (st != FM_OK) return st;
     *dd = reinterpret_cast<FrameDesc*>(c->arena + pl.desc_off);
@@ -686,10 +769,11 @@ static fm_status prepare_run(fm_ctx* c, const fm_frame* frames, int n, cudaStrea
     rp.n = n;
     rp.order.resize(n);
     for (int b = 0; b < n; ++b) rp.order[b] = b;
+    const std::vector<int> geo = geometry_ids(frames, n);
     auto key = [&](int b) {
         const fm_frame& f = frames[b];
-        const double d = f.arr.d_wl > 0.0 ? f.arr.d_wl : 0.5;
-        return std::make_tuple(f.arr.M, ncols_of(f.p), f.p.prec, f.grid.theta0_deg, f.grid.step_deg, d, f.grid.L);
+        return std::make_tuple(f.arr.M, ncols_of(f.p), f.p.prec, f.grid.theta0_deg, f.grid.step_deg, grid_spacing(f),
+                               f.grid.L, geo[b]);
     };
     std::stable_sort(rp.order.begin(), rp.order.end(), [&](int x, int y) { return key(x) < key(y); });
     std::vector<fm_frame> sorted(n);
@@ -719,8 +803,10 @@ static fm_status prepare_run(fm_ctx* c, const fm_frame* frames, int n, cudaStrea
             d.ldx = d.T + (d.T & 1);
             rp.any_repack = true;
         }
+        d.sweep_cap = c->sweep_cap;
         c->last_us[rp.order[k]] = std::make_tuple(pl.Us[k], d.M, d.ncols);
         d.qtab = reinterpret_cast<float2*>(c->arena + pl.qtab[pl.grid_of[k]]);
+        if (pl.geom_of[k]) d.pos = reinterpret_cast<const float2*>(c->arena + pl.pos_tab[pl.geom_of[k] - 1]);
         ds[k] = d;
     }
     std::vector<CUtensorMap> maps;
@@ -799,7 +885,7 @@ static fm_status enqueue_run(fm_ctx* c, const RunPrep& rp, cudaStream_t s) {
     if (st != FM_OK) return st;
     st = stage(c, kStScan, s, [&] {
         if (rp.scan_simt) {  // frames without a tensor-core group (the kernel skips the others)
-            cudaError_t e = fm::launch_scan(dd, n, mx.L, mx.M, mx.kpad, s);
+            cudaError_t e = fm::launch_scan(dd, n, mx.L, mx.M, mx.kpad, mx.scan_smem, s);
             if (e != cudaSuccess) return e;
         }
         if (rp.scan_tc) {
@@ -808,11 +894,12 @@ static fm_status enqueue_run(fm_ctx* c, const RunPrep& rp, cudaStream_t s) {
                 const Plan::ScanGroup& sg = pl.scan_groups[g];
                 float* bp = reinterpret_cast<float*>(c->arena + sg.bprep_off);
                 const char* bmap_dev = c->arena + pl.tmap_off + sizeof(CUtensorMap) * ((size_t)n + g);
-                cudaError_t e = fm::launch_scan_tc(dd + sg.f0, sg.nf, sg.M, sg.nc, sg.L, sg.prec, bp, bmap_dev, s);
+                cudaError_t e = fm::launch_scan_tc(dd + sg.f0, sg.nf, sg.M, sg.nc, sg.L, sg.prec,
+                                                   pl.geom_of[sg.f0] != 0, bp, bmap_dev, s);
                 if (e != cudaSuccess) return e;
             }
             // main-lobe angles again on the FP32 CUDA cores (see scan_kernel<..., FIXUP>)
-            return fm::launch_scan_fixup(dd, n, mx.L, mx.M, mx.kpad, s);
+            return fm::launch_scan_fixup(dd, n, mx.L, mx.M, mx.kpad, mx.scan_smem, s);
         }
         return cudaSuccess;
     });
@@ -1102,6 +1189,7 @@ fm_status fm_graph_create(fm_ctx* c, const fm_frame* frames, int n, fm_graph** o
     g->sub->cov_path = c->cov_path;
     g->sub->scan_path = c->scan_path;
     g->sub->sketch_path = c->sketch_path;
+    g->sub->sweep_cap = c->sweep_cap;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamCreate"));
     RunPrep rp;
@@ -1276,21 +1364,28 @@ fm_status fm_subspace(fm_ctx* c, const void* R, int n, int M, const fm_params* p
     return run_subspace_chain(c, dd, n, maxes_of(ds), s);
 }
 
-fm_status fm_spectrum(fm_ctx* c, const void* U, int n, int M, int ncols, double d_wl, const fm_grid* grid, float* P,
-                      fm_stream stream) {
+static fm_status spectrum_impl(fm_ctx* c, const void* U, int n, const fm_array& arr, int ncols, const fm_grid* grid,
+                               float* P, fm_stream stream, const char* name) {
     if (!c) return FM_ERR_INVALID_ARG;
+    const int M = arr.M;
     if (!U || !grid || !P || n < 1 || M < 1 || M > fm::kMMax || ncols < 1 || ncols > fm::kKPadMax ||
         (size_t)M * (size_t)((ncols + 3) / 4 * 4) > 24576 || grid->L < 1 || grid->L > 65536 ||
-        !(d_wl >= 0.0 && d_wl <= 1.0))
-        return fail(c, FM_ERR_INVALID_ARG, "fm_spectrum: invalid shape or pointer");
+        !std::isfinite(grid->theta0_deg) || !std::isfinite(grid->step_deg))
+        return fail(c, FM_ERR_INVALID_ARG, "%s: invalid shape or pointer", name);
+    if (arr.pos_wl) {
+        for (int m = 0; m < M; ++m)
+            if (!(std::fabs(arr.pos_wl[m]) <= 4096.0))
+                return fail(c, FM_ERR_INVALID_ARG, "%s: positions must be finite with |x| <= 4096", name);
+    } else if (!(arr.d_wl >= 0.0 && arr.d_wl <= 1.0)) {
+        return fail(c, FM_ERR_INVALID_ARG, "%s: d_wl must be in (0, 1] (0 selects 0.5)", name);
+    }
     fm_status st = set_device(c);
     if (st != FM_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     std::vector<fm_frame> fr(n);
     for (int b = 0; b < n; ++b) {
         fm_frame f{};
-        f.arr.M = M;
-        f.arr.d_wl = d_wl;
+        f.arr = arr;
         f.grid = *grid;
         f.p.K = ncols;
         f.p.l = ncols;
@@ -1306,6 +1401,7 @@ fm_status fm_spectrum(fm_ctx* c, const void* U, int n, int M, int ncols, double 
         d.Us = const_cast<float2*>(reinterpret_cast<const float2*>(U)) + (int64_t)b * M * ncols;
         d.P = P + (int64_t)b * grid->L;
         d.qtab = reinterpret_cast<float2*>(c->arena + pl.qtab[pl.grid_of[b]]);
+        if (pl.geom_of[b]) d.pos = reinterpret_cast<const float2*>(c->arena + pl.pos_tab[pl.geom_of[b] - 1]);
         ds[b] = d;
     }
     FrameDesc* dd;
@@ -1315,7 +1411,22 @@ fm_status fm_spectrum(fm_ctx* c, const void* U, int n, int M, int ncols, double 
     const Maxes mx = maxes_of(ds);
     st = stage(c, kStGrid, s, [&] { return fm::launch_grid_table(dg, (int)pl.grids.size(), mx.L, nullptr, 0, s); });
     if (st != FM_OK) return st;
-    return stage(c, kStScan, s, [&] { return fm::launch_scan(dd, n, mx.L, mx.M, mx.kpad, s); });
+    return stage(c, kStScan, s, [&] { return fm::launch_scan(dd, n, mx.L, mx.M, mx.kpad, mx.scan_smem, s); });
+}
+
+fm_status fm_spectrum(fm_ctx* c, const void* U, int n, int M, int ncols, double d_wl, const fm_grid* grid, float* P,
+                      fm_stream stream) {
+    fm_array arr{};
+    arr.M = M;
+    arr.d_wl = d_wl;
+    return spectrum_impl(c, U, n, arr, ncols, grid, P, stream, "fm_spectrum");
+}
+
+fm_status fm_spectrum_array(fm_ctx* c, const void* U, int n, const fm_array* arr, int ncols, const fm_grid* grid,
+                            float* P, fm_stream stream) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (!arr) return fail(c, FM_ERR_INVALID_ARG, "fm_spectrum_array: arr is NULL");
+    return spectrum_impl(c, U, n, *arr, ncols, grid, P, stream, "fm_spectrum_array");
 }
 
 fm_status fm_peaks(fm_ctx* c, const float* P, int n, int L, int K, const fm_grid* grid, int* peak_idx,
@@ -1445,6 +1556,13 @@ fm_status fm_set_sketch_path(fm_ctx* c, int path) {
 
 int fm_last_sketch_path(const fm_ctx* c) { return c ? c->last_sketch_path : 0; }
 
+fm_status fm_set_sweep_cap(fm_ctx* c, int cap) {
+    if (!c) return FM_ERR_INVALID_ARG;
+    if (cap < 0 || cap > 30) return fail(c, FM_ERR_INVALID_ARG, "sweep cap %d not in [0, 30]", cap);
+    c->sweep_cap = cap;
+    return FM_OK;
+}
+
 uint64_t fm_launch_count(const fm_ctx* c) { return c ? c->launches + c->serve_launches : 0; }
 
 // ------------------------------------------------------------ serving ----
@@ -1473,12 +1591,16 @@ static size_t serve_held(const fm_ctx* c) {
 
 static void serve_progress(fm_ctx* c) {
     // retire finished slots
+    // (any result but "not ready" ends the batch: an error fails its tickets, whose
+    // fm_serve_poll then returns FM_ERR_CUDA, and is kept as the context's message)
     for (fm_ctx::Slot* sl : c->slots) {
-        if (sl->busy && cudaEventQuery(sl->ev) == cudaSuccess) {
-            for (uint64_t t : sl->tickets) c->done[t] = 1;
-            sl->tickets.clear();
-            sl->busy = false;
-        }
+        if (!sl->busy) continue;
+        const cudaError_t q = cudaEventQuery(sl->ev);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) cuda_fail(c, q, "serving batch");
+        for (uint64_t t : sl->tickets) c->done[t] = (q == cudaSuccess) ? 1 : -1;
+        sl->tickets.clear();
+        sl->busy = false;
     }
     std::vector<fm_frame> batch;
     while (!c->queue.empty()) {
@@ -1499,6 +1621,7 @@ static void serve_progress(fm_ctx* c) {
             sl->sub->cov_path = c->cov_path;
             sl->sub->scan_path = c->scan_path;
             sl->sub->sketch_path = c->sketch_path;
+            sl->sub->sweep_cap = c->sweep_cap;
             c->slots.push_back(sl);
             pick = sl;
         }

@@ -10,7 +10,6 @@
 // context.  The array is part of the loaded module: every GPU that loads this
 // library holds it (kNoAllocScratchBytes) until the process exits.
 #include <cmath>
-#include <mutex>
 
 #include "fm_internal.cuh"
 
@@ -25,22 +24,14 @@ constexpr size_t kNoAllocScratchBytes = kTabOff + sizeof(float2) * kNoAllocMaxL;
 
 static __device__ __align__(256) unsigned char g_spectrum_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-char* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once per
-// device (the host-side name g_spectrum_scratch is only a stand-in).
+// Device address of the scratch array on the current device.  The host-side name
+// g_spectrum_scratch is only a stand-in for it; the lookup is cheap, so every call
+// makes it afresh and a device reset or a new primary context between calls never
+// leaves a stale address behind.
 fm_status scratch_on_current_device(char** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FM_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_spectrum_scratch) != cudaSuccess || p == nullptr) return FM_ERR_CUDA;
-        g_scratch_addr[dev] = static_cast<char*>(p);
-    }
-    *out = g_scratch_addr[dev];
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_spectrum_scratch) != cudaSuccess || p == nullptr) return FM_ERR_CUDA;
+    *out = static_cast<char*>(p);
     return FM_OK;
 }
 
@@ -89,6 +80,6 @@ extern "C" fm_status fm_spectrum_noalloc(const void* U, int n_frames, int M, int
     const fm::FrameDesc* dd = reinterpret_cast<const fm::FrameDesc*>(scratch);
     const fm::GridDesc* dg = reinterpret_cast<const fm::GridDesc*>(scratch + kGridOff);
     e = fm::launch_grid_table(dg, 1, grid->L, nullptr, 0, s);
-    if (e == cudaSuccess) e = fm::launch_scan(dd, n_frames, grid->L, M, ncols, s);
+    if (e == cudaSuccess) e = fm::launch_scan(dd, n_frames, grid->L, M, ncols, fm::scan_smem_elems(M, ncols, false), s);
     return e == cudaSuccess ? FM_OK : FM_ERR_CUDA;
 }

@@ -1,6 +1,9 @@
 // scan.cu -- MUSIC pseudo-spectrum on the angle grid (Eq. 5 / Eq. 10):
 //   P(theta_i) = 1 / (||a(theta_i)||^2 - ||U_s^H a(theta_i)||^2),
-//   a_m(theta) = exp(j pi m q),  q = 2 d_wl sin(theta),  ||a||^2 = M.
+//   a_m(theta) = exp(j pi m q),  q = 2 d_wl sin(theta),  ||a||^2 = M
+// for a uniform array; for explicit element positions x_m (wavelengths)
+// a_m(theta) = exp(j pi x_m q) with q = 2 sin(theta) (steer_pos, one sincospi per
+// element and angle; the positions sit in shared memory beside U_s).
 //
 // Steering vectors are generated in registers, never stored: each thread owns
 // one angle, splits m = 64 m1 + m0 and forms a_m = c_{m1} b_{m0} with
@@ -40,10 +43,11 @@ __global__ void grid_table_kernel(const GridDesc* __restrict__ grids, int n_grid
 }
 
 // c_k += sum over m = 64 b + m0 (m0 = m0_begin, m0_begin + m0_stride, ... < min(64, M))
-// of conj(U_s[m][k]) a_m(theta), with U_s in shared memory.
+// of conj(U_s[m][k]) a_m(theta), with U_s in shared memory (rows of kp4 = the column
+// count rounded up to 4, zero-padded; KP >= kp4 accumulators, those past kp4 stay 0).
 template <int KP, int NB>
-__device__ __forceinline__ void accumulate_angle(const float2* __restrict__ Usm, int M, float2 qq, int m0_begin,
-                                                 int m0_stride, float2 (&acc)[KP]) {
+__device__ __forceinline__ void accumulate_angle(const float2* __restrict__ Usm, int kp4, int M, float2 qq,
+                                                 int m0_begin, int m0_stride, float2 (&acc)[KP]) {
     const int nb = (M + 63) / 64;
     float2 cb[NB];
 #pragma unroll
@@ -61,13 +65,45 @@ __device__ __forceinline__ void accumulate_angle(const float2* __restrict__ Usm,
             const int m = 64 * b + m0;
             if (b < nb && m < M) {
                 const float2 a = cmul(cb[b], bm);
-                const float4* urow = reinterpret_cast<const float4*>(Usm + m * KP);
+                const float4* urow = reinterpret_cast<const float4*>(Usm + m * kp4);
 #pragma unroll
                 for (int k2 = 0; k2 < KP / 2; ++k2) {
+                    if (2 * k2 >= kp4) break;
                     const float4 u = urow[k2];
                     cfmac(part[2 * k2], make_float2(u.x, u.y), a);
                     cfmac(part[2 * k2 + 1], make_float2(u.z, u.w), a);
                 }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KP; ++k) acc[k] = cadd(acc[k], part[k]);
+    }
+}
+
+// The same sum for an array with explicit element positions (in shared memory, pos):
+// one steer_pos per element; m runs over the residue class m0_begin mod m0_stride of
+// each 64-element block, partial sums per block (two-level sum, as above).
+template <int KP, int NB>
+__device__ __forceinline__ void accumulate_angle_pos(const float2* __restrict__ Usm, int kp4,
+                                                     const float2* __restrict__ pos, int M, float2 qq, int m0_begin,
+                                                     int m0_stride, float2 (&acc)[KP]) {
+#pragma unroll
+    for (int k = 0; k < KP; ++k) acc[k] = make_float2(0.f, 0.f);
+    const int nb = (M + 63) / 64;
+    for (int b = 0; b < nb; ++b) {
+        float2 part[KP];
+#pragma unroll
+        for (int k = 0; k < KP; ++k) part[k] = make_float2(0.f, 0.f);
+        const int m_end = min(64 * b + 64, M);
+        for (int m = 64 * b + m0_begin; m < m_end; m += m0_stride) {
+            const float2 a = steer_pos(pos[m], qq.x, qq.y);
+            const float4* urow = reinterpret_cast<const float4*>(Usm + m * kp4);
+#pragma unroll
+            for (int k2 = 0; k2 < KP / 2; ++k2) {
+                if (2 * k2 >= kp4) break;
+                const float4 u = urow[k2];
+                cfmac(part[2 * k2], make_float2(u.x, u.y), a);
+                cfmac(part[2 * k2 + 1], make_float2(u.z, u.w), a);
             }
         }
 #pragma unroll
@@ -100,12 +136,11 @@ __device__ __forceinline__ void store_spectrum(const FrameDesc* dp, int i, int M
 __host__ __device__ constexpr int fix_groups(int kp) { return kp <= 8 ? 8 : (kp == 16 ? 4 : 2); }
 constexpr int kFixChunks = 4;
 
-// Usm (M x KP, zero-padded columns) <- U_s (M x kp): float4 copies issued four at a
+// Usm (M x kp4, zero-padded columns) <- U_s (M x kp): float4 copies issued four at a
 // time when the layouts agree, else element by element.
-template <int KP>
-__device__ __forceinline__ void load_us(const float2* __restrict__ Us, float2* Usm, int M, int kp) {
-    if (kp == KP && (reinterpret_cast<uintptr_t>(Us) & 15) == 0) {
-        const int n4 = M * KP / 2;  // KP is even
+__device__ __forceinline__ void load_us(const float2* __restrict__ Us, float2* Usm, int M, int kp, int kp4) {
+    if (kp == kp4 && (reinterpret_cast<uintptr_t>(Us) & 15) == 0) {
+        const int n4 = M * kp4 / 2;  // kp4 is a multiple of 4
         const float4* __restrict__ src = reinterpret_cast<const float4*>(Us);
         float4* dst = reinterpret_cast<float4*>(Usm);
         for (int e = threadIdx.x; e < n4; e += 4 * kThreads) {
@@ -119,8 +154,8 @@ __device__ __forceinline__ void load_us(const float2* __restrict__ Us, float2* U
         }
         return;
     }
-    for (int e = threadIdx.x; e < M * KP; e += kThreads) {
-        const int m = e / KP, k = e % KP;
+    for (int e = threadIdx.x; e < M * kp4; e += kThreads) {
+        const int m = e / kp4, k = e % kp4;
         Usm[e] = (k < kp) ? Us[(int64_t)m * kp + k] : make_float2(0.f, 0.f);
     }
 }
@@ -128,10 +163,10 @@ __device__ __forceinline__ void load_us(const float2* __restrict__ Us, float2* U
 template <int KP, int NB, bool FIXUP>
 __global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restrict__ descs) {
     extern __shared__ float4 smem_raw[];
-    float2* Usm = reinterpret_cast<float2*>(smem_raw);  // [M][KP]
+    float2* Usm = reinterpret_cast<float2*>(smem_raw);  // [M][kp4]
     const FrameDesc* dp = descs + blockIdx.y;
     if ((dp->scan_tc != 0) != FIXUP) return;  // the plain scan skips tensor-core frames, the fixup the others
-    const int M = dp->M, L = dp->L, kp = dp->kpad;
+    const int M = dp->M, L = dp->L, kp = dp->kpad, kp4 = (kp + 3) & ~3;
     const int i0 = blockIdx.x * kThreads * (FIXUP ? kFixChunks : 1);
     if (i0 >= L) return;
     const float2* __restrict__ Us = dp->Us;
@@ -172,13 +207,21 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restr
         }
         // s_list is ordered by the __syncthreads after the U_s load
     }
-    load_us<KP>(Us, Usm, M, kp);
+    load_us(Us, Usm, M, kp, kp4);
+    // element positions of a non-uniform array follow U_s in shared memory
+    float2* possm = Usm + (size_t)M * kp4;
+    const bool has_pos = dp->pos != nullptr;
+    if (has_pos)
+        for (int m = threadIdx.x; m < M; m += kThreads) possm[m] = dp->pos[m];
     __syncthreads();
     float2 acc[KP];
     if (!FIXUP) {
         const int i = i0 + threadIdx.x;
         if (i >= L) return;
-        accumulate_angle<KP, NB>(Usm, M, dp->qtab[i], 0, 1, acc);
+        if (has_pos)
+            accumulate_angle_pos<KP, NB>(Usm, kp4, possm, M, dp->qtab[i], 0, 1, acc);
+        else
+            accumulate_angle<KP, NB>(Usm, kp4, M, dp->qtab[i], 0, 1, acc);
         store_spectrum<KP>(dp, i, M, acc);
         return;
     }
@@ -190,8 +233,10 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restr
         const int a = base + grp * 32 + lane;
         const bool act = a < n_fix;
         const int i = act ? s_list[a] : 0;
-        if (act) {
-            accumulate_angle<KP, NB>(Usm, M, dp->qtab[i], g, G, acc);
+        if (act && has_pos) {
+            accumulate_angle_pos<KP, NB>(Usm, kp4, possm, M, dp->qtab[i], g, G, acc);
+        } else if (act) {
+            accumulate_angle<KP, NB>(Usm, kp4, M, dp->qtab[i], g, G, acc);
         } else {
 #pragma unroll
             for (int k = 0; k < KP; ++k) acc[k] = make_float2(0.f, 0.f);
@@ -223,8 +268,8 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restr
 }
 
 template <int KP, int NB, bool FIXUP>
-cudaError_t launch_kp(const FrameDesc* d, int n_frames, int max_L, int max_M, cudaStream_t s) {
-    const size_t smem = sizeof(float2) * (size_t)max_M * KP;
+cudaError_t launch_kp(const FrameDesc* d, int n_frames, int max_L, size_t smem_elems, cudaStream_t s) {
+    const size_t smem = sizeof(float2) * smem_elems;
     const size_t static_smem = FIXUP ? sizeof(int) * (kThreads * kFixChunks + kFixChunks * kThreads / 32) +
                                            sizeof(float2) * kThreads * 8
                                      : sizeof(int) * (1 + kThreads / 32) + sizeof(float2);
@@ -241,19 +286,20 @@ cudaError_t launch_kp(const FrameDesc* d, int n_frames, int max_L, int max_M, cu
 }
 
 template <int NB, bool FIXUP>
-cudaError_t launch_nb(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s) {
-    if (max_kpad <= 4) return launch_kp<4, NB, FIXUP>(d, n_frames, max_L, max_M, s);
-    if (max_kpad <= 8) return launch_kp<8, NB, FIXUP>(d, n_frames, max_L, max_M, s);
-    if (max_kpad <= 16) return launch_kp<16, NB, FIXUP>(d, n_frames, max_L, max_M, s);
-    return launch_kp<32, NB, FIXUP>(d, n_frames, max_L, max_M, s);
+cudaError_t launch_nb(const FrameDesc* d, int n_frames, int max_L, int max_kpad, size_t smem_elems, cudaStream_t s) {
+    if (max_kpad <= 4) return launch_kp<4, NB, FIXUP>(d, n_frames, max_L, smem_elems, s);
+    if (max_kpad <= 8) return launch_kp<8, NB, FIXUP>(d, n_frames, max_L, smem_elems, s);
+    if (max_kpad <= 16) return launch_kp<16, NB, FIXUP>(d, n_frames, max_L, smem_elems, s);
+    return launch_kp<32, NB, FIXUP>(d, n_frames, max_L, smem_elems, s);
 }
 
 template <bool FIXUP>
-cudaError_t launch_scan_t(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s) {
-    if (max_M <= 128) return launch_nb<2, FIXUP>(d, n_frames, max_L, max_M, max_kpad, s);
-    if (max_M <= 256) return launch_nb<4, FIXUP>(d, n_frames, max_L, max_M, max_kpad, s);
-    if (max_M <= 512) return launch_nb<8, FIXUP>(d, n_frames, max_L, max_M, max_kpad, s);
-    return launch_nb<16, FIXUP>(d, n_frames, max_L, max_M, max_kpad, s);
+cudaError_t launch_scan_t(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, size_t smem_elems,
+                          cudaStream_t s) {
+    if (max_M <= 128) return launch_nb<2, FIXUP>(d, n_frames, max_L, max_kpad, smem_elems, s);
+    if (max_M <= 256) return launch_nb<4, FIXUP>(d, n_frames, max_L, max_kpad, smem_elems, s);
+    if (max_M <= 512) return launch_nb<8, FIXUP>(d, n_frames, max_L, max_kpad, smem_elems, s);
+    return launch_nb<16, FIXUP>(d, n_frames, max_L, max_kpad, smem_elems, s);
 }
 
 }  // namespace
@@ -267,12 +313,14 @@ cudaError_t launch_grid_table(const GridDesc* g, int n_grids, int max_L, const F
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s) {
-    return launch_scan_t<false>(d, n_frames, max_L, max_M, max_kpad, s);
+cudaError_t launch_scan(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, size_t smem_elems,
+                        cudaStream_t s) {
+    return launch_scan_t<false>(d, n_frames, max_L, max_M, max_kpad, smem_elems, s);
 }
 
-cudaError_t launch_scan_fixup(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, cudaStream_t s) {
-    return launch_scan_t<true>(d, n_frames, max_L, max_M, max_kpad, s);
+cudaError_t launch_scan_fixup(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, size_t smem_elems,
+                              cudaStream_t s) {
+    return launch_scan_t<true>(d, n_frames, max_L, max_M, max_kpad, smem_elems, s);
 }
 
 }  // namespace fm

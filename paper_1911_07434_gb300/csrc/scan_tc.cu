@@ -4,7 +4,8 @@
 // Frames that share M and the angle grid share their steering vectors, so the
 // scan of a batch is one real GEMM per 128-angle tile:
 //   D[i][n] = sum_k A[i][k] B[n][k],  A = steering rows [ar_0, ai_0, ar_1, ai_1, ...]
-//   (a_m = ar + j ai = e^{j pi m q_i}), B = two rows per (frame f, column k of U_s):
+//   (a_m = ar + j ai = e^{j pi m q_i}, or e^{j pi x_m q_i} for a group whose array has
+//   explicit element positions x_m), B = two rows per (frame f, column k of U_s):
 //   [ur_m, ui_m]_m -> Re(u^H a),  [-ui_m, ur_m]_m -> Im(u^H a),
 // and P_f(i) = 1 / (M - sum_k (Re^2 + Im^2)).  A is generated in registers by
 // the CTA itself (the exact phase reduction of scan.cu, one sincospi per
@@ -80,7 +81,17 @@ __global__ void scan_bprep_kernel(const FrameDesc* __restrict__ descs, int n_fra
     im_row[s * 32 + 16 + p + 1] = __uint_as_float(lo[1]);
 }
 
-template <int NCP>
+// Steering entry m of angle row (q_hi, q_lo): a uniform array, or the element
+// positions of the scan group (POS; every frame of a group shares them).
+template <bool POS>
+__device__ __forceinline__ float2 steer_elem(int m, float2 qq, const float2* __restrict__ pos) {
+    if constexpr (POS)
+        return steer_pos(pos[m], qq.x, qq.y);
+    else
+        return steer_exact(m, qq.x, qq.y);
+}
+
+template <int NCP, bool POS>
 __global__ void __launch_bounds__(kThreads, 1)
     scan_tc_kernel(const FrameDesc* __restrict__ descs, int n_frames, const CUtensorMap* __restrict__ tmB, int M,
                    int Mp, int L, int prec) {
@@ -189,6 +200,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int r = (threadIdx.x - 64) & (kRowsA - 1), g = (threadIdx.x - 64) >> 7;
         const int i = i0 + r;
         const float2 qq = (i < L) ? descs[0].qtab[i] : make_float2(0.f, 0.f);
+        const float2* __restrict__ pos = descs[0].pos;
         for (int s = 0; s < nstages; ++s) {
             const int slot = s % kNStages;
             if (!mbar_wait(&empty[slot], ((uint32_t)(s / kNStages) & 1u) ^ 1u, abort_flag)) break;
@@ -198,8 +210,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int cc = 0; cc < 2; ++cc) {
                     const int c = 2 * g + cc;
                     const int m0 = 8 * s + 2 * c;
-                    const float2 a0 = (i < L && m0 < M) ? steer_exact(m0, qq.x, qq.y) : make_float2(0.f, 0.f);
-                    const float2 a1 = (i < L && m0 + 1 < M) ? steer_exact(m0 + 1, qq.x, qq.y) : make_float2(0.f, 0.f);
+                    const float2 a0 = (i < L && m0 < M) ? steer_elem<POS>(m0, qq, pos) : make_float2(0.f, 0.f);
+                    const float2 a1 = (i < L && m0 + 1 < M) ? steer_elem<POS>(m0 + 1, qq, pos) : make_float2(0.f, 0.f);
                     *reinterpret_cast<uint2*>(arow + swz(r, c >> 1) + 8 * (c & 1)) =
                         make_uint2(bf16x2_rn(a0.x, a0.y), bf16x2_rn(a1.x, a1.y));
                 }
@@ -213,8 +225,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint4 hi, lo;
                 uint32_t h[2], w[2];
                 const int m0 = 8 * s + 2 * c;
-                float2 a0 = (i < L && m0 < M) ? steer_exact(m0, qq.x, qq.y) : make_float2(0.f, 0.f);
-                float2 a1 = (i < L && m0 + 1 < M) ? steer_exact(m0 + 1, qq.x, qq.y) : make_float2(0.f, 0.f);
+                float2 a0 = (i < L && m0 < M) ? steer_elem<POS>(m0, qq, pos) : make_float2(0.f, 0.f);
+                float2 a1 = (i < L && m0 + 1 < M) ? steer_elem<POS>(m0 + 1, qq, pos) : make_float2(0.f, 0.f);
                 split2(a0.x, a0.y, h, w);
                 hi.x = h[0];
                 hi.y = h[1];
@@ -301,18 +313,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-template <int NCP>
-cudaError_t launch_ncp(const FrameDesc* d, int n_frames, const void* tmB, int M, int Mp, int L, int prec,
-                       cudaStream_t s) {
+template <int NCP, bool POS>
+cudaError_t launch_ncp_t(const FrameDesc* d, int n_frames, const void* tmB, int M, int Mp, int L, int prec,
+                         cudaStream_t s) {
     cudaError_t e =
-        cudaFuncSetAttribute(scan_tc_kernel<NCP>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        cudaFuncSetAttribute(scan_tc_kernel<NCP, POS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     const int fpc = kRowsB / (2 * NCP);
     dim3 grid((L + kRowsA - 1) / kRowsA, (n_frames + fpc - 1) / fpc);
     count_launch();
-    scan_tc_kernel<NCP><<<grid, kThreads, kSmemBytes, s>>>(d, n_frames, reinterpret_cast<const CUtensorMap*>(tmB),
-                                                           M, Mp, L, prec);
+    scan_tc_kernel<NCP, POS><<<grid, kThreads, kSmemBytes, s>>>(d, n_frames, reinterpret_cast<const CUtensorMap*>(tmB),
+                                                                M, Mp, L, prec);
     return cudaGetLastError();
+}
+
+template <int NCP>
+cudaError_t launch_ncp(const FrameDesc* d, int n_frames, const void* tmB, int M, int Mp, int L, int prec, bool pos,
+                       cudaStream_t s) {
+    return pos ? launch_ncp_t<NCP, true>(d, n_frames, tmB, M, Mp, L, prec, s)
+               : launch_ncp_t<NCP, false>(d, n_frames, tmB, M, Mp, L, prec, s);
 }
 
 }  // namespace
@@ -323,7 +342,7 @@ int scan_tc_ncp(int ncols) {
     return p;
 }
 
-cudaError_t launch_scan_tc(const FrameDesc* d, int n_frames, int M, int ncols, int L, int prec, float* bprep,
+cudaError_t launch_scan_tc(const FrameDesc* d, int n_frames, int M, int ncols, int L, int prec, bool pos, float* bprep,
                            const void* tmB, cudaStream_t s) {
     const int ncp = scan_tc_ncp(ncols);
     const int Mp = (M + 7) / 8 * 8;
@@ -333,11 +352,11 @@ cudaError_t launch_scan_tc(const FrameDesc* d, int n_frames, int M, int ncols, i
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     switch (ncp) {
-        case 1: return launch_ncp<1>(d, n_frames, tmB, M, Mp, L, prec, s);
-        case 2: return launch_ncp<2>(d, n_frames, tmB, M, Mp, L, prec, s);
-        case 4: return launch_ncp<4>(d, n_frames, tmB, M, Mp, L, prec, s);
-        case 8: return launch_ncp<8>(d, n_frames, tmB, M, Mp, L, prec, s);
-        default: return launch_ncp<16>(d, n_frames, tmB, M, Mp, L, prec, s);
+        case 1: return launch_ncp<1>(d, n_frames, tmB, M, Mp, L, prec, pos, s);
+        case 2: return launch_ncp<2>(d, n_frames, tmB, M, Mp, L, prec, pos, s);
+        case 4: return launch_ncp<4>(d, n_frames, tmB, M, Mp, L, prec, pos, s);
+        case 8: return launch_ncp<8>(d, n_frames, tmB, M, Mp, L, prec, pos, s);
+        default: return launch_ncp<16>(d, n_frames, tmB, M, Mp, L, prec, pos, s);
     }
 }
 

@@ -560,8 +560,8 @@ __device__ void sort_desc(const float* w, int* perm, int n) {
 // column order by eigenvalue descending (ties: lower index).  One round = one
 // set of disjoint rotations: phase A computes them, phase B applies U^H A U as
 // independent 2x2 blocks (k, k') and rotates the columns of Z.  Returns the
-// number of sweeps or -1 if the sweep cap was hit.
-__device__ int jacobi(float2* A, float2* Z, float* w, int* perm, int n, const Sm& sm) {
+// number of sweeps or -1 if `cap` sweeps did not converge.
+__device__ int jacobi(float2* A, float2* Z, float* w, int* perm, int n, const Sm& sm, int cap) {
     const int ne = n + (n & 1), np = ne / 2, nr = ne - 1;
     const int nblk = np * (np + 1) / 2, nitems = nblk + np * n;
     for (int e = threadIdx.x; e < n * n; e += kThreads)
@@ -579,7 +579,7 @@ __device__ int jacobi(float2* A, float2* Z, float* w, int* perm, int n, const Sm
     for (int e = threadIdx.x; e < kMaxSweeps; e += kThreads) sm.flags[e] = 0;
     __syncthreads();
     int sweeps = -1;
-    for (int sweep = 0; sweep < kMaxSweeps && nr > 0; ++sweep) {
+    for (int sweep = 0; sweep < cap && nr > 0; ++sweep) {
         for (int r = 0; r < nr; ++r) {
             if (threadIdx.x < np) {
                 const int k = threadIdx.x;
@@ -700,8 +700,10 @@ __device__ int jacobi(float2* A, float2* Z, float* w, int* perm, int n, const Sm
 // at the start of every sweep and updated by each rotation (a - t|g|, b + t|g|),
 // so a pair costs one reduced inner product.  Working copy column-major in Wc;
 // eigenvectors (row-major, Z[i n + k]) into Z, eigenvalues into w, and perm
-// orders them descending.  Returns the sweeps used, -1 without convergence.
-__device__ int eig_onesided(const float2* Frm, float2* Wc, float2* Z, float* w, int* perm, int n, const Sm& sm) {
+// orders them descending.  Returns the sweeps used, -1 without convergence within
+// `cap` sweeps.
+__device__ int eig_onesided(const float2* Frm, float2* Wc, float2* Z, float* w, int* perm, int n, const Sm& sm,
+                             int cap) {
     const int ne = n + (n & 1), np = ne / 2, nr = ne - 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // one pair per half-warp and slot: 16 lanes hold the pair's two columns (up to kE
@@ -722,7 +724,7 @@ __device__ int eig_onesided(const float2* Frm, float2* Wc, float2* Z, float* w, 
     // largest |g|^2 / (a b) met in the sweep, as int bits (non-negative floats order as ints)
     int* sweep_max = sm.flags + kMaxSweeps + 6;
     int sweeps = -1;
-    for (int sweep = 0; sweep < kMaxSweeps && nr > 0; ++sweep) {
+    for (int sweep = 0; sweep < cap && nr > 0; ++sweep) {
         if (threadIdx.x == 0) *sweep_max = 0;
         for (int k = warp; k < n; k += kWarps) {  // exact column norms for this sweep
             float a = 0.f;
@@ -986,6 +988,9 @@ __global__ void __launch_bounds__(kThreads, 3) small_cluster_kernel(const FrameD
     const int rows = min(Mr, M - r0);
     Sm sm;
     smem_layout(Mr, l, &sm, reinterpret_cast<char*>(smem_raw));
+    // sweeps allowed in the eigensolves (a host-set cap below the solver's own exercises
+    // the no-convergence report on ordinary data)
+    const int cap = dp->sweep_cap > 0 ? min(dp->sweep_cap, kMaxSweeps) : kMaxSweeps;
 
     load_rows(dp->C, sm.Cs, r0, rows, l);
     if (mode == kOrth) {
@@ -1072,7 +1077,7 @@ __global__ void __launch_bounds__(kThreads, 3) small_cluster_kernel(const FrameD
         __syncthreads();
     } else {
         // eigenvalue pseudo-inverse: H = Z diag(w) Z^H, B = (R_c Z) diag(w+) (R_c Z)^H
-        const int s0 = jacobi(sm.H, sm.Z, sm.w, sm.perm, l, sm);
+        const int s0 = jacobi(sm.H, sm.Z, sm.w, sm.perm, l, sm, cap);
         if (s0 < 0) ok = false;
         if (threadIdx.x == 0) {
             float amax = 0.f;
@@ -1106,13 +1111,13 @@ __global__ void __launch_bounds__(kThreads, 3) small_cluster_kernel(const FrameD
     // Jacobi on B
     int s2;
     if (pd) {
-        s2 = eig_onesided(sm.T, sm.Xf, sm.Z, sm.w, sm.perm, l, sm);  // Xf is free after F was formed
+        s2 = eig_onesided(sm.T, sm.Xf, sm.Z, sm.w, sm.perm, l, sm, cap);  // Xf is free after F was formed
         for (int e = threadIdx.x; e < l * l; e += kThreads) sm.T[e] = sm.H[e];
         __syncthreads();
     } else {
         for (int e = threadIdx.x; e < l * l; e += kThreads) sm.T[e] = sm.H[e];
         __syncthreads();
-        s2 = jacobi(sm.H, sm.Z, sm.w, sm.perm, l, sm);
+        s2 = jacobi(sm.H, sm.Z, sm.w, sm.perm, l, sm, cap);
     }
     const int nc_out = dp->ncols;
     refine_subspace(sm, l, nc_out);

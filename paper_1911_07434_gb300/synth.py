@@ -9,7 +9,8 @@ the CUDA path and the FP64 oracle can be fed from it.  numpy only; it never
 loads the CUDA library.
 
 Signal model (Sec. II-A):  x_m(t) = sum_k a_m(theta_k) s_k(t) + n_m(t), with
-a_m(theta) = exp(j 2 pi d m sin theta) (d in wavelengths, 0.5 = lambda/2),
+a_m(theta) = exp(j 2 pi d m sin theta) (d in wavelengths, 0.5 = lambda/2) for a
+uniform array, or exp(j 2 pi x_m sin theta) for element positions x_m,
 s_k(t) ~ CN(0, P_k) i.i.d. over snapshots and n_m(t) ~ CN(0, sigma^2), i.e.
 (N(0, sigma^2) + j N(0, sigma^2)) / sqrt(2).  SNR_k = 10 log10(P_k / sigma^2).
 """
@@ -50,6 +51,32 @@ def ula_snapshots(rng: np.random.Generator, M: int, T: int, angles_deg, powers, 
     return X.astype(np.complex64)
 
 
+def array_snapshots(rng: np.random.Generator, pos_wl, T: int, angles_deg, powers, sigma2: float) -> np.ndarray:
+    """One frame X (M x T, complex64) of the Sec. II-A model for a linear array whose
+    element m sits at pos_wl[m] wavelengths: a_m(theta) = exp(j 2 pi x_m sin theta)."""
+    x = np.asarray(pos_wl, dtype=np.float64)[:, None]
+    angles = np.deg2rad(np.asarray(angles_deg, dtype=np.float64))
+    powers = np.asarray(powers, dtype=np.float64)
+    K = angles.shape[0]
+    M = x.shape[0]
+    A = np.exp(1j * 2.0 * np.pi * x * np.sin(angles)[None, :])  # M x K
+    S = (rng.standard_normal((K, T)) + 1j * rng.standard_normal((K, T))) * np.sqrt(powers / 2.0)[:, None]
+    N = (rng.standard_normal((M, T)) + 1j * rng.standard_normal((M, T))) * np.sqrt(sigma2 / 2.0)
+    return (A @ S + N).astype(np.complex64)
+
+
+def sparse_virtual_array(M: int, seed: int = 0, fill: float = 0.75, jitter_wl: float = 0.02) -> np.ndarray:
+    """Element positions (wavelengths, ascending) of a sparse virtual array: M of the
+    ceil(M / fill) sites of a half-wavelength lattice, drawn at random (the first and
+    last site always kept), each moved by a uniform offset in +-jitter_wl (residual
+    placement error of a cascaded MIMO layout).  Non-uniform and off the lattice."""
+    rng = rng_for(seed, 40000 + M)
+    n_sites = int(np.ceil(M / fill))
+    inner = rng.choice(np.arange(1, n_sites - 1), size=M - 2, replace=False)
+    sites = np.sort(np.concatenate([[0, n_sites - 1], inner]))
+    return 0.5 * sites + rng.uniform(-jitter_wl, jitter_wl, size=M)
+
+
 @dataclass
 class Frame:
     X: np.ndarray            # complex64, M x T
@@ -63,6 +90,7 @@ class Frame:
     L: int                   # grid points
     frame_id: int
     d: float = 0.5
+    pos: np.ndarray | None = None   # element positions (wavelengths); None: uniform spacing d
 
     @property
     def M(self) -> int:
@@ -118,6 +146,26 @@ def precision_study_frames(n_frames: int, seed: int = 0) -> Workload:
     wl = massive_mimo_frames(n_frames, seed, M=1024, T=2048, K=16, extra=32, t=1, fov=60.0,
                              min_sep=1.0, snr_lo=5.0, snr_hi=25.0, grid=(-90.0, 90.0, 0.005))
     wl.name = "ula_M1024_T2048_K16_l48_L36001"
+    return wl
+
+
+def sparse_array_frames(n_frames: int, seed: int = 0, M: int = 256, T: int = 512, K: int = 6, extra: int = 10,
+                        t: int = 1, fov: float = 50.0, snr_lo: float = 10.0, snr_hi: float = 20.0,
+                        grid=(-60.0, 60.0, 0.02)) -> Workload:
+    """Frames of one sparse virtual array (sparse_virtual_array(M, seed)): K sources in
+    +-fov deg at least 3 beamwidths apart (beamwidth ~ 1 / aperture in sin(theta)),
+    per-source SNR U(snr_lo, snr_hi) dB, noise power 1, l = K + extra."""
+    pos = sparse_virtual_array(M, seed)
+    aperture = pos.max() - pos.min()
+    sep = 3.0 * np.rad2deg(1.0 / aperture)
+    wl = Workload(f"sparse_M{M}_T{T}_K{K}_aperture{aperture:.1f}wl")
+    th0, st, L = _grid(*grid)
+    for b in range(n_frames):
+        rng = rng_for(seed, 50000 + b)
+        ang = draw_angles(rng, K, -fov, fov, sep)
+        snr = rng.uniform(snr_lo, snr_hi, size=K)
+        X = array_snapshots(rng, pos, T, ang, 10.0 ** (snr / 10.0), 1.0)
+        wl.frames.append(Frame(X, ang, snr, K, K + extra, t, th0, st, L, frame_id=b, pos=pos))
     return wl
 
 

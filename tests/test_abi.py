@@ -35,11 +35,12 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_struct_layout_matches_header(lib):
     # sizes implied by the C declarations on an LP64 ABI
-    assert ctypes.sizeof(binding.FmArray) == 16
+    assert ctypes.sizeof(binding.FmArray) == 24
     assert ctypes.sizeof(binding.FmGrid) == 24
     assert ctypes.sizeof(binding.FmParams) == 40
-    assert binding.FmFrame.arr.offset == 24 and binding.FmFrame.p.offset == 64
-    assert ctypes.sizeof(binding.FmFrame) == 160
+    assert binding.FmFrame.arr.offset == 24 and binding.FmFrame.grid.offset == 48
+    assert binding.FmFrame.p.offset == 72
+    assert ctypes.sizeof(binding.FmFrame) == 168
 
 
 def _frame(M=64, T=200, K=3, l=13, t=1, method=2, L=1801, X=1, out=1):

@@ -415,3 +415,77 @@ def test_frame_peaks_at_true_angles():
         assert n == 3
         est = np.sort(fr.theta0 + fr.step * idx)
         assert np.max(np.abs(est - fr.angles_deg)) <= 0.3, (method, est)
+
+
+# ------------------------------------------------ non-uniform arrays (Sec. II-A) ---
+def test_sparse_lattice_array_reduces_to_zero_padded_ula():
+    """An array whose elements sit on the half-wavelength lattice is a subset S of a ULA's
+    elements, so a_sparse(theta) = a_ula(theta)[S].  With U' = U placed on rows S of the
+    ULA (zeros elsewhere), ||U'^H a_ula|| = ||U^H a_sparse||, hence
+    1/P_sparse - M_sparse = 1/P_ula(U') - M_ula at every angle: the position path reduces
+    to the pinned uniform-array scan (Dirichlet closed form above)."""
+    rng = np.random.default_rng(11)
+    N, M, nc = 40, 23, 4
+    S = np.sort(rng.choice(N, M, replace=False))
+    U = np.linalg.qr(rng.standard_normal((M, nc)) + 1j * rng.standard_normal((M, nc)))[0]
+    Up = np.zeros((N, nc), dtype=complex)
+    Up[S] = U
+    grid = (-89.5, 0.31, 578)
+    Ps = oracle.spectrum(U, *grid, pos=0.5 * S)
+    Pu = oracle.spectrum(Up, *grid)
+    assert np.max(np.abs((1 / Ps - M) - (1 / Pu - N))) < 1e-10
+
+
+def test_spectrum_position_invariances():
+    """Moving the whole array multiplies a(theta) by one phase per angle, and relabelling
+    the elements permutes a(theta) and the rows of U together: neither changes
+    ||U^H a||, so P is unchanged.  Mirroring the positions conjugates a(theta), which
+    conj(U) undoes.  Uniform positions d m give the uniform-array spectrum."""
+    rng = np.random.default_rng(12)
+    pos = synth.sparse_virtual_array(37, seed=5)
+    U = np.linalg.qr(rng.standard_normal((37, 5)) + 1j * rng.standard_normal((37, 5)))[0]
+    grid = (-80.0, 0.4, 401)
+    P = oracle.spectrum(U, *grid, pos=pos)
+    assert np.allclose(oracle.spectrum(U, *grid, pos=pos + 3.25), P, rtol=1e-9)
+    perm = rng.permutation(37)
+    assert np.allclose(oracle.spectrum(U[perm], *grid, pos=pos[perm]), P, rtol=1e-9)
+    assert np.allclose(oracle.spectrum(U.conj(), *grid, pos=-pos), P, rtol=1e-9)
+    assert np.allclose(oracle.spectrum(U, *grid, pos=0.5 * np.arange(37)), oracle.spectrum(U, *grid), rtol=1e-11)
+    # a shifted but unmirrored array is not the mirrored one: the check above is not vacuous
+    assert not np.allclose(oracle.spectrum(U, *grid, pos=-pos), P, rtol=1e-3)
+
+
+def test_sparse_array_signal_subspace_nulls_the_true_angles():
+    """Eq. 4-5 for any geometry: noise-free snapshots of K sources have R = A S A^H with
+    A the array's steering matrix, so U_K spans A and the MUSIC denominator
+    M - ||U_K^H a(theta)||^2 vanishes at every true angle (P -> inf) while it stays
+    well above zero elsewhere.  The data come from the signal model of the input
+    generator, the steering of the scan from the oracle: two codes, one geometry."""
+    pos = synth.sparse_virtual_array(48, seed=3)
+    angles = np.array([-30.0, 7.5, 41.0])
+    rng = synth.rng_for(9, 9)
+    X = synth.array_snapshots(rng, pos, 400, angles, np.array([1.0, 0.5, 2.0]), 0.0)
+    R = oracle.covariance(X)
+    U, lam = oracle.music_subspace(R, 3)
+    th0, step, L = -60.0, 0.5, 241
+    P = oracle.spectrum(U, th0, step, L, pos=pos)
+    on = np.round((angles - th0) / step).astype(int)
+    den = 1.0 / P
+    assert np.all(den[on] < 1e-5 * 48)
+    off = np.ones(L, bool)
+    for i in on:
+        off[max(0, i - 2):i + 3] = False
+    assert np.min(den[off]) > 1e-3
+    idx, n = oracle.peaks(P, 3)
+    assert n == 3 and sorted(idx.tolist()) == sorted(on.tolist())
+
+
+@pytest.mark.parametrize("method,t", [(2, 1), (1, 0), (0, 0)])
+def test_sparse_array_frame_peaks_at_true_angles(method, t):
+    """A noisy sparse-array frame (10-20 dB): standard MUSIC and both fast variants put
+    their K peaks within one grid step of the true angles."""
+    fr = synth.sparse_array_frames(1, seed=2, M=96, T=256, K=4, extra=8, grid=(-60.0, 60.0, 0.05)).frames[0]
+    P, idx, n = oracle.frame(fr.X, fr.K, fr.l, t, method, 0, 0, fr.theta0, fr.step, fr.L, pos=fr.pos)
+    assert n == fr.K
+    est = np.sort(fr.theta0 + fr.step * idx)
+    assert np.max(np.abs(est - fr.angles_deg)) <= 0.1, (est, fr.angles_deg)
