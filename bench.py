@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=20000.0, help="Poisson arrival rate of the serving run")
     ap.add_argument("--uneven-frames", type=int, default=4096, help="frames of the uneven-batch run (0: skip)")
     ap.add_argument("--precision-frames", type=int, default=32, help="frames of the precision study (0: skip)")
+    ap.add_argument("--no-variants", dest="variants", action="store_false",
+                    help="skip the sampling variant and the M = 64 frame")
+    ap.add_argument("--serve-sweep", default="40000,80000,160000,320000",
+                    help="offered rates (frames/s) of the serving sweep, '' to skip")
     return ap.parse_args()
 
 
@@ -188,6 +192,12 @@ def run_reference(args):
 TF32_PER_BF16 = 1.1 / 2.25   # nominal dense TF32 / BF16 tensor rate on GB300 (profiling recipe)
 
 
+def peak_3xtf32():
+    """FP32-equivalent tensor peak: measured BF16 burst x nominal TF32/BF16 ratio / 3."""
+    pk, _ = peaks_json()
+    return pk.get("bf16_tflops", 1895.2) * TF32_PER_BF16 / 3.0
+
+
 def profile_traffic(name):
     """DRAM bytes per launch (read + write) recorded in the committed ncu summary, or None."""
     path = os.path.join(ROOT, "profiles", name)
@@ -253,6 +263,37 @@ def job_rate(world: int, batch: int, steps: int, seconds: float) -> float:
     """Whole-job frames/s: every rank ran `steps` batches of `batch` frames; `seconds` is the
     slowest rank's time."""
     return world * batch * steps / seconds
+
+
+def pct(vals, q):
+    """q-th percentile (0..100) of vals by the nearest-rank rule."""
+    v = sorted(vals)
+    return v[min(len(v) - 1, max(0, int(round(q / 100.0 * len(v) + 0.5)) - 1))]
+
+
+def event_times(fn, reps, stream, warm=3):
+    """Per-call device time (ms) of fn() over reps calls, CUDA events on `stream`, one
+    synchronisation per call (latency, not throughput)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    out = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def frame_flops(M, T, K, l, t, L, method):
+    """Algorithmic flops of one frame: covariance 4 M^2 T (Hermitian half), sketch
+    8 M^2 l per product (t + 1 products for projection, t for sampling), scan 8 L M K."""
+    prods = t + 1 if method == 2 else t
+    return 4.0 * M * M * T + 8.0 * M * M * l * prods + 8.0 * L * M * K
 
 
 def serving_run(binding, synth, dev, n_req, rate, budget_gb=40, pool_per_profile=8, seed=0):
@@ -378,7 +419,15 @@ def uneven_run(binding, synth, dev, n_frames=4096, pool=256, steps=3, seed=0):
     bad = sum(int(b[5].abs().sum().item()) != 0 for b in bufs)
     ctx.close()
     names = {binding.FM_COV_TC: "tensor", binding.FM_COV_SIMT: "cuda-core"}
+    flops = sum(frame_flops(f.M, f.T, f.K, f.l, f.t, f.L, 2) for f in (wl.frames[i % pool] for i in range(n_frames)))
+    best_ms = min(run_ms, run2_ms, graph_ms)
+    tf = flops / (best_ms / 1e3) / 1e12
     return {"frames": n_frames, "distinct_frames": pool, "gpu_launches_per_step": int(per_run),
+            "algorithmic_tflop_per_step": flops / 1e12,
+            "roofline": {"bound": "tensor", "achieved": tf, "unit": "TFLOP/s",
+                         "peak": peak_3xtf32(), "frac": tf / peak_3xtf32(),
+                         "note": "covariance + sketch + scan flops of the batch over its best step time "
+                                 "(fm_run, autotuned or graph replay); peak = the 3xTF32 peak of the headline"},
             "stage_ms": {k: round(v[0], 4) for k, v in stg.items() if v[1]},
             "fm_run": {"frames_per_s": n_frames / (run_ms / 1e3), "ms_per_step": run_ms,
                        "host_wall_ms_per_step": run_wall},
@@ -435,6 +484,91 @@ def precision_run(binding, synth, dev, n_frames=32, steps=3, seed=0):
             out[f"{names[prec]}{'+refine' if refine else ''}"] = r
     ctx.close()
     return {"workload": wl.name, "frames": n_frames, "modes": out}
+
+
+def variants_run(binding, synth, ctx, X, B, M, T, K, l, L, fr0, wl, dev, stream, steps):
+    """The headline workload's other forms: random sampling (Alg. 1, t = 0) and random
+    sampling with the FP32 refinement step, each as a 64-frame batch and as single
+    frames; and the M = 64 frame (K = 3, T = 200, l = 13, t = 2, 1801 angles) with random
+    projection and with standard MUSIC.  Device-timed with CUDA events; U_s of frame 0
+    of each kept for the accuracy check of the CPU leg."""
+    import numpy as np
+    import torch
+    from paper_1911_07434_gb300.full_eig import full_eig_music
+    out = {}
+    P = torch.empty((B, L), dtype=torch.float32, device=dev)
+    idx = torch.empty((B, K), dtype=torch.int32, device=dev)
+    deg = torch.empty((B, K), dtype=torch.float32, device=dev)
+    npk = torch.empty(B, dtype=torch.int32, device=dev)
+    st = torch.zeros(B, dtype=torch.int32, device=dev)
+    for name, t_, refine in (("sampling_t0", 0, 0), ("sampling_t0_refine", 0, 1)):
+        fs = [ctx.frame(X[b], K, l, t_, binding.FM_RAND_SAMPLING, fr0.theta0, fr0.step, L, P[b], idx[b], deg[b],
+                        npk[b:b + 1], seed=0, frame_id=wl.frames[b].frame_id, status=st[b:b + 1], refine=refine)
+              for b in range(B)]
+        batch = event_times(lambda: ctx.run(fs), max(10, steps), stream)
+        ctx.set_timing(True)
+        ctx.run(fs)
+        ctx.set_timing(False)
+        stg = ctx.stage_times(reset=True)
+        tot = sum(v[0] for v in stg.values()) or 1.0
+        U0 = ctx.run_subspace(0, M, K).cpu().numpy()
+        one = event_times(lambda: ctx.run(fs[:1]), 30, stream)
+        ok = int(st.abs().sum()) == 0
+        out[name] = {"method": "random sampling (Alg. 1)" + (" + FP32 refinement step" if refine else ""),
+                     "t": t_, "refine": refine, "frames_per_s": B / (statistics.mean(batch) / 1e3),
+                     "step_ms": {"p50": pct(batch, 50), "p99": pct(batch, 99)},
+                     "single_frame_ms": {"p50": pct(one, 50), "p99": pct(one, 99)},
+                     "stage_share": {k: round(v[0] / tot, 4) for k, v in stg.items() if v[1]},
+                     "status_ok": ok, "_U0": U0}
+    # the M = 64 frame: random projection and standard MUSIC, one frame per call
+    sf = synth.small_frame()
+    Xs = torch.from_numpy(sf.X).to(dev)
+    Ps = torch.empty(sf.L, dtype=torch.float32, device=dev)
+    i_s = torch.empty(sf.K, dtype=torch.int32, device=dev)
+    d_s = torch.empty(sf.K, dtype=torch.float32, device=dev)
+    n_s = torch.empty(1, dtype=torch.int32, device=dev)
+    s_s = torch.zeros(1, dtype=torch.int32, device=dev)
+    f = [ctx.frame(Xs, sf.K, sf.l, sf.t, binding.FM_RAND_PROJECTION, sf.theta0, sf.step, sf.L, Ps, i_s, d_s, n_s,
+                   seed=0, frame_id=0, status=s_s)]
+    proj_ms = event_times(lambda: ctx.run(f), 50, stream)
+    U0 = ctx.run_subspace(0, sf.M, sf.K).cpu().numpy()
+    full_ms = event_times(lambda: full_eig_music(ctx, Xs, sf.K, sf.theta0, sf.step, sf.L), 50, stream)
+    out["small_frame_M64"] = {
+        "workload": "ULA M=64 T=200 K=3 (-20, 5, 30 deg) 10 dB, l=13, t=2, L=1801, one frame per call",
+        "projection": {"frames_per_s": 1e3 / statistics.mean(proj_ms), "p50_ms": pct(proj_ms, 50),
+                       "p99_ms": pct(proj_ms, 99), "peaks_deg": sorted(d_s.cpu().tolist()),
+                       "status_ok": int(s_s.item()) == 0, "_U0": U0},
+        "full_eig_music": {"frames_per_s": 1e3 / statistics.mean(full_ms), "p50_ms": pct(full_ms, 50),
+                           "p99_ms": pct(full_ms, 99)},
+        "p99_speedup_projection_vs_full": pct(full_ms, 99) / pct(proj_ms, 99)}
+    return out
+
+
+def variants_accuracy(variants, wl, small):
+    """Projector distance ||U U^H - U_o U_o^H||_F of frame 0 of each variant to the FP64
+    oracle's subspace from the same X, Omega / I (part of the CPU-baseline leg: the only
+    place the benchmark runs the oracle)."""
+    import numpy as np
+    import oracle
+    fr = wl.frames[0]
+    R = oracle.covariance(fr.X)
+    res = {}
+    for name, t_ in (("sampling_t0", 0), ("sampling_t0_refine", 1)):
+        v = variants.get(name)
+        if not v:
+            continue
+        Uo, _, _ = oracle.fast_music(R, fr.K, fr.l, t_, oracle.SAMPLING, 0, fr.frame_id)
+        U = v.pop("_U0").astype(np.complex128)
+        v["projector_vs_oracle"] = float(np.linalg.norm(U @ U.conj().T - Uo @ Uo.conj().T))
+        if t_ == 1:
+            v["projector_note"] = "against the oracle with t + 1 power steps (the refinement step is one more)"
+    sm = variants.get("small_frame_M64")
+    if sm:
+        Rs = oracle.covariance(small.X)
+        Uo, _, _ = oracle.fast_music(Rs, small.K, small.l, small.t, oracle.PROJECTION, 0, 0)
+        U = sm["projection"].pop("_U0").astype(np.complex128)
+        sm["projection"]["projector_vs_oracle"] = float(np.linalg.norm(U @ U.conj().T - Uo @ Uo.conj().T))
+    return res
 
 
 def main():
@@ -598,30 +732,37 @@ def main():
     # ---- full-eig MUSIC on the same GPU -----------------------------------------
     full = None
     if not args.no_baseline:
-        def full_eig_step():
-            R = ctx.covariance(X)
-            _, V = torch.linalg.eigh(R)                    # cuSOLVER, ascending eigenvalues
-            Uk = V[:, :, -K:].contiguous()
-            Pf = ctx.spectrum(Uk, fr0.theta0, fr0.step, L)
-            return ctx.peaks(Pf, K, fr0.theta0, fr0.step)
-        full_eig_step()
-        torch.cuda.synchronize()
-        fs = 3
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(fs):
-            full_eig_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        fms = e0.elapsed_time(e1) / fs
+        from paper_1911_07434_gb300.full_eig import full_eig_music
+        batch_ms = event_times(lambda: full_eig_music(ctx, X, K, fr0.theta0, fr0.step, L), 20, stream, warm=2)
+        one_ms = event_times(lambda: full_eig_music(ctx, X[:1], K, fr0.theta0, fr0.step, L), 30, stream)
+        fms = statistics.mean(batch_ms)
         full = {"value": B / (fms / 1e3), "unit": UNIT, "ms_per_step": fms,
-                "method": "standard MUSIC: our covariance kernel + torch.linalg.eigh (cuSOLVER) + our scan/peaks",
-                "speedup_fast_vs_full": (value / world) / (B / (fms / 1e3))}
+                "step_ms": {"p50": pct(batch_ms, 50), "p99": pct(batch_ms, 99), "repeats": len(batch_ms)},
+                "single_frame_ms": {"p50": pct(one_ms, 50), "p99": pct(one_ms, 99), "repeats": len(one_ms)},
+                "method": "standard MUSIC (Eq. 4-6): our covariance kernel + torch.linalg.eigh (cuSOLVER) + our "
+                          "scan/peaks (paper_1911_07434_gb300.full_eig)",
+                "speedup_fast_vs_full": (value / world) / (B / (fms / 1e3)),
+                "p99_speedup_single_frame": pct(one_ms, 99) / single["p99_ms"],
+                "p99_speedup_step": pct(batch_ms, 99) / pct(step_ms, 99)}
+
+    # ---- the other workloads of the headline: sampling variant, the M = 64 frame ---
+    variants = None
+    if args.variants:
+        variants = variants_run(binding, synth, ctx, X, B, M, T, K, l, L, fr0, wl, dev, stream, args.steps)
 
     # ---- serving mix: continuous batching under Poisson arrivals ----------------
     serving = None
     if args.serve_requests > 0:
         serving = serving_run(binding, synth, dev, args.serve_requests, args.serve_rate)
+        sweep, limit = [], None
+        for r in [float(x) for x in args.serve_sweep.split(",") if x.strip()]:
+            sv = serving_run(binding, synth, dev, 2000, r)
+            sweep.append({k: sv[k] for k in ("offered_frames_per_s", "frames_per_s", "p50_ms", "p99_ms")})
+            if sv["p99_ms"] > 2.0 and limit is None:
+                limit = r
+        serving["sweep"] = sweep
+        serving["p99_bound_ms"] = 2.0
+        serving["first_rate_over_bound"] = limit
 
     # ---- uneven batch: one fm_run, CUDA graph replay, autotuned paths -----------
     uneven = None
@@ -643,7 +784,13 @@ def main():
                "sample": f"{nfr} frames of the workload through the FP64 C oracle, one frame per process on "
                          f"{workers} host cores ({secs:.1f} s wall)",
                "single_thread": {"value": rate1, "frames": args.cpu_sample, "seconds": secs1}}
+        if variants:
+            variants_accuracy(variants, wl, synth.small_frame())
 
+    if variants:  # U_s kept for the accuracy check are not part of the report
+        for v in variants.values():
+            for sub in (v, v.get("projection", {})):
+                sub.pop("_U0", None)
     srt = sorted(step_ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -658,7 +805,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": roof, "dominant_stage": dom, "stages": stage_summary,
-        "serving": serving, "uneven_batch": uneven, "precision_study": precision, "full_eig_music": full, "cpu_baseline": cpu, "clocks": clk,
+        "serving": serving, "uneven_batch": uneven, "precision_study": precision, "full_eig_music": full,
+        "variants": variants, "cpu_baseline": cpu, "clocks": clk,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

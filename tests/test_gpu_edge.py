@@ -3,7 +3,9 @@ largest sizes the library takes, and the degenerate cases of the method.
 
 * Invalid requests return FM_ERR_INVALID_ARG and launch nothing.
 * Largest sizes: M = 1024, l = 48, a 65,536-point grid; sampled spectrum points against
-  the oracle (every 64th angle) and the peaks at the true angles.
+  the oracle (every 64th angle and the main lobes) and the peaks at the true angles.
+* A Jacobi sweep cap of 1 makes an ordinary frame report FM_ERR_NO_CONVERGENCE; the
+  next frame on the same context, with the cap restored, is clean.
 * Random sampling with l = M keeps every column, so fast MUSIC is exact MUSIC (the
   oracle's full Jacobi eigendecomposition): projector <= 1e-5.
 * Noise-free rank-K data make H = V^H R V singular in exact arithmetic, which takes the
@@ -105,12 +107,21 @@ def test_largest_sizes(lib, ctx):
     assert int(one.st.item()) == 0 and int(one.n.item()) == fr.K
     Uo, _, _ = oracle.fast_music(oracle.covariance(fr.X), fr.K, fr.l, fr.t, 2, 3, fr.frame_id)
     U = ctx.run_subspace(0, 1024, fr.K).cpu().numpy().astype(np.complex128)
-    assert np.linalg.norm(proj(U) - proj(Uo)) <= 1e-5
-    Po = oracle.spectrum(Uo, -90.0, 64 * step, L // 64)
-    Pg = one.P.cpu().numpy().astype(np.float64)[::64]
-    th = -90.0 + 64 * step * np.arange(L // 64)
+    eps = np.linalg.norm(proj(U) - proj(Uo))
+    assert eps <= 1e-5
+    # every 64th angle plus the 64 angles around each true source (main lobes included)
+    th_all = -90.0 + step * np.arange(L)
+    sel = np.arange(0, L, 64)
+    for a in fr.angles_deg:
+        c = int(round((a + 90.0) / step))
+        sel = np.union1d(sel, np.arange(max(0, c - 32), min(L, c + 32)))
+    Pg = one.P.cpu().numpy().astype(np.float64)[sel]
+    Po = np.array([oracle.spectrum(Uo, th_all[i], step, 1)[0] for i in sel])
+    th = th_all[sel]
     far = np.min(np.abs(th[:, None] - fr.angles_deg[None, :]), axis=1) > 2 * np.rad2deg(2.0 / 1024)
     assert np.max(np.abs(10 * np.log10(Pg[far] / Po[far]))) < 0.01
+    # every sampled denominator: |a^H (U U^H - Uo Uo^H) a| <= M eps, plus the scan's rounding
+    assert np.max(np.abs(1.0 / Pg - 1.0 / Po)) <= 1024 * eps + 16 * 2.0 ** -24 * 1024 * fr.K
     est = np.sort(one.deg.cpu().numpy())
     assert np.max(np.abs(est - np.sort(fr.angles_deg))) < 0.01
 
@@ -185,3 +196,30 @@ def test_bounded_wait_reports_timeout_and_context_stays_usable(lib, ctx):
     ctx.run([one.f])
     torch.cuda.synchronize()
     assert int(one.st.item()) == 0 and int(one.n.item()) == fr.K
+
+
+def test_sweep_cap_reports_no_convergence_and_next_frame_is_clean(lib, ctx):
+    """Failure detection of the l x l eigensolves (Alg. 1 / 2's SVD / EVD steps, run as
+    Jacobi sweeps): with one sweep allowed, the solve of an ordinary frame (l = 13)
+    cannot converge, so its status word carries FM_ERR_NO_CONVERGENCE while every output
+    stays finite; with the cap restored the next frame is clean and matches the oracle's
+    peaks."""
+    fr = synth.small_frame()
+    one = One(lib, fr.X, fr.K, fr.l, fr.t, 2, fr.theta0, fr.step, fr.L)
+    ctx.set_sweep_cap(1)
+    try:
+        ctx.run([one.f])
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_sweep_cap(0)
+    assert int(one.st.item()) & (1 << lib.FM_ERR_NO_CONVERGENCE)
+    assert not torch.isnan(one.P).any()
+    two = One(lib, fr.X, fr.K, fr.l, fr.t, 2, fr.theta0, fr.step, fr.L)
+    ctx.run([two.f])
+    torch.cuda.synchronize()
+    assert int(two.st.item()) == 0
+    _, io, no = oracle.frame(fr.X, fr.K, fr.l, fr.t, 2, 3, 0, fr.theta0, fr.step, fr.L)
+    assert int(two.n.item()) == no
+    assert sorted(two.idx.cpu().tolist()) == sorted(io.tolist())
+    with pytest.raises(lib.FmError):
+        ctx.set_sweep_cap(31)
