@@ -73,8 +73,7 @@ typedef enum {
  * and the scan (Eq. 10), when they run on the tensor cores; the accumulator is
  * FP32 in every mode, and the small solves and the main-lobe scan recompute stay
  * FP32 (double-float where stated).  The sketch products (Alg. 1 / 2, Eq. 11) take
- * TF32 operands in TF32 / BF16 mode; in FP32 mode the last one, which the final
- * solve reads, takes 3 TF32 MMAs per product and the ones before it one (see
+ * TF32 operands in TF32 / BF16 mode and 3 TF32 MMAs per product in FP32 mode (see
  * fm_set_sketch_path).  Where the CUDA-core
  * covariance runs instead (X not 16-byte aligned or ldx odd), it is FP32 in
  * every mode.  BF16 keeps FP32's exponent range, so no per-frame scaling is
@@ -320,8 +319,8 @@ int fm_last_scan_path(const fm_ctx* ctx);
 /* ---- sketch kernel selection (same constants) -----------------------------------
  * The sketch products C = R Omega (Alg. 2) and C = R V of the power steps (Eq. 11)
  * run on the tensor cores for every frame whose M is even (R's rows must be
- * 16-byte aligned for TMA): the last product of an FP32 frame with 3 TF32 MMAs
- * per FP32 product (hi*hi + hi*lo + lo*hi), every other product with one.  The
+ * 16-byte aligned for TMA): every product of an FP32 frame with 3 TF32 MMAs per
+ * FP32 product (hi*hi + hi*lo + lo*hi), those of TF32 / BF16 frames with one.  The
  * sampling sketch of Alg. 1 (a column gather) is not a product.  FM_COV_AUTO
  * (default): the tensor cores take the frames that can; FM_COV_TC: the same, and
  * fm_run fails with FM_ERR_INVALID_ARG if a frame with a product cannot;

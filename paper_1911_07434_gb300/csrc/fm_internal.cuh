@@ -45,6 +45,19 @@ struct FrameDesc {
     double theta0, step, d_wl;
 };
 
+// One CTA of the tensor-core covariance: the stages [s0, s1) (16 snapshots each) of the
+// 128 x 128 output tile (ti, tj), ti <= tj, of frame `frame`.  split < 0: the item is the
+// whole tile.  split >= 0: part k of the nparts items that share the tile along T; each
+// writes its partial tile to slot first + k of the partial workspace, and the last one
+// to finish (counter `split`) adds slots first .. first + nparts - 1 in order and writes R.
+struct CovItem {
+    int frame;
+    int ti, tj;
+    int s0, s1;
+    int split;
+    int first, k, nparts;
+};
+
 // One distinct angle grid: its (q_hi, q_lo) table is shared by every frame using it.
 struct GridDesc {
     double theta0, step, d_wl;
@@ -182,11 +195,17 @@ __device__ __forceinline__ void set_status(int* status, int code) {
 }
 
 // Sketch products on the tensor cores (sketch_tc.cu, for frames prepared for it): every
-// product R V (sampling has none at pass 0).  The last product of an FP32 frame, which
-// the final solve reads, takes three TF32 MMAs per FP32 product (sketch_split); the
-// other products take one.
+// product R V (sampling has none at pass 0).  Every product of an FP32 frame takes three
+// TF32 MMAs per FP32 product (sketch_split): the Nystrom core of Alg. 2 is built from the
+// last V = orth(C), so an earlier product rounded to TF32 moves the result itself (by
+// up to 3e-5 in the projector at M = 512), not only the path to it.  TF32 / BF16 frames
+// take one MMA per product.
 __host__ __device__ inline bool sketch_on_tc(int method, int pass) { return pass > 0 || method == FM_RAND_PROJECTION; }
-__host__ __device__ inline bool sketch_split(int prec, int t, int pass) { return prec == FM_PREC_FP32 && pass == t; }
+__host__ __device__ inline bool sketch_split(int prec, int t, int pass) {
+    (void)t;
+    (void)pass;
+    return prec == FM_PREC_FP32;
+}
 __host__ __device__ inline int sketch_tc_lpad(int l) { return (l + 7) / 8 * 8; }
 // Floats per B row of the split layout: ceil(2M / 16) chunks of [hi 16 | lo 16].
 __host__ __device__ inline int64_t sketch_split_rowlen(int M) { return 32 * (int64_t)((2 * M + 15) / 16); }
@@ -205,9 +224,13 @@ extern thread_local uint64_t g_kernel_launches;
 inline void count_launch() { ++g_kernel_launches; }
 
 // Implemented in the .cu files; each returns cudaGetLastError() after launching.
+// counters (nullable): n_counters ints cleared with the status words (the covariance's
+// split-tile counters, so that a run after an aborted one starts from zero)
 cudaError_t launch_grid_table(const GridDesc* g, int n_grids, int max_L, const FrameDesc* d, int n_frames,
-                              cudaStream_t s);
-cudaError_t launch_covariance_tc(const FrameDesc* d, const void* tmaps, int n_frames, int max_M, cudaStream_t s);
+                              int* counters, int n_counters, cudaStream_t s);
+cudaError_t launch_covariance_tc(const FrameDesc* d, const void* tmaps, const CovItem* items, int n_items,
+                                 float2* partials, int* counters, cudaStream_t s);
+constexpr int kCovTile = 128;  // complex rows per side of a covariance output tile
 size_t cov_tc_smem_bytes();
 cudaError_t launch_scan_tc(const FrameDesc* d, int n_frames, int M, int ncols, int L, int prec, bool pos, float* bprep,
                            const void* tmB, cudaStream_t s);

@@ -312,6 +312,129 @@ std::vector<int> geometry_ids(const fm_frame* f, int n, std::vector<const fm_fra
     return id;
 }
 
+// SM count of the current device (152 on GB300; the fallback when no device answers,
+// e.g. for host-only workspace sizing).
+int current_sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        n > 0)
+        return n;
+    cudaGetLastError();
+    return 152;
+}
+
+// Work items of the tensor-core covariance (see cov_tc.cu).  Each 128 x 128 tile of
+// the upper block triangle of every frame is one item, weighted in quarter stages (an
+// off-diagonal tile issues 4 blocks per 16-snapshot stage, a diagonal tile 3), plus a
+// fixed cost per CTA (prologue, first loads, epilogue: about six stages).  Items are
+// ordered longest first, and a greedy longest-first simulation on n_sm SMs (one CTA per
+// SM) finds the tiles that would still run after every other SM has finished; those
+// are split along T into s parts (s in 2..8, the s that shortens the simulated
+// makespan most; each part keeps at least 4 stages).  Small batches gain most: one
+// M = 512 frame's 10 tiles become 80 parts on 152 SMs.
+struct CovPlan {
+    std::vector<fm::CovItem> items;
+    int n_split = 0, n_slots = 0;
+};
+
+constexpr int64_t kCovCtaCost = 24;    // quarter stages per CTA
+constexpr int64_t kCovPartCost = 16;   // extra quarter stages of a split part
+
+int64_t lpt_makespan(const std::vector<int64_t>& w, int n_sm, std::vector<int64_t>* ends = nullptr) {
+    std::vector<int64_t> heap(n_sm, 0);  // min-heap of SM finish times
+    auto cmp = [](int64_t a, int64_t b) { return a > b; };
+    int64_t mk = 0;
+    if (ends) ends->resize(w.size());
+    for (size_t i = 0; i < w.size(); ++i) {
+        std::pop_heap(heap.begin(), heap.end(), cmp);
+        const int64_t e = heap.back() + w[i];
+        heap.back() = e;
+        std::push_heap(heap.begin(), heap.end(), cmp);
+        if (ends) (*ends)[i] = e;
+        mk = std::max(mk, e);
+    }
+    return mk;
+}
+
+// Indices of w sorted by weight, largest first, equal weights in index order.
+std::vector<int> longest_first(const std::vector<int64_t>& w) {
+    std::vector<int> order(w.size());
+    for (size_t i = 0; i < w.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return w[a] > w[b]; });
+    return order;
+}
+
+CovPlan plan_cov_items(const fm_frame* f, int n, int n_sm, bool allow_split) {
+    std::vector<fm::CovItem> tiles;
+    std::vector<int64_t> w;
+    for (int b = 0; b < n; ++b) {
+        const int nt = (f[b].arr.M + fm::kCovTile - 1) / fm::kCovTile;
+        const int ns = (f[b].T + 15) / 16;
+        for (int ti = 0; ti < nt; ++ti)
+            for (int tj = ti; tj < nt; ++tj) {
+                tiles.push_back(fm::CovItem{b, ti, tj, 0, ns, -1, 0, 0, 1});
+                w.push_back((int64_t)ns * (ti == tj ? 3 : 4));
+            }
+    }
+    const std::vector<int> order = longest_first(w);
+    CovPlan plan;
+    std::vector<int64_t> wo(order.size());
+    for (size_t i = 0; i < order.size(); ++i) wo[i] = w[order[i]] + kCovCtaCost;
+    int best_s = 1;
+    std::vector<int64_t> ends;
+    int64_t total = 0;
+    for (int64_t x : wo) total += x;
+    const double late = n_sm > 0 ? 1.02 * (double)total / n_sm : 0.0;  // finishing later: split candidates
+    auto is_candidate = [&](size_t i, int s) { return (double)ends[i] > late && tiles[order[i]].s1 >= 4 * s; };
+    if (allow_split && n_sm > 0 && (int64_t)order.size() <= 8 * (int64_t)n_sm) {
+        int64_t best = lpt_makespan(wo, n_sm, &ends);
+        for (int s : {2, 3, 4, 6, 8}) {
+            std::vector<int64_t> cand;
+            for (size_t i = 0; i < order.size(); ++i) {
+                if (is_candidate(i, s))
+                    for (int k = 0; k < s; ++k) cand.push_back(w[order[i]] / s + kCovCtaCost + kCovPartCost);
+                else
+                    cand.push_back(wo[i]);
+            }
+            std::stable_sort(cand.begin(), cand.end(), [](int64_t a, int64_t b) { return a > b; });
+            const int64_t mk = lpt_makespan(cand, n_sm);
+            if ((double)mk < 0.99 * (double)best) {
+                best = mk;
+                best_s = s;
+            }
+        }
+    }
+    // the items in launch order: whole tiles and the parts of split tiles, longest first
+    std::vector<fm::CovItem> items;
+    std::vector<int64_t> iw;
+    for (size_t i = 0; i < order.size(); ++i) {
+        const fm::CovItem t = tiles[order[i]];
+        if (best_s == 1 || !is_candidate(i, best_s)) {
+            items.push_back(t);
+            iw.push_back(w[order[i]]);
+            continue;
+        }
+        const int ns = t.s1;
+        for (int k = 0; k < best_s; ++k) {
+            fm::CovItem p = t;
+            p.s0 = (int)((int64_t)ns * k / best_s);
+            p.s1 = (int)((int64_t)ns * (k + 1) / best_s);
+            p.split = plan.n_split;
+            p.first = plan.n_slots;
+            p.k = k;
+            p.nparts = best_s;
+            items.push_back(p);
+            iw.push_back(w[order[i]] / best_s);
+        }
+        ++plan.n_split;
+        plan.n_slots += best_s;
+    }
+    const std::vector<int> o2 = longest_first(iw);
+    plan.items.reserve(items.size());
+    for (int i : o2) plan.items.push_back(items[i]);
+    return plan;
+}
+
 struct Plan {
     size_t desc_off, tmap_off, grid_off, pos_off, upload_bytes, total;
     // tensor-core scan groups: maximal runs of consecutive frames sharing M, ncols,
@@ -333,6 +456,9 @@ struct Plan {
     std::vector<size_t> pos_tab;        // offset of geometry k's table (index k - 1)
     std::vector<float2> pos_host;       // every table back to back
     std::vector<size_t> pos_host_at;    // start of table k - 1 in pos_host
+    // tensor-core covariance work items (uploaded), partial tiles and counters of split tiles
+    CovPlan cov;
+    size_t cov_items_off = 0, cov_part_off = 0, cov_cnt_off = 0;
 };
 
 typedef std::tuple<double, double, double, int> GridKey;
@@ -383,7 +509,18 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
             off = aup(off + sizeof(float2) * (size_t)r->arr.M);
         }
     }
+    if (need_R) {
+        pl.cov = plan_cov_items(f, n, current_sm_count(), true);
+        pl.cov_items_off = off;
+        off = aup(off + sizeof(fm::CovItem) * pl.cov.items.size());
+    }
     pl.upload_bytes = off;
+    if (need_R && pl.cov.n_split) {
+        pl.cov_part_off = off;
+        off = aup(off + sizeof(float2) * (size_t)fm::kCovTile * fm::kCovTile * (size_t)pl.cov.n_slots);
+        pl.cov_cnt_off = off;
+        off = aup(off + sizeof(int) * (size_t)pl.cov.n_split);
+    }
     for (size_t g = 0; g < pl.grids.size(); ++g) {
         pl.qtab.push_back(off);
         off = aup(off + sizeof(float2) * (size_t)pl.grids[g].L);
@@ -599,8 +736,12 @@ fm_status choose_cov_path(fm_ctx* c, const std::vector<FrameDesc>& ds, std::vect
     return FM_OK;
 }
 
-fm_status launch_cov(fm_ctx* c, bool tc, FrameDesc* dd, const char* tm_dev, int n, int max_M, cudaStream_t s) {
-    if (tc) return stage(c, 1, s, [&] { return fm::launch_covariance_tc(dd, tm_dev, n, max_M, s); });
+// items / partials / counters: the tensor-core path's work items (device) and the
+// workspace of its split tiles (null when no tile is split)
+fm_status launch_cov(fm_ctx* c, bool tc, FrameDesc* dd, const char* tm_dev, const fm::CovItem* items, int n_items,
+                     float2* partials, int* counters, int n, int max_M, cudaStream_t s) {
+    if (tc)
+        return stage(c, 1, s, [&] { return fm::launch_covariance_tc(dd, tm_dev, items, n_items, partials, counters, s); });
     return stage(c, 1, s, [&] { return fm::launch_covariance(dd, n, max_M, s); });
 }
 
@@ -624,6 +765,8 @@ fm_status upload_descs(fm_ctx* c, const Plan& pl, std::vector<FrameDesc>& ds, co
     std::vector<GridDesc> g = pl.grids;
     for (size_t i = 0; i < g.size(); ++i) g[i].qtab = reinterpret_cast<float2*>(c->arena + pl.qtab[i]);
     if (!g.empty()) memcpy(host + pl.grid_off, g.data(), sizeof(GridDesc) * g.size());
+    if (!pl.cov.items.empty())
+        memcpy(host + pl.cov_items_off, pl.cov.items.data(), sizeof(fm::CovItem) * pl.cov.items.size());
     for (size_t k = 0; k < pl.pos_tab.size(); ++k) {
         const size_t end = k + 1 < pl.pos_host_at.size() ? pl.pos_host_at[k + 1] : pl.pos_host.size();
         memcpy(host + pl.pos_tab[k], pl.pos_host.data() + pl.pos_host_at[k], sizeof(float2) * (end - pl.pos_host_at[k]));
@@ -742,11 +885,29 @@ fm_status fm_destroy(fm_ctx* c) {
 
 const char* fm_last_error(const fm_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
+// The order fm_run processes frames in: the frames of each tensor-core scan group (same
+// M, ncols, prec, grid and geometry) next to each other, otherwise the caller's order.
+static std::vector<int> run_order(const fm_frame* frames, int n) {
+    std::vector<int> order(n);
+    for (int b = 0; b < n; ++b) order[b] = b;
+    const std::vector<int> geo = geometry_ids(frames, n);
+    auto key = [&](int b) {
+        const fm_frame& f = frames[b];
+        return std::make_tuple(f.arr.M, ncols_of(f.p), f.p.prec, f.grid.theta0_deg, f.grid.step_deg, grid_spacing(f),
+                               f.grid.L, geo[b]);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key(x) < key(y); });
+    return order;
+}
+
 size_t fm_workspace_bytes(const fm_frame* frames, int n) {
     if (!frames || n < 1) return 0;
     for (int b = 0; b < n; ++b)
         if (check_frame(frames[b])) return 0;
-    return plan_frames(frames, n, true, true, true, true).total;
+    const std::vector<int> order = run_order(frames, n);
+    std::vector<fm_frame> sorted(n);
+    for (int k = 0; k < n; ++k) sorted[k] = frames[order[k]];
+    return plan_frames(sorted.data(), n, true, true, true, true).total;
 }
 
 // ---- fm_run, split into host preparation and the device chain -----------------
@@ -767,15 +928,7 @@ struct RunPrep {
 
 static fm_status prepare_run(fm_ctx* c, const fm_frame* frames, int n, cudaStream_t s, RunPrep& rp) {
     rp.n = n;
-    rp.order.resize(n);
-    for (int b = 0; b < n; ++b) rp.order[b] = b;
-    const std::vector<int> geo = geometry_ids(frames, n);
-    auto key = [&](int b) {
-        const fm_frame& f = frames[b];
-        return std::make_tuple(f.arr.M, ncols_of(f.p), f.p.prec, f.grid.theta0_deg, f.grid.step_deg, grid_spacing(f),
-                               f.grid.L, geo[b]);
-    };
-    std::stable_sort(rp.order.begin(), rp.order.end(), [&](int x, int y) { return key(x) < key(y); });
+    rp.order = run_order(frames, n);
     std::vector<fm_frame> sorted(n);
     for (int k = 0; k < n; ++k) sorted[k] = frames[rp.order[k]];
     rp.pl = plan_frames(sorted.data(), n, true, true, true, true);
@@ -872,13 +1025,19 @@ static fm_status enqueue_run(fm_ctx* c, const RunPrep& rp, cudaStream_t s) {
     const Maxes& mx = rp.mx;
     FrameDesc* dd = rp.dd;
     const int n = rp.n, ng = (int)pl.grids.size();
-    fm_status st = stage(c, kStGrid, s, [&] { return fm::launch_grid_table(rp.dg, ng, mx.L, dd, n, s); });
+    int* counters = pl.cov.n_split ? reinterpret_cast<int*>(c->arena + pl.cov_cnt_off) : nullptr;
+    fm_status st = stage(c, kStGrid, s, [&] {
+        return fm::launch_grid_table(rp.dg, ng, mx.L, dd, n, counters, pl.cov.n_split, s);
+    });
     if (st != FM_OK) return st;
     if (rp.any_repack) {  // frames whose X TMA cannot read get a padded copy first
         st = stage(c, kStCov, s, [&] { return fm::launch_repack(dd, n, mx.M, mx.T, s); });
         if (st != FM_OK) return st;
     }
-    st = launch_cov(c, rp.cov_tc, dd, c->arena + pl.tmap_off, n, mx.M, s);
+    st = launch_cov(c, rp.cov_tc, dd, c->arena + pl.tmap_off,
+                    reinterpret_cast<const fm::CovItem*>(c->arena + pl.cov_items_off), (int)pl.cov.items.size(),
+                    pl.cov.n_split ? reinterpret_cast<float2*>(c->arena + pl.cov_part_off) : nullptr, counters, n, mx.M,
+                    s);
     if (st != FM_OK) return st;
     st = run_subspace_chain(c, dd, n, mx, s, c->arena + pl.tmap_off + sizeof(CUtensorMap) * 2 * (size_t)n,
                             &rp.tc_pass);
@@ -1275,8 +1434,17 @@ fm_status fm_covariance(fm_ctx* c, const void* X, int n, int M, int T, int64_t l
     fm_status st = set_device(c);
     if (st != FM_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // uniform frames: the tiles in frame order, none split
+    std::vector<fm::CovItem> items;
+    {
+        const int nt = (M + fm::kCovTile - 1) / fm::kCovTile, ns = (T + 15) / 16;
+        for (int b = 0; b < n; ++b)
+            for (int ti = 0; ti < nt; ++ti)
+                for (int tj = ti; tj < nt; ++tj) items.push_back(fm::CovItem{b, ti, tj, 0, ns, -1, 0, 0, 1});
+    }
     const size_t tmap_off = aup(sizeof(FrameDesc) * (size_t)n);
-    const size_t bytes = tmap_off + sizeof(CUtensorMap) * (size_t)n;
+    const size_t items_off = aup(tmap_off + sizeof(CUtensorMap) * (size_t)n);
+    const size_t bytes = items_off + sizeof(fm::CovItem) * items.size();
     st = ensure_arena(c, bytes);
     if (st != FM_OK) return st;
     std::vector<FrameDesc> ds(n);
@@ -1299,10 +1467,12 @@ fm_status fm_covariance(fm_ctx* c, const void* X, int n, int M, int T, int64_t l
     if (st != FM_OK) return st;
     memcpy(host, ds.data(), sizeof(FrameDesc) * n);
     if (tc) memcpy(host + tmap_off, maps.data(), sizeof(CUtensorMap) * n);
+    memcpy(host + items_off, items.data(), sizeof(fm::CovItem) * items.size());
     st = upload(c, host, c->arena, bytes, s);
     if (st != FM_OK) return st;
     FrameDesc* dd = reinterpret_cast<FrameDesc*>(c->arena);
-    return launch_cov(c, tc, dd, c->arena + tmap_off, n, M, s);
+    return launch_cov(c, tc, dd, c->arena + tmap_off, reinterpret_cast<const fm::CovItem*>(c->arena + items_off),
+                      (int)items.size(), nullptr, nullptr, n, M, s);
 }
 
 fm_status fm_subspace(fm_ctx* c, const void* R, int n, int M, const fm_params* p, uint64_t frame_id0, void* U,
@@ -1409,7 +1579,8 @@ static fm_status spectrum_impl(fm_ctx* c, const void* U, int n, const fm_array& 
     st = upload_descs(c, pl, ds, {}, s, &dd, &dg);
     if (st != FM_OK) return st;
     const Maxes mx = maxes_of(ds);
-    st = stage(c, kStGrid, s, [&] { return fm::launch_grid_table(dg, (int)pl.grids.size(), mx.L, nullptr, 0, s); });
+    st = stage(c, kStGrid, s,
+               [&] { return fm::launch_grid_table(dg, (int)pl.grids.size(), mx.L, nullptr, 0, nullptr, 0, s); });
     if (st != FM_OK) return st;
     return stage(c, kStScan, s, [&] { return fm::launch_scan(dd, n, mx.L, mx.M, mx.kpad, mx.scan_smem, s); });
 }

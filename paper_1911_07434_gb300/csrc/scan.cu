@@ -26,12 +26,14 @@ namespace {
 constexpr int kThreads = 256;
 
 // blockIdx.y < n_grids: fill the (q_hi, q_lo) table of grid blockIdx.y;
-// blockIdx.y == n_grids: clear the per-frame status words (first kernel of a run).
+// blockIdx.y == n_grids: clear the per-frame status words and the covariance's
+// split-tile counters (first kernel of a run).
 __global__ void grid_table_kernel(const GridDesc* __restrict__ grids, int n_grids, const FrameDesc* __restrict__ descs,
-                                  int n_frames) {
+                                  int n_frames, int* __restrict__ counters, int n_counters) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if ((int)blockIdx.y == n_grids) {
         if (descs && i < n_frames && descs[i].status) *descs[i].status = 0;
+        if (counters && i < n_counters) counters[i] = 0;
         return;
     }
     const GridDesc g = grids[blockIdx.y];
@@ -305,11 +307,11 @@ cudaError_t launch_scan_t(const FrameDesc* d, int n_frames, int max_L, int max_M
 }  // namespace
 
 cudaError_t launch_grid_table(const GridDesc* g, int n_grids, int max_L, const FrameDesc* d, int n_frames,
-                              cudaStream_t s) {
-    const int gx = (max(max_L, d ? n_frames : 0) + 255) / 256;
+                              int* counters, int n_counters, cudaStream_t s) {
+    const int gx = (max(max(max_L, d ? n_frames : 0), counters ? n_counters : 0) + 255) / 256;
     dim3 grid(gx, n_grids + 1);
     count_launch();
-    grid_table_kernel<<<grid, 256, 0, s>>>(g, n_grids, d, n_frames);
+    grid_table_kernel<<<grid, 256, 0, s>>>(g, n_grids, d, n_frames, counters, n_counters);
     return cudaGetLastError();
 }
 

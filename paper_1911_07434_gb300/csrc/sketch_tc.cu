@@ -10,11 +10,11 @@
 // * sketch_tc_kernel, TF32 operands, one MMA per product: R streams from HBM by
 //   TMA straight into the 128-byte-swizzled K-major layout the MMA reads (the tensor
 //   core takes the TF32 part of each FP32 value), B rows rounded to TF32.  It takes
-//   every product of a TF32 / BF16 frame and the products of an FP32 frame before
-//   its last power step, which only choose the subspace the next step refines.
+//   every product of a TF32 / BF16 frame.
 // * sketch_split_kernel, FP32 accuracy, three TF32 MMAs per product (hi*hi + hi*lo
-//   + lo*hi, as the covariance does): the last product of an FP32 frame, which the
-//   final solve reads.  R arrives raw (128 rows x 16 FP32 per chunk); four converter
+//   + lo*hi, as the covariance does): every product of an FP32 frame (the core
+//   matrix depends on the last basis V, so every product that leads to it is kept at
+//   FP32 accuracy).  R arrives raw (128 rows x 16 FP32 per chunk); four converter
 //   warps split it into [hi 16 | lo 16] TF32 rows of the swizzled A tile, and the B
 //   rows come pre-split in the same [hi 16 | lo 16] chunk layout.
 //
@@ -256,7 +256,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     constexpr int nr = split_nraw(NB);
     constexpr int stage = split_stage(NB);
     const FrameDesc* dp = descs + blockIdx.y;
-    if (!dp->sketch_tc || !sketch_on_tc(dp->method, pass) || !sketch_split(dp->prec, dp->t, pass)) return;
+    // frames whose last product is done (pass > t) keep their C
+    if (!dp->sketch_tc || pass > dp->t || !sketch_on_tc(dp->method, pass) || !sketch_split(dp->prec, dp->t, pass))
+        return;
     const int M = dp->M, l = dp->l, nb = 2 * sketch_tc_lpad(l);
     const int r0 = blockIdx.x * kRows;
     if (r0 >= M) return;
