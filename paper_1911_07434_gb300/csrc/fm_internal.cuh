@@ -248,13 +248,22 @@ cudaError_t launch_sketch_tc(const FrameDesc* d, int n_frames, int max_M, int ma
                              bool any_split, const void* tmA, const void* tmB, const void* tmA_split,
                              const void* tmB_split, cudaStream_t s);
 size_t sketch_tc_smem_bytes(int max_l, bool split);
-// smem_elems: the largest M * (ceil4(kpad) + (positions ? 1 : 0)) over the frames (float2
-// elements of shared memory per CTA: U_s rows and the element positions)
+// smem_elems: the largest M * (scan_row_stride(kpad, KP) + (positions ? 1 : 0)) over the
+// frames, KP = scan_kp_class(the launch's largest kpad) (float2 elements of shared memory
+// per CTA: U_s rows and the element positions)
 cudaError_t launch_scan(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, size_t smem_elems,
                         cudaStream_t s);
 cudaError_t launch_scan_fixup(const FrameDesc* d, int n_frames, int max_L, int max_M, int max_kpad, size_t smem_elems,
                               cudaStream_t s);
-inline size_t scan_smem_elems(int M, int kpad, bool pos) { return (size_t)M * (size_t)(((kpad + 3) & ~3) + (pos ? 1 : 0)); }
+__host__ __device__ inline int scan_kp_class(int max_kpad) {
+    return max_kpad <= 4 ? 4 : (max_kpad <= 8 ? 8 : (max_kpad <= 16 ? 16 : 32));
+}
+// Row stride (elements) of U_s in the CUDA-core scan's shared memory for a frame of kpad
+// columns in a launch of accumulator width KP.
+__host__ __device__ inline int scan_row_stride(int kpad, int KP) { return KP == 32 ? ((kpad + 3) & ~3) : KP; }
+inline size_t scan_smem_elems(int M, int kpad, bool pos, int KP) {
+    return (size_t)M * (size_t)(scan_row_stride(kpad, KP) + (pos ? 1 : 0));
+}
 cudaError_t launch_peaks(const FrameDesc* d, int n_frames, int max_K, cudaStream_t s);
 cudaError_t launch_test_matrix(uint64_t seed, uint64_t frame_id, int M, int l, float2* out, cudaStream_t s);
 cudaError_t launch_sample_indices(uint64_t seed, uint64_t frame_id, int M, int l, int* out, cudaStream_t s);

@@ -326,12 +326,14 @@ int current_sm_count() {
 // Work items of the tensor-core covariance (see cov_tc.cu).  Each 128 x 128 tile of
 // the upper block triangle of every frame is one item, weighted in quarter stages (an
 // off-diagonal tile issues 4 blocks per 16-snapshot stage, a diagonal tile 3), plus a
-// fixed cost per CTA (prologue, first loads, epilogue: about six stages).  Items are
-// ordered longest first, and a greedy longest-first simulation on n_sm SMs (one CTA per
-// SM) finds the tiles that would still run after every other SM has finished; those
-// are split along T into s parts (s in 2..8, the s that shortens the simulated
-// makespan most; each part keeps at least 4 stages).  Small batches gain most: one
-// M = 512 frame's 10 tiles become 80 parts on 152 SMs.
+// fixed cost per CTA (prologue, first loads, epilogue: about six stages).  Items stay
+// grouped by frame (the tiles of a frame run side by side and read its X from L2 once),
+// frames ordered by their work, largest first, off-diagonal tiles before diagonal ones.
+// A greedy simulation of that launch order on n_sm SMs (one CTA per SM) finds the tiles
+// that would still run after every other SM has finished; those are split along T into
+// s parts in place (s in 2..8, the s that shortens the simulated makespan most; each
+// part keeps at least 4 stages).  Small batches gain most: one M = 512 frame's 10 tiles
+// become 80 parts on 152 SMs.
 struct CovPlan {
     std::vector<fm::CovItem> items;
     int n_split = 0, n_slots = 0;
@@ -340,6 +342,8 @@ struct CovPlan {
 constexpr int64_t kCovCtaCost = 24;    // quarter stages per CTA
 constexpr int64_t kCovPartCost = 16;   // extra quarter stages of a split part
 
+// Greedy simulation of a launch: each item, in order, starts on the SM that frees up
+// first; returns the makespan (and each item's end time).
 int64_t lpt_makespan(const std::vector<int64_t>& w, int n_sm, std::vector<int64_t>* ends = nullptr) {
     std::vector<int64_t> heap(n_sm, 0);  // min-heap of SM finish times
     auto cmp = [](int64_t a, int64_t b) { return a > b; };
@@ -365,38 +369,46 @@ std::vector<int> longest_first(const std::vector<int64_t>& w) {
 }
 
 CovPlan plan_cov_items(const fm_frame* f, int n, int n_sm, bool allow_split) {
+    // frames by total tile work, largest first (ties in the caller's order)
+    std::vector<int64_t> fw(n);
+    for (int b = 0; b < n; ++b) {
+        const int64_t nt = (f[b].arr.M + fm::kCovTile - 1) / fm::kCovTile;
+        fw[b] = (int64_t)((f[b].T + 15) / 16) * (4 * nt * (nt - 1) / 2 + 3 * nt);
+    }
+    const std::vector<int> forder = longest_first(fw);
     std::vector<fm::CovItem> tiles;
     std::vector<int64_t> w;
-    for (int b = 0; b < n; ++b) {
+    for (int b : forder) {
         const int nt = (f[b].arr.M + fm::kCovTile - 1) / fm::kCovTile;
         const int ns = (f[b].T + 15) / 16;
         for (int ti = 0; ti < nt; ++ti)
-            for (int tj = ti; tj < nt; ++tj) {
+            for (int tj = ti + 1; tj < nt; ++tj) {
                 tiles.push_back(fm::CovItem{b, ti, tj, 0, ns, -1, 0, 0, 1});
-                w.push_back((int64_t)ns * (ti == tj ? 3 : 4));
+                w.push_back((int64_t)ns * 4);
             }
+        for (int ti = 0; ti < nt; ++ti) {
+            tiles.push_back(fm::CovItem{b, ti, ti, 0, ns, -1, 0, 0, 1});
+            w.push_back((int64_t)ns * 3);
+        }
     }
-    const std::vector<int> order = longest_first(w);
     CovPlan plan;
-    std::vector<int64_t> wo(order.size());
-    for (size_t i = 0; i < order.size(); ++i) wo[i] = w[order[i]] + kCovCtaCost;
+    std::vector<int64_t> wo(tiles.size());
+    int64_t total = 0;
+    for (size_t i = 0; i < tiles.size(); ++i) total += (wo[i] = w[i] + kCovCtaCost);
     int best_s = 1;
     std::vector<int64_t> ends;
-    int64_t total = 0;
-    for (int64_t x : wo) total += x;
     const double late = n_sm > 0 ? 1.02 * (double)total / n_sm : 0.0;  // finishing later: split candidates
-    auto is_candidate = [&](size_t i, int s) { return (double)ends[i] > late && tiles[order[i]].s1 >= 4 * s; };
-    if (allow_split && n_sm > 0 && (int64_t)order.size() <= 8 * (int64_t)n_sm) {
+    auto is_candidate = [&](size_t i, int s) { return (double)ends[i] > late && tiles[i].s1 >= 4 * s; };
+    if (allow_split && n_sm > 0 && (int64_t)tiles.size() <= 8 * (int64_t)n_sm) {
         int64_t best = lpt_makespan(wo, n_sm, &ends);
         for (int s : {2, 3, 4, 6, 8}) {
             std::vector<int64_t> cand;
-            for (size_t i = 0; i < order.size(); ++i) {
+            for (size_t i = 0; i < tiles.size(); ++i) {
                 if (is_candidate(i, s))
-                    for (int k = 0; k < s; ++k) cand.push_back(w[order[i]] / s + kCovCtaCost + kCovPartCost);
+                    for (int k = 0; k < s; ++k) cand.push_back(w[i] / s + kCovCtaCost + kCovPartCost);
                 else
                     cand.push_back(wo[i]);
             }
-            std::stable_sort(cand.begin(), cand.end(), [](int64_t a, int64_t b) { return a > b; });
             const int64_t mk = lpt_makespan(cand, n_sm);
             if ((double)mk < 0.99 * (double)best) {
                 best = mk;
@@ -404,14 +416,12 @@ CovPlan plan_cov_items(const fm_frame* f, int n, int n_sm, bool allow_split) {
             }
         }
     }
-    // the items in launch order: whole tiles and the parts of split tiles, longest first
-    std::vector<fm::CovItem> items;
-    std::vector<int64_t> iw;
-    for (size_t i = 0; i < order.size(); ++i) {
-        const fm::CovItem t = tiles[order[i]];
+    // the items in launch order; the parts of a split tile take its place
+    plan.items.reserve(tiles.size());
+    for (size_t i = 0; i < tiles.size(); ++i) {
+        const fm::CovItem t = tiles[i];
         if (best_s == 1 || !is_candidate(i, best_s)) {
-            items.push_back(t);
-            iw.push_back(w[order[i]]);
+            plan.items.push_back(t);
             continue;
         }
         const int ns = t.s1;
@@ -423,15 +433,11 @@ CovPlan plan_cov_items(const fm_frame* f, int n, int n_sm, bool allow_split) {
             p.first = plan.n_slots;
             p.k = k;
             p.nparts = best_s;
-            items.push_back(p);
-            iw.push_back(w[order[i]] / best_s);
+            plan.items.push_back(p);
         }
         ++plan.n_split;
         plan.n_slots += best_s;
     }
-    const std::vector<int> o2 = longest_first(iw);
-    plan.items.reserve(items.size());
-    for (int i : o2) plan.items.push_back(items[i]);
     return plan;
 }
 
@@ -630,8 +636,10 @@ Maxes maxes_of(const std::vector<FrameDesc>& ds) {
         m.any_projection |= d.method == FM_RAND_PROJECTION;
         m.any_status |= d.status != nullptr;
         m.any_pos |= d.pos != nullptr;
-        m.scan_smem = std::max(m.scan_smem, fm::scan_smem_elems(d.M, d.kpad, d.pos != nullptr));
     }
+    const int KP = fm::scan_kp_class(m.kpad);
+    for (const FrameDesc& d : ds)
+        m.scan_smem = std::max(m.scan_smem, fm::scan_smem_elems(d.M, d.kpad, d.pos != nullptr, KP));
     return m;
 }
 

@@ -80,6 +80,6 @@ extern "C" fm_status fm_spectrum_noalloc(const void* U, int n_frames, int M, int
     const fm::FrameDesc* dd = reinterpret_cast<const fm::FrameDesc*>(scratch);
     const fm::GridDesc* dg = reinterpret_cast<const fm::GridDesc*>(scratch + kGridOff);
     e = fm::launch_grid_table(dg, 1, grid->L, nullptr, 0, nullptr, 0, s);
-    if (e == cudaSuccess) e = fm::launch_scan(dd, n_frames, grid->L, M, ncols, fm::scan_smem_elems(M, ncols, false), s);
+    if (e == cudaSuccess) e = fm::launch_scan(dd, n_frames, grid->L, M, ncols, fm::scan_smem_elems(M, ncols, false, fm::scan_kp_class(ncols)), s);
     return e == cudaSuccess ? FM_OK : FM_ERR_CUDA;
 }

@@ -45,8 +45,10 @@ __global__ void grid_table_kernel(const GridDesc* __restrict__ grids, int n_grid
 }
 
 // c_k += sum over m = 64 b + m0 (m0 = m0_begin, m0_begin + m0_stride, ... < min(64, M))
-// of conj(U_s[m][k]) a_m(theta), with U_s in shared memory (rows of kp4 = the column
-// count rounded up to 4, zero-padded; KP >= kp4 accumulators, those past kp4 stay 0).
+// of conj(U_s[m][k]) a_m(theta), with U_s in shared memory in rows of kp4 elements,
+// zero-padded: kp4 = KP for KP <= 16 (a compile-time stride), and for KP = 32 the
+// column count rounded up to 4, so that M = 1024 frames with up to 24 columns fit;
+// accumulators past kp4 stay 0.
 template <int KP, int NB>
 __device__ __forceinline__ void accumulate_angle(const float2* __restrict__ Usm, int kp4, int M, float2 qq,
                                                  int m0_begin, int m0_stride, float2 (&acc)[KP]) {
@@ -70,7 +72,7 @@ __device__ __forceinline__ void accumulate_angle(const float2* __restrict__ Usm,
                 const float4* urow = reinterpret_cast<const float4*>(Usm + m * kp4);
 #pragma unroll
                 for (int k2 = 0; k2 < KP / 2; ++k2) {
-                    if (2 * k2 >= kp4) break;
+                    if (KP == 32 && 2 * k2 >= kp4) break;
                     const float4 u = urow[k2];
                     cfmac(part[2 * k2], make_float2(u.x, u.y), a);
                     cfmac(part[2 * k2 + 1], make_float2(u.z, u.w), a);
@@ -102,7 +104,7 @@ __device__ __forceinline__ void accumulate_angle_pos(const float2* __restrict__ 
             const float4* urow = reinterpret_cast<const float4*>(Usm + m * kp4);
 #pragma unroll
             for (int k2 = 0; k2 < KP / 2; ++k2) {
-                if (2 * k2 >= kp4) break;
+                if (KP == 32 && 2 * k2 >= kp4) break;
                 const float4 u = urow[k2];
                 cfmac(part[2 * k2], make_float2(u.x, u.y), a);
                 cfmac(part[2 * k2 + 1], make_float2(u.z, u.w), a);
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restr
     float2* Usm = reinterpret_cast<float2*>(smem_raw);  // [M][kp4]
     const FrameDesc* dp = descs + blockIdx.y;
     if ((dp->scan_tc != 0) != FIXUP) return;  // the plain scan skips tensor-core frames, the fixup the others
-    const int M = dp->M, L = dp->L, kp = dp->kpad, kp4 = (kp + 3) & ~3;
+    const int M = dp->M, L = dp->L, kp = dp->kpad, kp4 = scan_row_stride(kp, KP);
     const int i0 = blockIdx.x * kThreads * (FIXUP ? kFixChunks : 1);
     if (i0 >= L) return;
     const float2* __restrict__ Us = dp->Us;
