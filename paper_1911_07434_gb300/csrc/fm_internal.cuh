@@ -41,6 +41,8 @@ struct FrameDesc {
     float* peak_deg;   // K
     int* n_peaks;      // 1
     int* status;       // 1 (nullable)
+    int* fix_list;     // L: angles the tensor-core scan leaves to the main-lobe recompute (scan_tc only)
+    int* fix_count;    // 1: entries of fix_list
     uint64_t seed, frame_id;
     double theta0, step, d_wl;
 };

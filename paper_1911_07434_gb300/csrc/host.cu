@@ -451,6 +451,7 @@ struct Plan {
     };
     std::vector<ScanGroup> scan_groups;
     std::vector<size_t> R, C, V, Us, idx, Y;  // per-frame offsets (R == SIZE_MAX: caller-owned)
+    std::vector<size_t> fix;   // main-lobe list (L ints) and its count of a tensor-core scan (SIZE_MAX: none)
     std::vector<size_t> Xpad;  // repacked copy of X for the tensor-core covariance (SIZE_MAX: none)
     std::vector<size_t> Bsk;   // B rows of the tensor-core sketch (SIZE_MAX: none)
     std::vector<int> grid_of;
@@ -557,6 +558,9 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
         const size_t nc = (size_t)ncols_of(f[b].p);
         pl.Us.push_back(need_Us ? off : SIZE_MAX);
         if (need_Us) off = aup(off + sizeof(float2) * M * nc);
+        const bool fx = need_R && need_Us && need_grid;  // the frame may take the tensor-core scan
+        pl.fix.push_back(fx ? off : SIZE_MAX);
+        if (fx) off = aup(off + sizeof(int) * ((size_t)f[b].grid.L + 1));
     }
     if (need_R && need_Us && need_grid) {
         for (int b = 0; b < n;) {
@@ -965,6 +969,10 @@ static fm_status prepare_run(fm_ctx* c, const fm_frame* frames, int n, cudaStrea
             rp.any_repack = true;
         }
         d.sweep_cap = c->sweep_cap;
+        if (pl.fix[k] != SIZE_MAX) {
+            d.fix_count = reinterpret_cast<int*>(c->arena + pl.fix[k]);
+            d.fix_list = d.fix_count + 1;
+        }
         c->last_us[rp.order[k]] = std::make_tuple(pl.Us[k], d.M, d.ncols);
         d.qtab = reinterpret_cast<float2*>(c->arena + pl.qtab[pl.grid_of[k]]);
         if (pl.geom_of[k]) d.pos = reinterpret_cast<const float2*>(c->arena + pl.pos_tab[pl.geom_of[k] - 1]);

@@ -33,6 +33,7 @@ __global__ void grid_table_kernel(const GridDesc* __restrict__ grids, int n_grid
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if ((int)blockIdx.y == n_grids) {
         if (descs && i < n_frames && descs[i].status) *descs[i].status = 0;
+        if (descs && i < n_frames && descs[i].fix_count) *descs[i].fix_count = 0;
         if (counters && i < n_counters) counters[i] = 0;
         return;
     }
@@ -132,13 +133,16 @@ __device__ __forceinline__ void store_spectrum(const FrameDesc* dp, int i, int M
 // angle away from every source).  The tensor-core accumulator's error grows like
 // u M ||U_s^H a||^2 and is biased, while the sums here stay far below that, so
 // near a peak, where M - ||U_s^H a||^2 cancels, the CUDA-core value is kept.
-// The flagged angles of kFixChunks 256-angle chunks are compacted (one U_s load
-// serves them all); each is shared by fix_groups(KP) warps, warp g taking the m0
-// residue class g (all lanes of a warp read the same U_s row: a shared-memory
-// broadcast), and the partial c_k are summed in shared memory in a fixed order.
-// CTAs with no flagged angle exit before loading U_s.
+// The tensor-core scan's epilogue lists those angles per frame (fix_list); CTA x of
+// the kFixCtas of a frame takes chunks x, x + kFixCtas, ... of kFixChunk entries (one
+// U_s load serves them; a frame with a short list leaves the other CTAs idle).  Each
+// angle is shared by fix_groups(KP) warps, warp g taking the
+// m0 residue class g (all lanes of a warp read the same U_s row: a shared-memory
+// broadcast), and the partial c_k are summed in shared memory in a fixed order, so
+// an angle's value does not depend on where it sits in the list.
 __host__ __device__ constexpr int fix_groups(int kp) { return kp <= 8 ? 8 : (kp == 16 ? 4 : 2); }
-constexpr int kFixChunks = 4;
+constexpr int kFixCtas = 8;
+constexpr int kFixChunk = 64;
 
 // Usm (M x kp4, zero-padded columns) <- U_s (M x kp): float4 copies issued four at a
 // time when the layouts agree, else element by element.
@@ -171,45 +175,16 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restr
     const FrameDesc* dp = descs + blockIdx.y;
     if ((dp->scan_tc != 0) != FIXUP) return;  // the plain scan skips tensor-core frames, the fixup the others
     const int M = dp->M, L = dp->L, kp = dp->kpad, kp4 = scan_row_stride(kp, KP);
-    const int i0 = blockIdx.x * kThreads * (FIXUP ? kFixChunks : 1);
-    if (i0 >= L) return;
+    const int i0 = blockIdx.x * kThreads;
+    if (!FIXUP && i0 >= L) return;
     const float2* __restrict__ Us = dp->Us;
     constexpr int kWarps = kThreads / 32;
-    constexpr int kCh = FIXUP ? kFixChunks : 1;
-    __shared__ int s_list[FIXUP ? kThreads * kFixChunks : 1];
-    __shared__ int s_wcount[kCh * kWarps];
     __shared__ float2 s_red[FIXUP ? kThreads * 8 : 1];  // [warp][k % 8][lane]
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int n_fix = 0;
-    if (FIXUP) {
-        // flags of the CTA's kFixChunks chunks (loads issued together), compacted in
-        // (chunk, warp, lane) order
-        const float thr = (float)(M - 4 * dp->ncols);
-        float pv[kFixChunks];
-#pragma unroll
-        for (int c = 0; c < kFixChunks; ++c) {
-            const int ii = i0 + c * kThreads + threadIdx.x;
-            pv[c] = ii < L ? dp->P[ii] : 0.f;
-        }
-        unsigned bal[kFixChunks];
-#pragma unroll
-        for (int c = 0; c < kFixChunks; ++c) {
-            const int ii = i0 + c * kThreads + threadIdx.x;
-            const bool f = ii < L && !(1.0f / pv[c] >= thr);  // NaN is recomputed too
-            bal[c] = __ballot_sync(0xffffffffu, f);
-            if (lane == 0) s_wcount[c * kWarps + w] = __popc(bal[c]);
-        }
-        __syncthreads();
-        for (int j = 0; j < kCh * kWarps; ++j) n_fix += s_wcount[j];
-        if (n_fix == 0) return;
-#pragma unroll
-        for (int c = 0; c < kFixChunks; ++c) {
-            if (!((bal[c] >> lane) & 1u)) continue;
-            int base = 0;
-            for (int j = 0; j < c * kWarps + w; ++j) base += s_wcount[j];
-            s_list[base + __popc(bal[c] & ((1u << lane) - 1u))] = i0 + c * kThreads + threadIdx.x;
-        }
-        // s_list is ordered by the __syncthreads after the U_s load
+    int n_all = 0;
+    if (FIXUP) {  // chunks x, x + kFixCtas, ... of kFixChunk entries of the frame's list
+        n_all = *dp->fix_count;
+        if ((int)blockIdx.x * kFixChunk >= n_all) return;
     }
     load_us(Us, Usm, M, kp, kp4);
     // element positions of a non-uniform array follow U_s in shared memory
@@ -233,10 +208,11 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restr
     constexpr int kPerRound = kWarps / G * 32;   // angles per round
     const int g = w % G, grp = w / G;
     // uniform trip count: every thread reaches every __syncthreads
-    for (int base = 0; base < n_fix; base += kPerRound) {
-        const int a = base + grp * 32 + lane;
-        const bool act = a < n_fix;
-        const int i = act ? s_list[a] : 0;
+    for (int base = (int)blockIdx.x * kFixChunk; base < n_all; base += kFixChunk * kFixCtas)
+    for (int sub = 0; sub < kFixChunk; sub += kPerRound) {
+        const int a = base + sub + grp * 32 + lane;
+        const bool act = sub + grp * 32 + lane < kFixChunk && a < n_all;
+        const int i = act ? dp->fix_list[a] : 0;
         if (act && has_pos) {
             accumulate_angle_pos<KP, NB>(Usm, kp4, possm, M, dp->qtab[i], g, G, acc);
         } else if (act) {
@@ -274,16 +250,13 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restr
 template <int KP, int NB, bool FIXUP>
 cudaError_t launch_kp(const FrameDesc* d, int n_frames, int max_L, size_t smem_elems, cudaStream_t s) {
     const size_t smem = sizeof(float2) * smem_elems;
-    const size_t static_smem = FIXUP ? sizeof(int) * (kThreads * kFixChunks + kFixChunks * kThreads / 32) +
-                                           sizeof(float2) * kThreads * 8
-                                     : sizeof(int) * (1 + kThreads / 32) + sizeof(float2);
+    const size_t static_smem = FIXUP ? sizeof(float2) * kThreads * 8 : sizeof(float2);
     if (smem + static_smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(scan_kernel<KP, NB, FIXUP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const int per_cta = kThreads * (FIXUP ? kFixChunks : 1);
-    dim3 grid((max_L + per_cta - 1) / per_cta, n_frames);
+    dim3 grid(FIXUP ? kFixCtas : (max_L + kThreads - 1) / kThreads, n_frames);
     count_launch();
     scan_kernel<KP, NB, FIXUP><<<grid, kThreads, smem, s>>>(d);
     return cudaGetLastError();

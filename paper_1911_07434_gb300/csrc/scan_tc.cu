@@ -83,6 +83,20 @@ __global__ void scan_bprep_kernel(const FrameDesc* __restrict__ descs, int n_fra
 
 // Steering entry m of angle row (q_hi, q_lo): a uniform array, or the element
 // positions of the scan group (POS; every frame of a group shares them).
+// Angle ia of frame dp goes to the main-lobe recompute when ||U_s^H a||^2 = M - den
+// exceeds 4 ncols (or den is NaN).  Warp-wide: the flagged lanes take consecutive
+// entries of the frame's list (one atomic per warp); `frame_ok` and dp are uniform.
+__device__ __forceinline__ void list_main_lobe(const FrameDesc* dp, bool frame_ok, int ia, int L, float Mf, float den,
+                                               int lane) {
+    const bool flag = frame_ok && ia < L && !(den >= Mf - 4.0f * (float)dp->ncols);
+    const unsigned bal = __ballot_sync(0xffffffffu, flag);
+    if (!bal) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(dp->fix_count, __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (flag) dp->fix_list[base + __popc(bal & ((1u << lane) - 1u))] = ia;
+}
+
 template <bool POS>
 __device__ __forceinline__ float2 steer_elem(int m, float2 qq, const float2* __restrict__ pos) {
     if constexpr (POS)
@@ -268,13 +282,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                             acc = fmaf(x, x, acc);
                         }
                         const int f = (16 * ch + j) / kRowsPerFrame;
+                        const float den = Mf - acc;
                         if (f < nf && ia < L) {
                             const FrameDesc* dp = descs + f0 + f;
-                            const float den = Mf - acc;
                             const float P = (den > 0.f) ? 1.0f / den : INFINITY;
                             dp->P[ia] = P;
                             if (dp->Pdb) dp->Pdb[ia] = 10.0f * log10f(fminf(P, 3.402823466e38f));
                         }
+                        list_main_lobe(descs + f0 + min(f, nf - 1), f < nf, ia, L, Mf, den, lane);
                     }
                 }
             } else {
@@ -291,13 +306,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                             acc = fmaf(x, x, acc);
                         }
                     }
+                    const float den = Mf - acc;
                     if (ia < L) {
                         const FrameDesc* dp = descs + f0 + f;
-                        const float den = Mf - acc;
                         const float P = (den > 0.f) ? 1.0f / den : INFINITY;
                         dp->P[ia] = P;
                         if (dp->Pdb) dp->Pdb[ia] = 10.0f * log10f(fminf(P, 3.402823466e38f));
                     }
+                    list_main_lobe(descs + f0 + f, true, ia, L, Mf, den, lane);
                 }
             }
         }
