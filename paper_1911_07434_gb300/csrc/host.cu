@@ -74,7 +74,12 @@ struct fm_ctx {
     // serving state
     struct Slot;
     std::vector<Slot*> slots;
-    std::deque<std::pair<uint64_t, fm_frame>> queue;
+    struct Queued {
+        uint64_t ticket;
+        fm_frame frame;
+        size_t need;  // the frame's own workspace without split covariance tiles
+    };
+    std::deque<Queued> queue;
     std::map<uint64_t, int> done;  // ticket -> 1 when complete
     uint64_t next_ticket = 1;
     uint64_t serve_launches = 0;
@@ -340,6 +345,12 @@ struct CovPlan {
 };
 
 constexpr int64_t kCovCtaCost = 24;    // quarter stages per CTA
+// At most two partial tiles per SM (39 MB of partial workspace on 152 SMs), whatever
+// the batch, so that a batch's workspace is bounded by its frames' own plus this.
+inline int64_t cov_max_slots(int n_sm) { return 2 * (int64_t)n_sm; }
+inline size_t cov_split_cap_bytes(int n_sm) {
+    return (size_t)cov_max_slots(n_sm) * (sizeof(float2) * fm::kCovTile * fm::kCovTile + sizeof(int)) + 512;
+}
 constexpr int64_t kCovPartCost = 16;   // extra quarter stages of a split part
 
 // Greedy simulation of a launch: each item, in order, starts on the SM that frees up
@@ -402,6 +413,9 @@ CovPlan plan_cov_items(const fm_frame* f, int n, int n_sm, bool allow_split) {
     if (allow_split && n_sm > 0 && (int64_t)tiles.size() <= 8 * (int64_t)n_sm) {
         int64_t best = lpt_makespan(wo, n_sm, &ends);
         for (int s : {2, 3, 4, 6, 8}) {
+            int64_t slots = 0;
+            for (size_t i = 0; i < tiles.size(); ++i) slots += is_candidate(i, s) ? s : 0;
+            if (slots > cov_max_slots(n_sm)) continue;  // the partial workspace stays bounded
             std::vector<int64_t> cand;
             for (size_t i = 0; i < tiles.size(); ++i) {
                 if (is_candidate(i, s))
@@ -471,7 +485,8 @@ struct Plan {
 typedef std::tuple<double, double, double, int> GridKey;
 
 // Lays out the workspace for n frames.  need_R etc. say which buffers live in the workspace.
-Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool need_Us, bool need_grid) {
+Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool need_Us, bool need_grid,
+                 bool allow_split = true) {
     Plan pl;
     size_t off = 0;
     pl.desc_off = off;
@@ -517,7 +532,7 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
         }
     }
     if (need_R) {
-        pl.cov = plan_cov_items(f, n, current_sm_count(), true);
+        pl.cov = plan_cov_items(f, n, current_sm_count(), allow_split);
         pl.cov_items_off = off;
         off = aup(off + sizeof(fm::CovItem) * pl.cov.items.size());
     }
@@ -912,14 +927,21 @@ static std::vector<int> run_order(const fm_frame* frames, int n) {
     return order;
 }
 
+// Workspace of fm_run for these (valid) frames; without the covariance's split tiles
+// when split is false (then a batch of such frames needs at most the sum of their own
+// figures plus cov_split_cap_bytes).
+static size_t workspace_bytes(const fm_frame* frames, int n, bool split) {
+    const std::vector<int> order = run_order(frames, n);
+    std::vector<fm_frame> sorted(n);
+    for (int k = 0; k < n; ++k) sorted[k] = frames[order[k]];
+    return plan_frames(sorted.data(), n, true, true, true, true, split).total;
+}
+
 size_t fm_workspace_bytes(const fm_frame* frames, int n) {
     if (!frames || n < 1) return 0;
     for (int b = 0; b < n; ++b)
         if (check_frame(frames[b])) return 0;
-    const std::vector<int> order = run_order(frames, n);
-    std::vector<fm_frame> sorted(n);
-    for (int k = 0; k < n; ++k) sorted[k] = frames[order[k]];
-    return plan_frames(sorted.data(), n, true, true, true, true).total;
+    return workspace_bytes(frames, n, true);
 }
 
 // ---- fm_run, split into host preparation and the device chain -----------------
@@ -943,7 +965,9 @@ static fm_status prepare_run(fm_ctx* c, const fm_frame* frames, int n, cudaStrea
     rp.order = run_order(frames, n);
     std::vector<fm_frame> sorted(n);
     for (int k = 0; k < n; ++k) sorted[k] = frames[rp.order[k]];
-    rp.pl = plan_frames(sorted.data(), n, true, true, true, true);
+    // a serving slot shares the GPU with the other slots' batches, so its covariance
+    // does not split tiles to fill the SMs by itself
+    rp.pl = plan_frames(sorted.data(), n, true, true, true, true, c->arena_stream == nullptr);
     const Plan& pl = rp.pl;
     fm_status st = ensure_arena(c, pl.total);
     if (st != FM_OK) return st;
@@ -1816,11 +1840,18 @@ static void serve_progress(fm_ctx* c) {
         const size_t others = serve_held(c) - pick->sub->arena_bytes;
         const size_t room = c->budget > others ? c->budget - others : 0;
         batch.clear();
+        // the sum of the frames' own workspaces plus the split-tile cap bounds a batch's
+        // workspace; the exact plan is computed only once that cheap bound no longer fits
+        const size_t avail = std::max(pick->sub->arena_bytes, room);
+        const size_t cap = cov_split_cap_bytes(current_sm_count());
+        size_t own = 0;  // the batch's frames' own workspaces, without split tiles
         for (const auto& q : c->queue) {
             if ((int)batch.size() == kServeMaxBatch) break;
-            batch.push_back(q.second);
+            batch.push_back(q.frame);
+            own += q.need;
+            if (own + cap <= avail) continue;
             const size_t need = fm_workspace_bytes(batch.data(), (int)batch.size());
-            if (need > pick->sub->arena_bytes && need > room) {  // the slot could not grow that far
+            if (need > avail) {  // the slot could not grow that far
                 batch.pop_back();  // empty when not even the first frame fits
                 break;
             }
@@ -1841,7 +1872,7 @@ static void serve_progress(fm_ctx* c) {
         fm_status st = fm_run(pick->sub, batch.data(), (int)batch.size(), reinterpret_cast<fm_stream>(pick->stream));
         pick->tickets.clear();
         for (size_t i = 0; i < batch.size(); ++i) {
-            pick->tickets.push_back(c->queue.front().first);
+            pick->tickets.push_back(c->queue.front().ticket);
             c->queue.pop_front();
         }
         if (st != FM_OK) {
@@ -1863,12 +1894,12 @@ fm_status fm_serve_submit(fm_ctx* c, const fm_frame* frame, uint64_t* ticket) {
     if (!frame || !ticket) return fail(c, FM_ERR_INVALID_ARG, "fm_serve_submit: NULL argument");
     const char* why = check_frame(*frame);
     if (why) return fail(c, FM_ERR_INVALID_ARG, "fm_serve_submit: %s", why);
-    if (fm_workspace_bytes(frame, 1) > c->budget)
+    if (workspace_bytes(frame, 1, true) > c->budget)
         return fail(c, FM_ERR_OOM_BUDGET, "fm_serve_submit: frame needs more workspace than the budget");
     fm_status st = set_device(c);
     if (st != FM_OK) return st;
     *ticket = c->next_ticket++;
-    c->queue.push_back({*ticket, *frame});
+    c->queue.push_back({*ticket, *frame, workspace_bytes(frame, 1, false)});
     serve_progress(c);
     return FM_OK;
 }
@@ -1882,7 +1913,7 @@ fm_status fm_serve_poll(fm_ctx* c, uint64_t ticket, int* done) {
     if (it == c->done.end()) {
         *done = 0;
         for (auto& q : c->queue)
-            if (q.first == ticket) return FM_OK;
+            if (q.ticket == ticket) return FM_OK;
         for (fm_ctx::Slot* sl : c->slots)
             if (sl->busy)
                 for (uint64_t t : sl->tickets)
