@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--method", default="projection", choices=["projection", "sampling"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16"],
+                    help="operand precision of the covariance / sketch / scan GEMMs (FP32 = 3xTF32)")
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--no-baseline", action="store_true", help="skip full-eig MUSIC and the CPU oracle")
     ap.add_argument("--cpu-sample", type=int, default=3, help="frames of the workload the oracle times")
@@ -57,10 +59,12 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(method: str, batch: int):
+def workload_config(method: str, batch: int, prec: str = "fp32"):
     return {"workload": f"ULA M=512 T=1024 K=8 l=24 t=1 L=15001, {batch} frames per step",
             "method": "random projection (Alg. 2)" if method == "projection" else "random sampling (Alg. 1)",
             "frames_per_step": batch, "M": 512, "T": 1024, "K": 8, "l": 24, "t": 1, "L": 15001,
+            "precision": {"fp32": "FP32 (3xTF32 tensor-core products)", "tf32": "TF32 operands",
+                          "bf16": "BF16 operands"}[prec],
             "l2_flush": "none: inputs (268 MB/step) exceed the 129 MB L2"}
 
 
@@ -181,7 +185,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args.method, args.batch),
+            "data": "synthetic", "config": workload_config(args.method, args.batch, args.prec),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "one frame of the workload per step, single-threaded FP64 C oracle"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -213,7 +217,7 @@ def profile_traffic(name):
     return (rd + wr) if rd is not None and wr is not None else None
 
 
-def roofline(stages, ctx, pk, pk_kind, B, M, T, K, L):
+def roofline(stages, ctx, pk, pk_kind, B, M, T, K, L, prec="fp32"):
     """Roofline entry for the covariance (the dominant contraction of the step).
 
     achieved = algorithmic FP32 flops per launch (4 M^2 T per frame: the Hermitian
@@ -227,6 +231,14 @@ def roofline(stages, ctx, pk, pk_kind, B, M, T, K, L):
     avg_s = cov_ms / max(cov_n, 1) / 1e3
     flops = 4.0 * M * M * T * B
     achieved = flops / avg_s / 1e12
+    if ctx.last_cov_path() == binding.FM_COV_TC and prec != "fp32":
+        bf16 = pk.get("bf16_tflops", 1895.2)
+        peak = bf16 if prec == "bf16" else bf16 * TF32_PER_BF16
+        return {"kernel": f"covariance (cov_tc_kernel, tcgen05, {prec.upper()} operands)", "bound": "tensor",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "algorithmic_bytes": 8.0 * M * T * B + 8.0 * M * M * B, "avg_launch_ms": avg_s * 1e3,
+                "peak_source": f"bf16_tflops {bf16} ({pk_kind})" + ("" if prec == "bf16" else
+                                                                    f" x {TF32_PER_BF16:.4f} (nominal TF32/BF16)")}
     if ctx.last_cov_path() == binding.FM_COV_TC:
         tf32 = pk.get("bf16_tflops", 1895.2) * TF32_PER_BF16
         peak = tf32 / 3.0
@@ -606,8 +618,10 @@ def main():
     npk = torch.empty(B, dtype=torch.int32, device=dev)
     status = torch.zeros(B, dtype=torch.int32, device=dev)
     ctx = binding.Context(device=local)
+    prec_id = {"fp32": binding.FM_PREC_FP32, "tf32": binding.FM_PREC_TF32, "bf16": binding.FM_PREC_BF16}[args.prec]
     frames = [ctx.frame(X[b], K, l, t, method_id, fr0.theta0, fr0.step, L, P[b], idx[b], deg[b], npk[b:b + 1],
-                        seed=0, frame_id=wl.frames[b].frame_id, status=status[b:b + 1]) for b in range(B)]
+                        seed=0, frame_id=wl.frames[b].frame_id, status=status[b:b + 1], prec=prec_id)
+              for b in range(B)]
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -680,7 +694,7 @@ def main():
     npkh = torch.empty(B, dtype=torch.int32).pin_memory()
     sth = torch.zeros(B, dtype=torch.int32).pin_memory()
     frames_h = [ctx.frame(Xh[b], K, l, t, method_id, fr0.theta0, fr0.step, L, Ph[b], idxh[b], degh[b],
-                          npkh[b:b + 1], seed=0, frame_id=wl.frames[b].frame_id, status=sth[b:b + 1])
+                          npkh[b:b + 1], seed=0, frame_id=wl.frames[b].frame_id, status=sth[b:b + 1], prec=prec_id)
                 for b in range(B)]
     e2e_steps = max(10, args.steps)
     for _ in range(2):
@@ -701,7 +715,7 @@ def main():
     # ---- roofline of the dominant kernel ----------------------------------------
     pk, pk_kind = peaks_json()
     names = list(stages.keys())
-    roof = roofline(stages, ctx, pk, pk_kind, B, M, T, K, L)
+    roof = roofline(stages, ctx, pk, pk_kind, B, M, T, K, L, args.prec)
     tot = max(1e-9, sum(v[0] for v in stages.values()))
     stage_summary = {n: {"ms_per_launch": (stages[n][0] / stages[n][1]) if stages[n][1] else 0.0,
                          "launches": stages[n][1], "share": stages[n][0] / tot} for n in names}
@@ -795,8 +809,9 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(args.method, B),
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[args.prec],
+        "data": "synthetic",
+        "config": workload_config(args.method, B, args.prec),
         "latency_ms": {"p50_step": srt[len(srt) // 2], "p99_step": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
                        "single_frame": single},
         "kernel_paths": paths,
