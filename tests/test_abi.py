@@ -65,3 +65,27 @@ def test_workspace_planning_is_host_only(lib):
     for bad in (_frame(K=14), _frame(l=65, M=128), _frame(M=1), _frame(method=0), _frame(L=0), _frame(X=0),
                 _frame(out=0), _frame(t=9), _frame(M=2048)):
         assert binding.fm_workspace_bytes([bad]) == 0
+
+
+def test_array_positions_are_validated_and_sized_on_the_host(lib):
+    """fm_array.pos_wl (Sec. II-A, element positions in wavelengths): invalid positions
+    (non-finite, beyond 4096 wavelengths) are refused before any launch, and a frame with
+    positions plans one position table beside the uniform frame's workspace."""
+    import numpy as np
+    f = _frame()
+    base = binding.fm_workspace_bytes([f])
+    good = np.linspace(0.0, 40.0, 64)
+    f.arr = binding.FmArray(64, 0.5, good.ctypes.data)
+    with_pos = binding.fm_workspace_bytes([f])
+    assert with_pos >= base + 64 * 8
+    for bad in (np.full(64, np.nan), np.full(64, 5000.0), np.concatenate([good[:-1], [np.inf]])):
+        f.arr = binding.FmArray(64, 0.5, bad.ctypes.data)
+        assert binding.fm_workspace_bytes([f]) == 0
+    # two frames with equal positions (different buffers) share one table
+    g1, g2 = _frame(), _frame()
+    p1, p2 = good.copy(), good.copy()
+    g1.arr = binding.FmArray(64, 0.5, p1.ctypes.data)
+    g2.arr = binding.FmArray(64, 0.5, p2.ctypes.data)
+    both = binding.fm_workspace_bytes([g1, g2])
+    p2[3] += 0.25
+    assert binding.fm_workspace_bytes([g1, g2]) >= both + 64 * 8
