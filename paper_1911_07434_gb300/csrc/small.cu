@@ -694,167 +694,181 @@ __device__ int jacobi(float2* A, float2* Z, float* w, int* perm, int n, const Sm
 // tolerance, F <- F J with J the 2 x 2 unitary that diagonalises the pair's Gram
 // matrix [[a, g], [g*, b]] (a = |f_p|^2, b = |f_q|^2, g = f_p^H f_q).  The columns
 // of the converged F are then sigma_k u_k with B u_k = sigma_k^2 u_k.  Pairs follow
-// the same round-robin order as the two-sided solver; within a round the pairs
-// touch disjoint columns, so warp w handles pairs w, w + 8, w + 16 together (lanes
-// over the rows, one block barrier per round).  The column norms are recomputed
-// at the start of every sweep and updated by each rotation (a - t|g|, b + t|g|),
-// so a pair costs one reduced inner product.  Working copy column-major in Wc;
-// eigenvectors (row-major, Z[i n + k]) into Z, eigenvalues into w, and perm
-// orders them descending.  Returns the sweeps used, -1 without convergence within
-// `cap` sweeps.
-__device__ int eig_onesided(const float2* Frm, float2* Wc, float2* Z, float* w, int* perm, int n, const Sm& sm,
-                             int cap) {
+// the same round-robin order as the two-sided solver.  Within a round the pairs
+// touch disjoint columns: pair k is held by lanes [k kP, (k + 1) kP) of the first
+// np kP threads (KE column entries per lane, the inner product reduced over kP
+// lanes), and only those threads take part in the sweeps, meeting at named barrier
+// 1 once per round.  A round is a chain of latencies (loads, reduction, rotation,
+// stores, barrier), so a small group with a short reduction beats spreading a pair
+// over more lanes.  The column norms are recomputed at the start of every sweep and
+// updated by each rotation (a - t|g|, b + t|g|), so a pair costs one reduced inner
+// product.  Working copy column-major in Wc; eigenvectors (row-major, Z[i n + k])
+// into Z, eigenvalues into w, and perm orders them descending.  Returns the sweeps
+// used, -1 without convergence within `cap` sweeps.
+constexpr int kP = 8;  // lanes per pair: 3 warps at n = 24, 6 at n = 48
+static_assert((kLMax / 2) * kP <= kThreads, "the sweep group must fit in the block");
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+template <int KE>
+__device__ int eig_onesided_t(const float2* Frm, float2* Wc, float2* Z, float* w, int* perm, int n, const Sm& sm,
+                              int cap) {
     const int ne = n + (n & 1), np = ne / 2, nr = ne - 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // one pair per half-warp and slot: 16 lanes hold the pair's two columns (up to kE
-    // entries each) and reduce over 16 lanes; every half-warp evaluates the same
-    // rotation formulas for its own pair
-    constexpr int kHW = kThreads / 16;
-    constexpr int kPH = (kLMax / 2 + kHW - 1) / kHW;  // pair slots per half-warp (2 at l = 48)
-    constexpr int kE = (kLMax + 15) / 16;             // column entries per lane (3 at l = 48)
-    const int hw = threadIdx.x >> 4, hl = threadIdx.x & 15;
-    const int nslot = (np + kHW - 1) / kHW, nent = (n + 15) / 16;  // block-uniform
+    const int nsync = (np * kP + 31) & ~31;  // whole warps; <= kThreads by the assert above
+    const int k = threadIdx.x / kP, gl = threadIdx.x % kP;
+    const int nent = (n + kP - 1) / kP;  // entries per lane and column (<= KE)
     for (int e = threadIdx.x; e < n * n; e += kThreads) {
         const int i = e / n, p = e % n;
         Wc[p * n + i] = Frm[e];
     }
     for (int e = threadIdx.x; e < kMaxSweeps; e += kThreads) sm.flags[e] = 0;
-    __syncthreads();
-    const float tol2 = kOneSidedTol * kOneSidedTol;
     // largest |g|^2 / (a b) met in the sweep, as int bits (non-negative floats order as ints)
     int* sweep_max = sm.flags + kMaxSweeps + 6;
-    int sweeps = -1;
-    for (int sweep = 0; sweep < cap && nr > 0; ++sweep) {
-        if (threadIdx.x == 0) *sweep_max = 0;
-        for (int k = warp; k < n; k += kWarps) {  // exact column norms for this sweep
-            float a = 0.f;
-            for (int i = lane; i < n; i += 32) a = fmaf(Wc[k * n + i].x, Wc[k * n + i].x, fmaf(Wc[k * n + i].y, Wc[k * n + i].y, a));
+    int* s_sweeps = sm.flags + kMaxSweeps + 7;
+    if (threadIdx.x == 0) *s_sweeps = -1;
+    __syncthreads();
+    if (nr > 0 && threadIdx.x < nsync) {
+        const bool live_k = k < np;
+        const float tol2 = kOneSidedTol * kOneSidedTol;
+        int sweeps = -1;
+        for (int sweep = 0; sweep < cap; ++sweep) {
+            if (threadIdx.x == 0) *sweep_max = 0;
+            // round-robin positions, advanced by one each round; the round-0 pairs
+            // (k, ne - 1 - k) cover every column once, so each group takes the exact
+            // norms of its two columns
+            int ia = (k == 0) ? 0 : (k - 1) % nr;
+            int ib = (ne - 2 - k + nr) % nr;
+            {
+                const int c0 = (k == 0) ? 0 : 1 + ia, c1 = 1 + ib;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            if (lane == 0) w[k] = a;
-        }
-        // round-robin positions, advanced by one each round
-        int ia[kPH], ib[kPH];
+                for (int s = 0; s < 2; ++s) {
+                    const int c = s ? c1 : c0;
+                    const bool own = live_k && c < n;
+                    float a = 0.f;
 #pragma unroll
-        for (int j = 0; j < kPH; ++j) {
-            const int k = hw + kHW * j;
-            ia[j] = (k == 0 || nr == 0) ? 0 : (k - 1) % nr;
-            ib[j] = nr ? (ne - 2 - k + nr) % nr : 0;
-        }
-        float ratio = 0.f;  // this thread's largest pair ratio in the sweep
-        bool any = false;
-        __syncthreads();
-        for (int r = 0; r < nr; ++r) {
-            float2* fp[kPH];
-            float2* fq[kPH];
-            float2 xp[kPH][kE], xq[kPH][kE];
-            float g[kPH][2], na[kPH], nb[kPH];
-            int pi[kPH], qi[kPH];
-            bool live[kPH];
+                    for (int h = 0; h < KE; ++h) {
+                        const int i = gl + kP * h;
+                        if (own && h < nent && i < n) {
+                            const float2 v = Wc[c * n + i];
+                            a = fmaf(v.x, v.x, fmaf(v.y, v.y, a));
+                        }
+                    }
 #pragma unroll
-            for (int j = 0; j < kPH; ++j) {
-                if (j >= nslot) break;
-                const int k = hw + kHW * j;
-                const int pa = (k == 0) ? 0 : 1 + ia[j];
-                const int pb = 1 + ib[j];
-                const int p = min(pa, pb), q = max(pa, pb);
-                live[j] = k < np && q < n;  // q == n: the dummy column of an odd n
-                pi[j] = live[j] ? p : 0;
-                qi[j] = live[j] ? q : 0;
-                fp[j] = Wc + pi[j] * n;
-                fq[j] = Wc + qi[j] * n;
-                na[j] = live[j] ? w[p] : 1.f;
-                nb[j] = live[j] ? w[q] : 1.f;
-                float gr = 0.f, gi = 0.f;
-#pragma unroll
-                for (int h = 0; h < kE; ++h) {
-                    if (h >= nent) break;
-                    const int i = hl + 16 * h;
-                    xp[j][h] = (live[j] && i < n) ? fp[j][i] : make_float2(0.f, 0.f);
-                    xq[j][h] = (live[j] && i < n) ? fq[j][i] : make_float2(0.f, 0.f);
-                    gr = fmaf(xp[j][h].x, xq[j][h].x, fmaf(xp[j][h].y, xq[j][h].y, gr));  // conj(f_p) f_q
-                    gi = fmaf(xp[j][h].x, xq[j][h].y, fmaf(-xp[j][h].y, xq[j][h].x, gi));
+                    for (int o = kP / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o, kP);
+                    if (own && gl == 0) w[c] = a;
                 }
-                g[j][0] = gr;
-                g[j][1] = gi;
-                if (++ia[j] == nr) ia[j] = 0;
-                if (++ib[j] == nr) ib[j] = 0;
             }
+            float ratio = 0.f;  // this thread's largest pair ratio in the sweep
+            bool any = false;
+            named_sync(1, nsync);
+            for (int r = 0; r < nr; ++r) {
+                const int pa = (k == 0) ? 0 : 1 + ia;
+                const int pb = 1 + ib;
+                const int p = min(pa, pb), q = max(pa, pb);
+                const bool live = live_k && q < n;  // q == n: the dummy column of an odd n
+                float2* fp = Wc + (live ? p : 0) * n;
+                float2* fq = Wc + (live ? q : 0) * n;
+                const float na = live ? w[p] : 1.f, nb = live ? w[q] : 1.f;
+                float2 xp[KE], xq[KE];
 #pragma unroll
-            for (int o = 8; o > 0; o >>= 1)
-#pragma unroll
-                for (int j = 0; j < kPH; ++j) {
-                    if (j >= nslot) break;
-                    g[j][0] += __shfl_xor_sync(0xffffffffu, g[j][0], o, 16);
-                    g[j][1] += __shfl_xor_sync(0xffffffffu, g[j][1], o, 16);
+                for (int h = 0; h < KE; ++h) {
+                    const int i = gl + kP * h;
+                    const bool in = live && h < nent && i < n;
+                    xp[h] = in ? fp[i] : make_float2(0.f, 0.f);
+                    xq[h] = in ? fq[i] : make_float2(0.f, 0.f);
                 }
-            // rotation of every pair (identity where the pair is already orthogonal to the
-            // tolerance), then the column updates
+                float gr = 0.f, gi = 0.f;  // conj(f_p) f_q
 #pragma unroll
-            for (int j = 0; j < kPH; ++j) {
-                if (j >= nslot) break;
-                const float gr = g[j][0], gi = g[j][1];
+                for (int h = 0; h < KE; ++h) {
+                    gr = fmaf(xp[h].x, xq[h].x, fmaf(xp[h].y, xq[h].y, gr));
+                    gi = fmaf(xp[h].x, xq[h].y, fmaf(-xp[h].y, xq[h].x, gi));
+                }
+#pragma unroll
+                for (int o = kP / 2; o > 0; o >>= 1) {
+                    gr += __shfl_xor_sync(0xffffffffu, gr, o, kP);
+                    gi += __shfl_xor_sync(0xffffffffu, gi, o, kP);
+                }
+                if (++ia == nr) ia = 0;
+                if (++ib == nr) ib = 0;
+                // rotation of the pair, skipped where it is already orthogonal to the tolerance
                 const float mag2 = fmaf(gr, gr, gi * gi);
-                const float ab = na[j] * nb[j];
-                const bool rot = live[j] && mag2 > FLT_MIN && mag2 > tol2 * ab;  // uniform over the half-warp
-                if (live[j] && ab > 0.f) ratio = fmaxf(ratio, __fdividef(mag2, ab));
-                const float inv = rsqrtf(fmaxf(mag2, FLT_MIN));
-                const float mag = mag2 * inv;
-                const float tau = 0.5f * (nb[j] - na[j]) * inv;
-                // smaller root of t^2 + 2 tau t - 1 = 0 (t -> 0 as |tau| -> inf)
-                const float q1 = fmaf(tau, tau, 1.f);
-                const float t = rot ? copysignf(__fdividef(1.f, fabsf(tau) + q1 * rsqrtf(q1)), tau) : 0.f;
-                const float c = rsqrtf(fmaf(t, t, 1.f));
-                const float sn = t * c;
-                // F <- F U, U = [[c, s], [-s conj(ph), c conj(ph)]], ph = g / |g| (1 if no rotation)
-                const float2 phc = rot ? make_float2(gr * inv, -gi * inv) : make_float2(1.f, 0.f);
-                const float2 u10 = cscale(phc, -sn), u11 = cscale(phc, c);
+                const float ab = na * nb;
+                const bool rot = live && mag2 > FLT_MIN && mag2 > tol2 * ab;  // uniform over the group
+                if (live && ab > 0.f) ratio = fmaxf(ratio, __fdividef(mag2, ab));
                 any |= rot;
-                if (!live[j]) continue;  // a dead pair's pointers alias column 0 of a live one
+                if (rot) {
+                    const float inv = rsqrtf(mag2);
+                    const float mag = mag2 * inv;
+                    const float tau = 0.5f * (nb - na) * inv;
+                    // smaller root of t^2 + 2 tau t - 1 = 0 (t -> 0 as |tau| -> inf)
+                    const float q1 = fmaf(tau, tau, 1.f);
+                    const float t = copysignf(__fdividef(1.f, fabsf(tau) + q1 * rsqrtf(q1)), tau);
+                    const float c = rsqrtf(fmaf(t, t, 1.f));
+                    const float sn = t * c;
+                    // F <- F U, U = [[c, s], [-s conj(ph), c conj(ph)]], ph = g / |g|
+                    const float2 phc = make_float2(gr * inv, -gi * inv);
+                    const float2 u10 = cscale(phc, -sn), u11 = cscale(phc, c);
 #pragma unroll
-                for (int h = 0; h < kE; ++h) {
-                    if (h >= nent) break;
-                    const int i = hl + 16 * h;
-                    if (i < n) {
-                        fp[j][i] = cadd(cscale(xp[j][h], c), cmul(xq[j][h], u10));
-                        fq[j][i] = cadd(cscale(xp[j][h], sn), cmul(xq[j][h], u11));
+                    for (int h = 0; h < KE; ++h) {
+                        const int i = gl + kP * h;
+                        if (h < nent && i < n) {
+                            fp[i] = cadd(cscale(xp[h], c), cmul(xq[h], u10));
+                            fq[i] = cadd(cscale(xp[h], sn), cmul(xq[h], u11));
+                        }
+                    }
+                    if (gl == 0) {
+                        w[p] = na - t * mag;
+                        w[q] = nb + t * mag;
                     }
                 }
-                if (hl == 0) {
-                    w[pi[j]] = na[j] - t * mag;
-                    w[qi[j]] = nb[j] + t * mag;
-                }
+                named_sync(1, nsync);
             }
-            __syncthreads();
+            // sweep summary over the group's warps
+            const bool wany = __any_sync(0xffffffffu, any);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ratio = fmaxf(ratio, __shfl_xor_sync(0xffffffffu, ratio, o));
+            if (lane == 0) {
+                if (wany) sm.flags[sweep] = 1;
+                atomicMax(sweep_max, __float_as_int(ratio));
+            }
+            named_sync(1, nsync);
+            // converged: no rotation in this sweep, or every pair of it was within 1e-4 before its
+            // rotation, so after it (quadratic convergence) within 1e-8 < the tolerance
+            if (!sm.flags[sweep] || __int_as_float(*sweep_max) < 1e-8f) {
+                sweeps = sweep + (sm.flags[sweep] ? 1 : 0);
+                break;
+            }
+            named_sync(1, nsync);  // every thread has read *sweep_max before the next sweep resets it
         }
-        if (hl == 0) {
-            if (any) sm.flags[sweep] = 1;
-            atomicMax(sweep_max, __float_as_int(ratio));
-        }
-        __syncthreads();
-        // converged: no rotation in this sweep, or every pair of it was within 1e-4 before its
-        // rotation, so after it (quadratic convergence) within 1e-8 < the tolerance
-        if (!sm.flags[sweep] || __int_as_float(*sweep_max) < 1e-8f) {
-            sweeps = sweep + (sm.flags[sweep] ? 1 : 0);
-            break;
-        }
-        __syncthreads();  // every thread has read *sweep_max before the next sweep resets it
+        if (threadIdx.x == 0) *s_sweeps = sweeps;
     }
-    if (nr == 0) sweeps = 0;
+    if (nr == 0 && threadIdx.x == 0) *s_sweeps = 0;
+    __syncthreads();
+    const int sweeps = *s_sweeps;
     // eigenvalues |f_k|^2, eigenvectors f_k / |f_k| (row-major into Z)
-    for (int k = warp; k < n; k += kWarps) {
+    for (int c = warp; c < n; c += kWarps) {
         float a = 0.f;
-        for (int i = lane; i < n; i += 32) a = fmaf(Wc[k * n + i].x, Wc[k * n + i].x, fmaf(Wc[k * n + i].y, Wc[k * n + i].y, a));
+        for (int i = lane; i < n; i += 32) a = fmaf(Wc[c * n + i].x, Wc[c * n + i].x, fmaf(Wc[c * n + i].y, Wc[c * n + i].y, a));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
         const float inv = (a > 0.f) ? rsqrtf(a) : 0.f;
-        for (int i = lane; i < n; i += 32) Z[i * n + k] = cscale(Wc[k * n + i], inv);
+        for (int i = lane; i < n; i += 32) Z[i * n + c] = cscale(Wc[c * n + i], inv);
         __syncwarp();
-        if (lane == 0) w[k] = a;
+        if (lane == 0) w[c] = a;
     }
     __syncthreads();
     sort_desc(w, perm, n);
     return sweeps;
+}
+
+__device__ int eig_onesided(const float2* Frm, float2* Wc, float2* Z, float* w, int* perm, int n, const Sm& sm,
+                             int cap) {
+    constexpr int kEMax = (kLMax + kP - 1) / kP;
+    return n <= 3 * kP ? eig_onesided_t<3>(Frm, Wc, Z, w, perm, n, sm, cap)
+                       : eig_onesided_t<kEMax>(Frm, Wc, Z, w, perm, n, sm, cap);
 }
 
 // One Rayleigh-Ritz correction of the leading ncols-dimensional eigenspace of B
