@@ -127,10 +127,11 @@ __global__ void __launch_bounds__(kThreads) sketch_dense_kernel(const FrameDesc*
     }
 }
 
-// Omega -> V for projection frames (pass 0), one thread per entry.
+// Omega -> V for projection frames (pass 0), one thread per entry.  Frames whose first
+// product runs on the tensor cores get Omega from the B-row preparation instead.
 __global__ void omega_kernel(const FrameDesc* __restrict__ descs) {
     const FrameDesc* dp = descs + blockIdx.y;
-    if (dp->method != FM_RAND_PROJECTION) return;
+    if (dp->method != FM_RAND_PROJECTION || dp->sketch_tc) return;
     const int M = dp->M, l = dp->l;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= M * l) return;

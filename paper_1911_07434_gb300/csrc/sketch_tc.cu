@@ -6,7 +6,8 @@
 //   [Vr_0, -Vi_0, Vr_1, -Vi_1, ...] -> Re C[., j],   [Vi_0, Vr_0, Vi_1, Vr_1, ...] -> Im C[., j],
 // so one real GEMM D = R_rows B^T (K = 2M, N = 2 l_pad) gives C.
 //
-// Two kernels (sketch_bprep_kernel writes the B rows of both):
+// Two kernels (sketch_bprep_kernel writes the B rows of both, and generates Omega for the
+// projection variant's first product):
 // * sketch_tc_kernel, TF32 operands, one MMA per product: R streams from HBM by
 //   TMA straight into the 128-byte-swizzled K-major layout the MMA reads (the tensor
 //   core takes the TF32 part of each FP32 value), B rows rounded to TF32.  It takes
@@ -57,44 +58,80 @@ __host__ __device__ constexpr int split_smem(int nb_max) {
 static_assert(split_nraw(2 * kLMax) >= 3 && split_smem(2 * kLMax) <= kSmemPerCta, "split ring too large");
 static_assert(plain_nstages(2 * kLMax) * plain_stage(2 * kLMax) + kSmemExtra <= kSmemPerCta, "ring too large");
 
-// B rows of pass `pass`, element (j, m) per thread.  Plain layout (2 l_pad rows x 2M):
-// TF32-rounded [Vr, -Vi] and [Vi, Vr] rows.  Split layout (2 l_pad rows x 32 ceil(2M/16)):
-// chunk c of 16 values stored as [hi 16 | lo 16], hi = rn_tf32(v), lo = rn_tf32(v - hi);
-// m runs over M rounded up to 8 so the last chunk's padding is written as zeros.
-__global__ void sketch_bprep_kernel(const FrameDesc* __restrict__ descs, int pass) {
+// B rows of pass `pass` from 64 rows of V per block.  Plain layout (2 l_pad rows x
+// 2M): TF32-rounded [Vr, -Vi] and [Vi, Vr] rows.  Split layout (2 l_pad rows x 32
+// ceil(2M/16)): chunk c of 16 values stored as [hi 16 | lo 16], hi = rn_tf32(v),
+// lo = rn_tf32(v - hi), the last chunk's padding (m >= M) written as zeros.  The V
+// tile (64 x l complex, contiguous in V) is staged in shared memory with coalesced
+// loads; for the projection variant's first product it is generated instead (the
+// Gaussian test matrix Omega of Alg. 2, also written to V, which holds Pi for the
+// core matrix when t = 0).  Consecutive threads then write consecutive 16-byte
+// pieces (split) or complex pairs (plain) of a B row segment.
+constexpr int kBpRows = 64;
+constexpr int kBpLd = kLMax + 1;  // odd row stride (in float2) against bank conflicts
+__global__ void __launch_bounds__(256) sketch_bprep_kernel(const FrameDesc* __restrict__ descs, int pass) {
+    __shared__ float2 vt[kBpRows * kBpLd];
     const FrameDesc* dp = descs + blockIdx.y;
     if (!dp->sketch_tc || pass > dp->t || !sketch_on_tc(dp->method, pass)) return;
     const int M = dp->M, l = dp->l, lp = sketch_tc_lpad(l);
-    const bool split = sketch_split(dp->prec, dp->t, pass);
-    const int Mq = split ? (M + 7) / 8 * 8 : M;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;  // (j, m)
-    if (e >= lp * Mq) return;
-    const int j = e / Mq, m = e % Mq;
-    float2 v = make_float2(0.f, 0.f);
-    if (j < l && m < M) v = dp->V[(int64_t)m * l + j];
-    const float val[4] = {v.x, -v.y, v.y, v.x};  // re row (2m, 2m+1), im row (2m, 2m+1)
-    if (!split) {
+    const int m0 = blockIdx.x * kBpRows;
+    if (m0 >= M) return;
+    const int rows = min(kBpRows, M - m0);
+    const bool gen = pass == 0 && dp->method == FM_RAND_PROJECTION;
+    for (int e = threadIdx.x; e < kBpRows * l; e += blockDim.x) {
+        const int r = e / l, j = e - r * l;
+        float2 v = make_float2(0.f, 0.f);
+        if (r < rows) {
+            const int64_t at = (int64_t)m0 * l + e;
+            if (gen) {
+                v = gaussian_entry(dp->seed, dp->frame_id, m0 + r, j);
+                dp->V[at] = v;
+            } else {
+                v = dp->V[at];
+            }
+        }
+        vt[r * kBpLd + j] = v;
+    }
+    __syncthreads();
+    const int nrow = 2 * lp;
+    if (!sketch_split(dp->prec, dp->t, pass)) {
+        // one complex entry m per thread: (re row) [Vr, -Vi], (im row) [Vi, Vr] at 2m
         const int64_t rowlen = 2 * (int64_t)M;
-        float* re = dp->Bsk + (2 * (int64_t)j) * rowlen;
-        float* im = re + rowlen;
-        re[2 * m] = __uint_as_float(tf32_rn(val[0]));
-        re[2 * m + 1] = __uint_as_float(tf32_rn(val[1]));
-        im[2 * m] = __uint_as_float(tf32_rn(val[2]));
-        im[2 * m + 1] = __uint_as_float(tf32_rn(val[3]));
+        for (int t = threadIdx.x; t < nrow * kBpRows; t += blockDim.x) {
+            const int R = t / kBpRows, r = t - R * kBpRows;
+            if (r >= rows) continue;
+            const int j = R >> 1;
+            const float2 v = j < l ? vt[r * kBpLd + j] : make_float2(0.f, 0.f);
+            const float a = (R & 1) ? v.y : v.x, b = (R & 1) ? v.x : -v.y;
+            *reinterpret_cast<float2*>(dp->Bsk + R * rowlen + 2 * (int64_t)(m0 + r)) =
+                make_float2(__uint_as_float(tf32_rn(a)), __uint_as_float(tf32_rn(b)));
+        }
         return;
     }
+    // split: a row segment is 8 chunks x 8 pieces of 16 bytes; piece p < 4 holds the hi
+    // values 4p .. 4p+3 of its chunk (entries m = 8c + 2p, 8c + 2p + 1), p >= 4 their lo
     const int64_t rowlen = sketch_split_rowlen(M);
-    const int f = 2 * m, c = f >> 4, w = f & 15;  // chunk c, position w (even) of the value pair
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        float* row = dp->Bsk + (2 * (int64_t)j + h) * rowlen + 32 * (int64_t)c;
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const float x = val[2 * h + u];
-            const uint32_t hi = tf32_rn(x);
-            row[w + u] = __uint_as_float(hi);
-            row[16 + w + u] = __uint_as_float(tf32_rn(x - __uint_as_float(hi)));
+    const int nchunks = (2 * M + 15) / 16, c0 = m0 / 8;
+    for (int t = threadIdx.x; t < nrow * 64; t += blockDim.x) {
+        const int R = t >> 6, cc = (t >> 3) & 7, p = t & 7;
+        const int c = c0 + cc;
+        if (c >= nchunks) continue;
+        const int j = R >> 1, ra = 8 * cc + 2 * (p & 3);
+        float2 va = make_float2(0.f, 0.f), vb = va;
+        if (j < l) {
+            va = vt[ra * kBpLd + j];
+            vb = vt[(ra + 1) * kBpLd + j];
         }
+        const float x[4] = {(R & 1) ? va.y : va.x, (R & 1) ? va.x : -va.y, (R & 1) ? vb.y : vb.x,
+                            (R & 1) ? vb.x : -vb.y};
+        uint4 o;
+        uint32_t* ov = reinterpret_cast<uint32_t*>(&o);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t hi = tf32_rn(x[u]);
+            ov[u] = p < 4 ? hi : tf32_rn(x[u] - __uint_as_float(hi));
+        }
+        *reinterpret_cast<uint4*>(dp->Bsk + R * rowlen + 32 * (int64_t)c + 4 * p) = o;
     }
 }
 
@@ -454,9 +491,8 @@ cudaError_t launch_sketch_tc(const FrameDesc* d, int n_frames, int max_M, int ma
                              bool any_split, const void* tmA, const void* tmB, const void* tmA_split,
                              const void* tmB_split, cudaStream_t s) {
     const int lp = sketch_tc_lpad(max_l), nb_max = 2 * lp;
-    const int Mq = any_split ? (max_M + 7) / 8 * 8 : max_M;
     count_launch();
-    sketch_bprep_kernel<<<dim3((unsigned)((lp * Mq + 255) / 256), n_frames), 256, 0, s>>>(d, pass);
+    sketch_bprep_kernel<<<dim3((unsigned)((max_M + kBpRows - 1) / kBpRows), n_frames), 256, 0, s>>>(d, pass);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)((max_M + kRows - 1) / kRows), n_frames);

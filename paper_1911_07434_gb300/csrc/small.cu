@@ -475,6 +475,155 @@ __device__ void trinv_d(const float4* R, float4* X, int l, const Sm& sm) {
     }
 }
 
+// Cholesky factor and its inverse in one elimination sweep.  Reducing G to R by
+// row operations (row k scaled by 1/r_kk, then row i > k minus conj(r_ki) times
+// row k) and applying the same operations to the identity beside it leaves that
+// identity as E with E G = R, i.e. E = R^{-H} (lower triangular); X = R^{-1} = E^H.
+// One block barrier per column: every thread derives the pivot's square root and
+// its inverse itself (same inputs, same results), rows i > k are updated from row
+// k scaled on the fly, and the finished row k is written where nothing reads it in
+// the same phase (R's row parked below G's diagonal, E's row conjugated into
+// column k of X), so the next column only waits for the updates.  Aw (l x l) is
+// scratch for E.  Task slots of the trailing triangle: rows a and n - 1 - a share
+// n + 1 slots, so the triangle packs densely into the block.
+__device__ __forceinline__ bool trailing_slot(int t, int n, int& a, int& b) {
+    const int p = t / (n + 1), c = t - p * (n + 1);
+    if (c < n - p) {
+        a = p;
+        b = p + c;
+        return true;
+    }
+    a = n - 1 - p;
+    b = a + (c - (n - p));
+    return a != p;  // odd n: the middle row is listed once
+}
+
+// Double-float: pivots below 2^-40 x the largest diagonal entry (a numerically
+// rank-deficient sketch) are raised to that floor; only a non-finite pivot fails.
+// G (in place) becomes R (upper, zero below), X = R^{-1}.
+__device__ bool chol_inv_d(float4* G, float4* X, float4* Aw, int l, const Sm& sm) {
+    if (threadIdx.x == 0) {
+        sm.flags[kMaxSweeps + 4] = 0;
+        float dmax = 0.f;
+        for (int k = 0; k < l; ++k) dmax = fmaxf(dmax, G[k * l + k].x);
+        sm.scal[2] = 0x1p-40f * dmax;
+    }
+    for (int e = threadIdx.x; e < l * l; e += kThreads) {
+        Aw[e] = make_float4((e / l == e % l) ? 1.f : 0.f, 0.f, 0.f, 0.f);
+        X[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    const float dfloor = sm.scal[2];
+    df rprev{0.f, 0.f};
+    for (int k = 0; k < l; ++k) {
+        // the previous pivot's R entry: every thread has read G[k-1][k-1] by now
+        if (k > 0 && threadIdx.x == 0) G[(k - 1) * l + k - 1] = make_float4(rprev.hi, rprev.lo, 0.f, 0.f);
+        df d = zload(G[k * l + k]).re;
+        const bool bad = !isfinite(d.hi);
+        if (bad) {
+            d = df{1e-30f, 0.f};
+        } else if (!(d.hi > dfloor)) {
+            d = df{dfloor > 0.f ? dfloor : 1e-30f, 0.f};
+        }
+        const df r = dd_sqrt(d);
+        const df inv = dd_div(df{1.f, 0.f}, r);
+        if (bad && threadIdx.x == 0) sm.flags[kMaxSweeps + 4] = 1;
+        rprev = r;
+        const int n = l - k - 1;
+        const int nt = ((n + 1) / 2) * (n + 1);  // trailing upper-triangle slots
+        const int na = n * (k + 1);              // E entries of the rows below
+        const int ntot = nt + na + n + k + 1;    // + R row k (right of the pivot) + E row k
+        for (int t = threadIdx.x; t < ntot; t += kThreads) {
+            if (t < nt) {
+                int a, b;
+                if (!trailing_slot(t, n, a, b)) continue;
+                const int i = k + 1 + a, j = k + 1 + b;
+                const zd ri = zscale(zload(G[k * l + i]), inv), rj = zscale(zload(G[k * l + j]), inv);
+                G[i * l + j] = zpack(zadd(zload(G[i * l + j]), zneg(zmulc(ri, rj))));
+            } else if (t < nt + na) {
+                const int u = t - nt, a = u / (k + 1), m = u - a * (k + 1);
+                const int i = k + 1 + a;
+                const zd ri = zscale(zload(G[k * l + i]), inv), em = zscale(zload(Aw[k * l + m]), inv);
+                Aw[i * l + m] = zpack(zadd(zload(Aw[i * l + m]), zneg(zmulc(ri, em))));
+            } else if (t < nt + na + n) {
+                const int j = k + 1 + (t - nt - na);
+                G[j * l + k] = zpack(zscale(zload(G[k * l + j]), inv));  // R[k][j], parked
+            } else {
+                const int m = t - nt - na - n;
+                const zd em = zscale(zload(Aw[k * l + m]), inv);
+                X[m * l + k] = zpack(zd{em.re, dd_neg(em.im)});
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) G[(l - 1) * l + l - 1] = make_float4(rprev.hi, rprev.lo, 0.f, 0.f);
+    // R's rows back above the diagonal, zeros below
+    for (int e = threadIdx.x; e < l * l; e += kThreads) {
+        const int i = e / l, j = e % l;
+        if (i < j) {
+            G[e] = G[j * l + i];
+            G[j * l + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    __syncthreads();
+    return sm.flags[kMaxSweeps + 4] == 0;
+}
+
+// FP32, any non-positive pivot fails (the core matrix H: W then falls back to the
+// eigenvalue pseudo-inverse).  G (in place) becomes R (upper, zero below), X = R^{-1}.
+__device__ bool chol_inv_f(float2* G, float2* X, float2* Aw, int l, const Sm& sm) {
+    if (threadIdx.x == 0) sm.flags[kMaxSweeps + 4] = 0;
+    for (int e = threadIdx.x; e < l * l; e += kThreads) {
+        Aw[e] = make_float2((e / l == e % l) ? 1.f : 0.f, 0.f);
+        X[e] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float rprev = 0.f;
+    for (int k = 0; k < l; ++k) {
+        if (k > 0 && threadIdx.x == 0) G[(k - 1) * l + k - 1] = make_float2(rprev, 0.f);
+        float d = G[k * l + k].x;
+        const bool bad = !isfinite(d) || !(d > 0.f);
+        if (bad) d = 1e-30f;
+        const float r = sqrtf(d);
+        const float inv = 1.f / r;
+        if (bad && threadIdx.x == 0) sm.flags[kMaxSweeps + 4] = 1;
+        rprev = r;
+        const int n = l - k - 1;
+        const int nt = ((n + 1) / 2) * (n + 1);
+        const int na = n * (k + 1);
+        const int ntot = nt + na + n + k + 1;
+        for (int t = threadIdx.x; t < ntot; t += kThreads) {
+            if (t < nt) {
+                int a, b;
+                if (!trailing_slot(t, n, a, b)) continue;
+                const int i = k + 1 + a, j = k + 1 + b;
+                G[i * l + j] = csub(G[i * l + j], cmulc(cscale(G[k * l + i], inv), cscale(G[k * l + j], inv)));
+            } else if (t < nt + na) {
+                const int u = t - nt, a = u / (k + 1), m = u - a * (k + 1);
+                const int i = k + 1 + a;
+                Aw[i * l + m] = csub(Aw[i * l + m], cmulc(cscale(G[k * l + i], inv), cscale(Aw[k * l + m], inv)));
+            } else if (t < nt + na + n) {
+                const int j = k + 1 + (t - nt - na);
+                G[j * l + k] = cscale(G[k * l + j], inv);
+            } else {
+                const int m = t - nt - na - n;
+                X[m * l + k] = cconj(cscale(Aw[k * l + m], inv));
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) G[(l - 1) * l + l - 1] = make_float2(rprev, 0.f);
+    for (int e = threadIdx.x; e < l * l; e += kThreads) {
+        const int i = e / l, j = e % l;
+        if (i < j) {
+            G[e] = G[j * l + i];
+            G[j * l + i] = make_float2(0.f, 0.f);
+        }
+    }
+    __syncthreads();
+    return sm.flags[kMaxSweeps + 4] == 0;
+}
+
 // In place, row-local: rows of A (rows x l) <- A * X for X upper triangular given
 // in double-float (hi, lo) pairs.  Output (r, c) sums k = 0 .. c, so a task pairs
 // column c with column l - 1 - c of the same row (l + 1 terms per task whatever c)
@@ -527,8 +676,7 @@ __device__ void apply_upper_d(float2* A, int rows, int l, const float4* X) {
 __device__ bool cholqr_pass_d(cg::cluster_group& cl, float2* A, int rows, int l, const Sm& sm, float2* Rk) {
     gram_part_d(A, rows, l, sm.part);
     reduce_d(cl, sm.part, sm.Gd, l);
-    const bool ok = chol_d(sm.Gd, l, sm);
-    trinv_d(sm.Gd, sm.Xd, l, sm);
+    const bool ok = chol_inv_d(sm.Gd, sm.Xd, sm.part, l, sm);  // part is free after the reduction
     for (int e = threadIdx.x; e < l * l; e += kThreads) {
         const float4 g = sm.Gd[e];
         Rk[e] = make_float2(g.x + g.y, g.z + g.w);
@@ -1057,8 +1205,7 @@ __global__ void __launch_bounds__(kThreads, 3) small_cluster_kernel(const FrameD
     // from here on.
     gram_part_d(sm.Cs, rows, l, sm.part);
     reduce_d(cl, sm.part, sm.Gd, l);
-    bool ok = chol_d(sm.Gd, l, sm);
-    trinv_d(sm.Gd, sm.Xd, l, sm);
+    bool ok = chol_inv_d(sm.Gd, sm.Xd, sm.part, l, sm);  // part is free after the reduction
     for (int e = threadIdx.x; e < l * l; e += kThreads) {
         const float4 g = sm.Gd[e];
         sm.Rc[e] = make_float2(g.x + g.y, g.z + g.w);
@@ -1068,9 +1215,8 @@ __global__ void __launch_bounds__(kThreads, 3) small_cluster_kernel(const FrameD
     // B = R_c H^+ R_c^H
     for (int e = threadIdx.x; e < l * l; e += kThreads) sm.Gf[e] = sm.H[e];
     __syncthreads();
-    const bool pd = chol_f(sm.Gf, l, sm);
+    const bool pd = chol_inv_f(sm.Gf, sm.Xf, reinterpret_cast<float2*>(sm.part), l, sm);
     if (pd) {
-        trinv_f(sm.Gf, sm.Xf, l);
         // F = R_c R_h^{-1} (upper) into T, B = F F^H into H
         for (int e = threadIdx.x; e < l * l; e += kThreads) {
             const int i = e / l, j = e % l;
