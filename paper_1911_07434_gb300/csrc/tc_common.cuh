@@ -72,11 +72,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
         : "memory");
 }
 
-__device__ __forceinline__ uint32_t tf32_rn(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
+// FP32 -> TF32 (10 explicit mantissa bits) rounded to nearest, ties away from zero,
+// on the bit pattern: adding half a TF32 ulp (bit 12) to the magnitude carries into
+// bit 13 exactly when the 13 dropped bits are at least half an ulp, and a carry out of
+// the mantissa raises the exponent as the rounding requires.  For every finite input
+// this is the value cvt.rna.tf32.f32 returns (checked over all 2^32 patterns on the
+// GPU); it takes two integer operations, which issue faster than the conversion.
+// NaN payloads are not preserved.
+__device__ __forceinline__ uint32_t tf32_rn(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
 
 // K-major, 128-byte-swizzled shared-memory matrix descriptor (tcgen05):
 // start address >> 4 in [0,14), leading-dim offset (unused for this layout) = 1,
