@@ -211,6 +211,9 @@ __host__ __device__ inline bool sketch_split(int prec, int t, int pass) {
 __host__ __device__ inline int sketch_tc_lpad(int l) { return (l + 7) / 8 * 8; }
 // Floats per B row of the split layout: ceil(2M / 16) chunks of [hi 16 | lo 16].
 __host__ __device__ inline int64_t sketch_split_rowlen(int M) { return 32 * (int64_t)((2 * M + 15) / 16); }
+// Antennas of the tensor-core scan's B rows (a multiple of the 16 antennas of an FP32-mode
+// stage; the TF32 and BF16 stages take 8).
+__host__ __device__ inline int scan_tc_mp(int M) { return (M + 15) / 16 * 16; }
 
 // One device -> host output copy of fm_run_host (dst: a host address the device can write).
 struct CopyEntry {

@@ -592,7 +592,7 @@ Plan plan_frames(const fm_frame* f, int n, bool need_R, bool need_sketch, bool n
             sg.nc = nc0;
             sg.L = pl.grids[g0].L;
             sg.prec = pr0;
-            const int ncp = fm::scan_tc_ncp(nc0), Mp = (M0 + 7) / 8 * 8;
+            const int ncp = fm::scan_tc_ncp(nc0), Mp = fm::scan_tc_mp(M0);
             sg.rows = (size_t)sg.nf * 2 * ncp;  // one B operand row pair per (frame, column of U_s)
             sg.rowlen = 4 * (size_t)Mp;
             sg.bprep_off = off;

@@ -9,12 +9,16 @@
 //   [ur_m, ui_m]_m -> Re(u^H a),  [-ui_m, ur_m]_m -> Im(u^H a),
 // and P_f(i) = 1 / (M - sum_k (Re^2 + Im^2)).  A is generated in registers by
 // the CTA itself (the exact phase reduction of scan.cu, one sincospi per
-// element) and written to shared memory as TF32 hi/lo pairs; B (U_s of up to
+// element) and written to shared memory as hi/lo pairs; B (U_s of up to
 // 512 / (2 ncp) frames, already split into hi/lo by scan_bprep_kernel) arrives by
-// TMA.  Each FP32 product is formed as hi*hi + hi*lo + lo*hi (3xTF32); the
-// batch's precision mode may instead take hi*hi alone (FM_PREC_TF32) or BF16
-// operands (FM_PREC_BF16, one kind::f16 MMA per 8 antennas).  Two 128 x 256 FP32
-// accumulators fill the 512 TMEM columns.
+// TMA.  Each FP32 product is formed as hi*hi + hi*lo + lo*hi.  In the FP32 mode the
+// pairs are FP16 (kind::f16, twice the TF32 rate): both operands are bounded a priori
+// (|a_m| = 1, U_s has unit columns), so scaled by 2^8 they stay below 2^8, hi + lo
+// carries 22 significant bits whenever lo is a normal FP16 value and otherwise misses
+// x by at most 2^-25 (2^-33 unscaled), and the products match 3xTF32 accuracy; a stage
+// is 16 antennas.  The batch's precision mode may instead take TF32 hi*hi alone
+// (FM_PREC_TF32) or BF16 operands (FM_PREC_BF16, one MMA per 8 antennas); those
+// stages are 8 antennas.  Two 128 x 256 FP32 accumulators fill the 512 TMEM columns.
 //
 // Warp roles (320 threads): warp 0 TMA producer, warp 1 TMEM allocation + MMA
 // issue, warps 2-9 steering generation (two threads per angle row, half of each
@@ -38,6 +42,12 @@ constexpr int kSmemBytes = kTiles + 1024 + 256;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kIdesc = idesc_tf32(128, 256);
 constexpr uint32_t kIdescBf16 = idesc_bf16(128, 256);
+constexpr uint32_t kIdescF16 = idesc_f16(128, 256);
+constexpr float kScaleF16 = 256.f;          // both FP16 operands of the FP32 mode
+constexpr float kUnscaleF16 = 1.f / 65536.f;  // exact: 2^-16 on the accumulator
+
+// antennas per stage: 16 in the FP32 mode (two K = 16 FP16 steps), 8 otherwise
+__host__ __device__ inline int scan_stage_ant(int prec) { return prec == FM_PREC_FP32 ? 16 : 8; }
 
 __device__ __forceinline__ void split2(float a, float b, uint32_t* hi, uint32_t* lo) {
     hi[0] = tf32_rn(a);
@@ -46,8 +56,11 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t* hi, uint32_t*
     lo[1] = tf32_rn(b - __uint_as_float(hi[1]));
 }
 
-// B rows for the frames of one launch: row f*2ncp + 2k (Re) and + 1 (Im); along a
-// row, stage s (8 antennas) holds 32 floats [hi of 16 interleaved values | lo].
+// B rows for the frames of one launch: row f*2ncp + 2k (Re) and + 1 (Im).  TF32 and
+// BF16 modes: along a row, stage s (8 antennas) holds 32 floats [hi of 16 interleaved
+// values | lo] (BF16: 16 values in the first 32 bytes).  FP32 mode: stage s (16
+// antennas, 128 bytes) holds FP16 [hi | lo] of the values of antennas 16s .. 16s+7,
+// then [hi | lo] of antennas 16s+8 .. 16s+15, scaled by 2^8 (the first half of the row).
 __global__ void scan_bprep_kernel(const FrameDesc* __restrict__ descs, int n_frames, int M, int Mp, int ncp, int prec,
                                   float* __restrict__ Bp) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (f, k, m)
@@ -62,6 +75,19 @@ __global__ void scan_bprep_kernel(const FrameDesc* __restrict__ descs, int n_fra
     const int64_t rowlen = 4 * (int64_t)Mp;
     float* re_row = Bp + ((int64_t)f * 2 * ncp + 2 * k) * rowlen;
     float* im_row = re_row + rowlen;
+    if (prec == FM_PREC_FP32) {
+        uint32_t* re_w = reinterpret_cast<uint32_t*>(re_row);
+        uint32_t* im_w = reinterpret_cast<uint32_t*>(im_row);
+        const int at = (m >> 4) * 32 + ((m >> 3) & 1) * 16 + (m & 7);  // 4-byte words
+        uint32_t hi, lo;
+        split_f16x2(kScaleF16 * u.x, kScaleF16 * u.y, hi, lo);  // Re row: [ur, ui]
+        re_w[at] = hi;
+        re_w[at + 8] = lo;
+        split_f16x2(-kScaleF16 * u.y, kScaleF16 * u.x, hi, lo);  // Im row: [-ui, ur]
+        im_w[at] = hi;
+        im_w[at + 8] = lo;
+        return;
+    }
     const int s = m >> 3, p = (2 * m) & 15;
     if (prec == FM_PREC_BF16) {  // 16 BF16 values in the first 32 bytes of the stage's 128
         reinterpret_cast<uint32_t*>(re_row)[s * 32 + p / 2] = bf16x2_rn(u.x, u.y);
@@ -128,7 +154,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int nrows = nf * kRowsPerFrame;
     const bool two = nrows > 256;
     const int i0 = blockIdx.x * kRowsA;
-    const int nstages = Mp / 8;
+    const int nstages = Mp / scan_stage_ant(prec);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -181,6 +207,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t acc0 = s > 0 ? 1u : 0u;
                     mma_bf16(tmem, desc_sw128(a), desc_sw128(b), kIdescBf16, acc0);
                     if (two) mma_bf16(tmem + 256, desc_sw128(a), desc_sw128(b + 256 * 128), kIdescBf16, acc0);
+                } else if (prec == FM_PREC_FP32) {  // two K = 16 FP16 steps: [hi | lo] at 64 kk
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint32_t acc0 = (s > 0 || kk > 0) ? 1u : 0u;
+                        const uint64_t a_hi = desc_sw128(a + 64 * kk), a_lo = desc_sw128(a + 64 * kk + 32);
+                        const uint64_t b0_hi = desc_sw128(b + 64 * kk), b0_lo = desc_sw128(b + 64 * kk + 32);
+                        mma_bf16(tmem, a_hi, b0_hi, kIdescF16, acc0);
+                        mma_bf16(tmem, a_hi, b0_lo, kIdescF16, 1u);
+                        mma_bf16(tmem, a_lo, b0_hi, kIdescF16, 1u);
+                        if (two) {
+                            const uint32_t b1 = b + 256 * 128;
+                            const uint64_t b1_hi = desc_sw128(b1 + 64 * kk), b1_lo = desc_sw128(b1 + 64 * kk + 32);
+                            mma_bf16(tmem + 256, a_hi, b1_hi, kIdescF16, acc0);
+                            mma_bf16(tmem + 256, a_hi, b1_lo, kIdescF16, 1u);
+                            mma_bf16(tmem + 256, a_lo, b1_hi, kIdescF16, 1u);
+                        }
+                    }
                 } else {
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {
@@ -233,6 +276,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_arrive(&a_full[slot]);
                 continue;
             }
+            if (prec == FM_PREC_FP32) {  // antennas 16s + 8g .. +7: FP16 hi in 16-byte chunks 4g, 4g+1, lo in 4g+2, 4g+3
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    uint4 hi, lo;
+                    uint32_t* hv = reinterpret_cast<uint32_t*>(&hi);
+                    uint32_t* lv = reinterpret_cast<uint32_t*>(&lo);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int m = 16 * s + 8 * g + 4 * cc + u;
+                        const float2 a = (i < L && m < M) ? steer_elem<POS>(m, qq, pos) : make_float2(0.f, 0.f);
+                        split_f16x2(kScaleF16 * a.x, kScaleF16 * a.y, hv[u], lv[u]);
+                    }
+                    *reinterpret_cast<uint4*>(arow + swz(r, 4 * g + cc)) = hi;
+                    *reinterpret_cast<uint4*>(arow + swz(r, 4 * g + 2 + cc)) = lo;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&a_full[slot]);
+                continue;
+            }
 #pragma unroll
             for (int cc = 0; cc < 2; ++cc) {  // chunk c: antennas 8s + 2c, 8s + 2c + 1
                 const int c = 2 * g + cc;
@@ -252,7 +314,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 lo.z = w[0];
                 lo.w = w[1];
                 *reinterpret_cast<uint4*>(arow + swz(r, c)) = hi;
-                if (prec == FM_PREC_FP32) *reinterpret_cast<uint4*>(arow + swz(r, 4 + c)) = lo;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(&a_full[slot]);
@@ -267,6 +328,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int ia = i0 + row;
             const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
             const float Mf = (float)M;
+            const float us = prec == FM_PREC_FP32 ? kUnscaleF16 : 1.f;  // exact power of two
             if constexpr (kRowsPerFrame <= 16) {
                 const int nchunks = (nrows + 15) / 16;
                 for (int ch = half; ch < nchunks; ch += 2) {
@@ -278,7 +340,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         float acc = 0.f;
 #pragma unroll
                         for (int jj = 0; jj < kRowsPerFrame; ++jj) {
-                            const float x = __uint_as_float(v[j + jj]);
+                            const float x = __uint_as_float(v[j + jj]) * us;
                             acc = fmaf(x, x, acc);
                         }
                         const int f = (16 * ch + j) / kRowsPerFrame;
@@ -302,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tmem_wait_ld();
 #pragma unroll
                         for (int jj = 0; jj < 16; ++jj) {
-                            const float x = __uint_as_float(v[jj]);
+                            const float x = __uint_as_float(v[jj]) * us;
                             acc = fmaf(x, x, acc);
                         }
                     }
@@ -361,7 +423,7 @@ int scan_tc_ncp(int ncols) {
 cudaError_t launch_scan_tc(const FrameDesc* d, int n_frames, int M, int ncols, int L, int prec, bool pos, float* bprep,
                            const void* tmB, cudaStream_t s) {
     const int ncp = scan_tc_ncp(ncols);
-    const int Mp = (M + 7) / 8 * 8;
+    const int Mp = scan_tc_mp(M);
     const int64_t total = (int64_t)n_frames * ncp * Mp;
     count_launch();
     scan_bprep_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(d, n_frames, M, Mp, ncp, prec, bprep);

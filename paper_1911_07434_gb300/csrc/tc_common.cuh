@@ -111,7 +111,14 @@ __host__ __device__ constexpr uint32_t idesc_bf16(uint32_t m, uint32_t n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
 }
 
-// One K = 16 step with BF16 operands (both BF16) and FP32 accumulation.
+// Instruction descriptor for kind::f16 with FP16 A and B (bits 7-9 = bits 10-12 = 0)
+// and an FP32 accumulator; otherwise as idesc_tf32.
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t m, uint32_t n) {
+    return (1u << 4) | ((n >> 3) << 17) | ((m >> 4) << 24);
+}
+
+// One K = 16 step of kind::f16 (both operands BF16 or both FP16, as the instruction
+// descriptor says) with FP32 accumulation.
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -119,6 +126,26 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b,
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
+}
+
+// Two FP32 values rounded to nearest-even FP16 and packed, `first` in the low half.
+__device__ __forceinline__ uint32_t f16x2_rn(float first, float second) {
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(second), "f"(first));
+    return r;
+}
+// The two FP16 halves of a packed pair back in FP32 (exact).
+__device__ __forceinline__ float2 f16x2_to_f32(uint32_t h) {
+    float lo, hi;
+    asm("{\n\t.reg .f16 a, b;\n\tmov.b32 {a, b}, %2;\n\tcvt.f32.f16 %0, a;\n\tcvt.f32.f16 %1, b;\n\t}" : "=f"(lo), "=f"(hi) : "r"(h));
+    return make_float2(lo, hi);
+}
+// x (|x| <= 2^15) as an FP16 pair hi + lo: hi = rn(x), lo = rn(x - hi), for two values
+// at once, packed as for f16x2_rn.
+__device__ __forceinline__ void split_f16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    hi = f16x2_rn(a, b);
+    const float2 h = f16x2_to_f32(hi);
+    lo = f16x2_rn(a - h.x, b - h.y);
 }
 
 // Two FP32 values rounded to nearest-even BF16 and packed, `first` in the low half
