@@ -344,14 +344,20 @@ struct CovPlan {
     int n_split = 0, n_slots = 0;
 };
 
-constexpr int64_t kCovCtaCost = 24;    // quarter stages per CTA
+// Costs in quarter stages (one quarter of an off-diagonal tile's 16-snapshot stage,
+// about 420 SM cycles), measured per CTA on GB300: the prologue, the epilogue (TMEM ->
+// shared -> R and its mirror at about 30 bytes per cycle) and the launch gap of a CTA;
+// the partial tile a split part writes; the reduction that the last part of a tile
+// split in s adds (it reads the s partials, then writes the tile).
+constexpr int64_t kCovCtaCost = 64;
 // At most two partial tiles per SM (39 MB of partial workspace on 152 SMs), whatever
 // the batch, so that a batch's workspace is bounded by its frames' own plus this.
 inline int64_t cov_max_slots(int n_sm) { return 2 * (int64_t)n_sm; }
 inline size_t cov_split_cap_bytes(int n_sm) {
     return (size_t)cov_max_slots(n_sm) * (sizeof(float2) * fm::kCovTile * fm::kCovTile + sizeof(int)) + 512;
 }
-constexpr int64_t kCovPartCost = 16;   // extra quarter stages of a split part
+constexpr int64_t kCovPartCost = 24;
+inline int64_t cov_reduce_cost(int s) { return 36 + 12 * (int64_t)s; }
 
 // Greedy simulation of a launch: each item, in order, starts on the SM that frees up
 // first; returns the makespan (and each item's end time).
@@ -419,7 +425,8 @@ CovPlan plan_cov_items(const fm_frame* f, int n, int n_sm, bool allow_split) {
             std::vector<int64_t> cand;
             for (size_t i = 0; i < tiles.size(); ++i) {
                 if (is_candidate(i, s))
-                    for (int k = 0; k < s; ++k) cand.push_back(w[i] / s + kCovCtaCost + kCovPartCost);
+                    for (int k = 0; k < s; ++k)
+                        cand.push_back(w[i] / s + kCovCtaCost + kCovPartCost + (k == s - 1 ? cov_reduce_cost(s) : 0));
                 else
                     cand.push_back(wo[i]);
             }
