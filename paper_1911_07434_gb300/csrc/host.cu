@@ -53,10 +53,14 @@ struct fm_ctx {
     size_t budget = 0;
     char* arena = nullptr;
     size_t arena_bytes = 0;
-    char* pinned = nullptr;
-    size_t pinned_bytes = 0;
-    cudaEvent_t staging_done = nullptr;
-    bool staging_pending = false;
+    // descriptor staging: a ring of pinned buffers, each reusable once the upload that
+    // read it has run, so the host may prepare calls a few steps ahead of the GPU
+    static constexpr int kStaging = 4;
+    char* pinned[kStaging] = {};
+    size_t pinned_bytes[kStaging] = {};
+    cudaEvent_t staging_done[kStaging] = {};
+    bool staging_pending[kStaging] = {};
+    int staging_slot = 0;
     std::string err;
     unsigned timing = 0;  // bit s: stage s is bracketed by events
     std::vector<TimedEvent> pending;
@@ -214,32 +218,38 @@ fm_status ensure_arena(fm_ctx* c, size_t need) {
 }
 
 // Pinned staging for descriptor uploads; waits for the previous upload first.
+// The current slot of the staging ring, at least `need` bytes, once the upload that last
+// read it has run.
 fm_status staging(fm_ctx* c, size_t need, char** out) {
-    if (c->staging_pending) {
-        cudaEventSynchronize(c->staging_done);
-        c->staging_pending = false;
+    const int k = c->staging_slot;
+    if (c->staging_pending[k]) {
+        cudaEventSynchronize(c->staging_done[k]);
+        c->staging_pending[k] = false;
     }
-    if (need > c->pinned_bytes) {
-        if (c->pinned) cudaFreeHost(c->pinned);
+    if (need > c->pinned_bytes[k]) {
+        if (c->pinned[k]) cudaFreeHost(c->pinned[k]);
         size_t sz = std::max(need, (size_t)1 << 16);
-        cudaError_t e = cudaMallocHost(&c->pinned, sz);
+        cudaError_t e = cudaMallocHost(&c->pinned[k], sz);
         if (e != cudaSuccess) {
-            c->pinned = nullptr;
-            c->pinned_bytes = 0;
+            c->pinned[k] = nullptr;
+            c->pinned_bytes[k] = 0;
             return cuda_fail(c, e, "cudaMallocHost(staging)");
         }
-        c->pinned_bytes = sz;
+        c->pinned_bytes[k] = sz;
     }
-    *out = c->pinned;
+    *out = c->pinned[k];
     return FM_OK;
 }
 
+// Copies the current staging slot (host) to dev on s and moves to the next slot.
 fm_status upload(fm_ctx* c, const char* host, char* dev, size_t bytes, cudaStream_t s) {
+    const int k = c->staging_slot;
     cudaError_t e = cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync(descriptors)");
-    if (!c->staging_done) cudaEventCreateWithFlags(&c->staging_done, cudaEventDisableTiming);
-    cudaEventRecord(c->staging_done, s);
-    c->staging_pending = true;
+    if (!c->staging_done[k]) cudaEventCreateWithFlags(&c->staging_done[k], cudaEventDisableTiming);
+    cudaEventRecord(c->staging_done[k], s);
+    c->staging_pending[k] = true;
+    c->staging_slot = (k + 1) % fm_ctx::kStaging;
     return FM_OK;
 }
 
@@ -895,10 +905,11 @@ fm_status fm_destroy(fm_ctx* c) {
             cudaStreamSynchronize(hs);
             cudaStreamDestroy(hs);
         }
-    if (c->staging_done) {
-        cudaEventSynchronize(c->staging_done);
-        cudaEventDestroy(c->staging_done);
-    }
+    for (cudaEvent_t e : c->staging_done)
+        if (e) {
+            cudaEventSynchronize(e);
+            cudaEventDestroy(e);
+        }
     for (TimedEvent& t : c->pending) {
         cudaEventSynchronize(t.b);
         cudaEventDestroy(t.a);
@@ -912,7 +923,8 @@ fm_status fm_destroy(fm_ctx* c) {
         else
             cudaFree(c->arena);
     }
-    if (c->pinned) cudaFreeHost(c->pinned);
+    for (char* h : c->pinned)
+        if (h) cudaFreeHost(h);
     delete c;
     return FM_OK;
 }

@@ -15,9 +15,11 @@
 // * sketch_split_kernel, FP32 accuracy, three TF32 MMAs per product (hi*hi + hi*lo
 //   + lo*hi, as the covariance does): every product of an FP32 frame (the core
 //   matrix depends on the last basis V, so every product that leads to it is kept at
-//   FP32 accuracy).  R arrives raw (128 rows x 16 FP32 per chunk); four converter
-//   warps split it into [hi 16 | lo 16] TF32 rows of the swizzled A tile, and the B
-//   rows come pre-split in the same [hi 16 | lo 16] chunk layout.
+//   FP32 accuracy).  R arrives raw by TMA in the swizzled layout the MMA reads (128
+//   rows x 32 FP32 per stage) and serves as the hi operand as it is: the tensor core
+//   truncates each FP32 operand to TF32 (checked on GB300).  Four converter warps
+//   write only the lo tile, x - trunc_tf32(x) rounded to TF32, at the same swizzled
+//   positions; the B rows come pre-split in [hi 16 | lo 16] chunks (hi = rn_tf32).
 //
 // One CTA per 128 rows of R of one frame: warp 0 issues TMA loads (ring of stages),
 // warp 1 allocates TMEM and issues the MMAs (one thread), warps 2-5 convert (split
@@ -33,7 +35,6 @@ using namespace tc;
 
 constexpr int kRows = 128;
 constexpr int kTileA = kRows * 128;    // 16 KB: 128 rows x 128 B (32 FP32, or [hi 16 | lo 16] TF32)
-constexpr int kRawA = kRows * 64;      // 8 KB: 128 raw rows x 16 FP32 (split kernel)
 constexpr int kThreads = 192;
 constexpr int kSmemPerCta = 113 * 1024;  // two CTAs per SM (228 KB, 1 KB reserved per CTA)
 constexpr int kSmemExtra = 1024 + 256;   // 1024-B alignment slack + barriers
@@ -44,18 +45,22 @@ __host__ __device__ constexpr int plain_stage(int nb_max) { return kTileA + nb_m
 __host__ __device__ constexpr int plain_nstages(int nb_max) {
     return 4 * plain_stage(nb_max) + kSmemExtra <= kSmemPerCta ? 4 : 3;
 }
-// Split kernel: a ring of raw stages [B rows nb_max x 128 B | raw A 8 KB] as deep as two
-// CTAs per SM allow (at most 6), and two converted A tiles.
-__host__ __device__ constexpr int split_stage(int nb_max) { return nb_max * 128 + kRawA; }
+// Split kernel: a ring of stages [B chunk 0 | B chunk 1 (nb_max x 128 B each) | raw A 16 KB]
+// (32 FP32 of K per stage) as deep as two CTAs per SM allow (at most 6), and two lo tiles
+// where three stages still fit beside them (else one: the ring depth matters more).
+__host__ __device__ constexpr int split_stage(int nb_max) { return 2 * nb_max * 128 + kTileA; }
+__host__ __device__ constexpr int split_nlo(int nb_max) {
+    return 3 * split_stage(nb_max) + 2 * kTileA + kSmemExtra <= kSmemPerCta ? 2 : 1;
+}
 __host__ __device__ constexpr int split_nraw(int nb_max) {
     int n = 6;
-    while (n > 2 && n * split_stage(nb_max) + 2 * kTileA + kSmemExtra > kSmemPerCta) --n;
+    while (n > 2 && n * split_stage(nb_max) + split_nlo(nb_max) * kTileA + kSmemExtra > kSmemPerCta) --n;
     return n;
 }
 __host__ __device__ constexpr int split_smem(int nb_max) {
-    return split_nraw(nb_max) * split_stage(nb_max) + 2 * kTileA + kSmemExtra;
+    return split_nraw(nb_max) * split_stage(nb_max) + split_nlo(nb_max) * kTileA + kSmemExtra;
 }
-static_assert(split_nraw(2 * kLMax) >= 3 && split_smem(2 * kLMax) <= kSmemPerCta, "split ring too large");
+static_assert(split_nraw(2 * kLMax) >= 2 && split_smem(2 * kLMax) <= kSmemPerCta, "split ring too large");
 static_assert(plain_nstages(2 * kLMax) * plain_stage(2 * kLMax) + kSmemExtra <= kSmemPerCta, "ring too large");
 
 // B rows of pass `pass` from 64 rows of V per block.  Plain layout (2 l_pad rows x
@@ -273,14 +278,12 @@ __global__ void __launch_bounds__(kThreads, 2)
     tmem_teardown(dp, rg, tmem);
 }
 
-// Split kernel, two-level sum: the MMAs of each group of kGroup chunks accumulate in
+// Split kernel, two-level sum: the MMAs of each group of kGroup stages accumulate in
 // one of two TMEM buffers (columns 0 and 128), and warps 2-5 add every finished group
 // into FP32 registers, as the CUDA-core sketch sums per chunk and then across chunks.
-// A single accumulator over all 6 M / 16 MMAs of a row would carry the tensor core's
+// A single accumulator over all the MMAs of a row would carry the tensor core's
 // accumulation error of every step (measured: 2.4x the projector error at M = 1024).
-constexpr int kGroup = 8;                 // chunks per group (48 MMAs)
-constexpr int kDrainLag = 2;              // drain a group once conversion is this far past it
-static_assert(kDrainLag <= kGroup + 1, "the MMA waits for group g - 2 before group g");
+constexpr int kGroup = 4;                 // stages (32 values of K each) per group
 constexpr uint32_t kSplitTmemCols = 256;  // two accumulators of up to 128 columns
 
 template <int NB>
@@ -291,7 +294,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     unsigned char* base =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     constexpr int nr = split_nraw(NB);
+    constexpr int nlo = split_nlo(NB);
     constexpr int stage = split_stage(NB);
+    constexpr int b1_off = NB * 128, a_off = 2 * NB * 128;  // stage: [B chunk 0 | B chunk 1 | raw A]
     const FrameDesc* dp = descs + blockIdx.y;
     // frames whose last product is done (pass > t) keep their C
     if (!dp->sketch_tc || pass > dp->t || !sketch_on_tc(dp->method, pass) || !sketch_split(dp->prec, dp->t, pass))
@@ -299,24 +304,23 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int M = dp->M, l = dp->l, nb = 2 * sketch_tc_lpad(l);
     const int r0 = blockIdx.x * kRows;
     if (r0 >= M) return;
-    const int nchunks = (2 * M + 15) / 16;  // 16 FP32 of K per chunk
-    const int ngroups = (nchunks + kGroup - 1) / kGroup;
+    const int nst = (2 * M + 31) / 32;  // stages of 32 FP32 of K (the last one zero-filled past 2M)
+    const int ngroups = (nst + kGroup - 1) / kGroup;
     const CUtensorMap* ta = tmA + blockIdx.y;
     const CUtensorMap* tb = tmB + blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // layout: nr raw stages [B rows NB x 128 B | raw A 8 KB], two A tiles, barriers
-    unsigned char* conv = base + nr * stage;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(conv + 2 * kTileA);
-    uint64_t* full = bars;                    // [nr] raw A + B rows landed (TMA)
-    uint64_t* empty = bars + nr;              // [nr] MMA done with the stage's B rows
-    uint64_t* conv_full = bars + 2 * nr;      // [2] A tile written (128 converter arrivals)
-    uint64_t* conv_empty = bars + 2 * nr + 2;  // [2] MMA done with the A tile
-    uint64_t* acc_ready = bars + 2 * nr + 4;  // [2] group committed -> drain
-    uint64_t* acc_free = bars + 2 * nr + 6;   // [2] group drained (128 arrivals) -> MMA
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * nr + 8);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * nr + 9);
-    constexpr int raw_off = NB * 128;
+    // layout: nr stages, nlo lo tiles, barriers
+    unsigned char* lo_tiles = base + nr * stage;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(lo_tiles + nlo * kTileA);
+    uint64_t* full = bars;                 // [nr] raw A + B chunks landed (TMA)
+    uint64_t* empty = bars + nr;           // [nr] MMA done with the stage
+    uint64_t* conv_full = bars + 2 * nr;   // [2] lo tile written (128 converter arrivals)
+    uint64_t* conv_empty = conv_full + 2;  // [2] MMA done with the lo tile
+    uint64_t* acc_ready = conv_full + 4;   // [2] group committed -> drain
+    uint64_t* acc_free = conv_full + 6;    // [2] group drained (128 arrivals) -> MMA
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(conv_full + 8);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(conv_full + 9);
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < nr; ++i) {
@@ -347,56 +351,61 @@ __global__ void __launch_bounds__(kThreads, 2)
 
     if (warp == 0) {
         if (lane == 0) {
-            const uint32_t bytes = (uint32_t)kRawA + (uint32_t)nb * 128u;
-            for (int s = 0; s < nchunks; ++s) {
+            const uint32_t bytes = (uint32_t)kTileA + 2u * (uint32_t)nb * 128u;
+            for (int s = 0; s < nst; ++s) {
                 const int slot = s % nr;
                 if (!mbar_wait(&empty[slot], ((uint32_t)(s / nr) & 1u) ^ 1u, abort_flag)) break;
                 unsigned char* st = base + slot * stage;
                 mbar_expect_tx(&full[slot], bytes);
-                tma_load_2d(st + raw_off, ta, s * 16, r0, &full[slot]);
-                tma_load_2d(st, tb, s * 32, 0, &full[slot]);
+                tma_load_2d(st + a_off, ta, s * 32, r0, &full[slot]);
+                tma_load_2d(st, tb, s * 64, 0, &full[slot]);
+                tma_load_2d(st + b1_off, tb, s * 64 + 32, 0, &full[slot]);
             }
-            for (int s = max(0, nchunks - nr); s < nchunks; ++s)
+            for (int s = max(0, nst - nr); s < nst; ++s)
                 mbar_wait(&full[s % nr], (uint32_t)(s / nr) & 1u, abort_flag);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = idesc_tf32(128, (uint32_t)nb);
-            for (int s = 0; s < nchunks; ++s) {
-                const int slot = s % nr, cs = s & 1, g = s / kGroup, buf = g & 1, sg = s % kGroup;
+            for (int s = 0; s < nst; ++s) {
+                const int slot = s % nr, g = s / kGroup, buf = g & 1, sg = s % kGroup;
                 const uint32_t d = tmem + 128u * (uint32_t)buf;
                 if (sg == 0 && g >= 2) {  // buffer buf still holds group g - 2 until it is drained
                     if (!mbar_wait(&acc_free[buf], (uint32_t)((g >> 1) + 1) & 1u, abort_flag)) break;
                 }
                 if (!mbar_wait(&full[slot], (uint32_t)(s / nr) & 1u, abort_flag)) break;
-                if (!mbar_wait(&conv_full[cs], (uint32_t)(s >> 1) & 1u, abort_flag)) break;
                 tc_fence_after();
-                const uint32_t a = sa(conv + cs * kTileA), b = sa(base + slot * stage);
+                const uint32_t st = sa(base + slot * stage), a = st + a_off, alo = sa(lo_tiles + (s % nlo) * kTileA);
+                // the raw (hi) products first, while the converters write the lo tile; K = 8
+                // steps, the tensor core truncating raw A to TF32
 #pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {  // 16 values per chunk = two K = 8 steps
-                    const uint64_t a_hi = desc_sw128(a + 32 * kk), a_lo = desc_sw128(a + 64 + 32 * kk);
-                    const uint64_t b_hi = desc_sw128(b + 32 * kk), b_lo = desc_sw128(b + 64 + 32 * kk);
-                    mma_tf32(d, a_hi, b_hi, idesc, (sg > 0 || kk > 0) ? 1u : 0u);
-                    mma_tf32(d, a_hi, b_lo, idesc, 1u);
-                    mma_tf32(d, a_lo, b_hi, idesc, 1u);
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint32_t bt = st + (kk >> 1) * b1_off + 32 * (kk & 1);
+                    const uint64_t a_hi = desc_sw128(a + 32 * kk);
+                    mma_tf32(d, a_hi, desc_sw128(bt), idesc, (sg > 0 || kk > 0) ? 1u : 0u);
+                    mma_tf32(d, a_hi, desc_sw128(bt + 64), idesc, 1u);
                 }
-                mma_commit(&conv_empty[cs]);
+                if (!mbar_wait(&conv_full[s % nlo], (uint32_t)(s / nlo) & 1u, abort_flag)) break;
+                tc_fence_after();
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint32_t bt = st + (kk >> 1) * b1_off + 32 * (kk & 1);
+                    mma_tf32(d, desc_sw128(alo + 32 * kk), desc_sw128(bt), idesc, 1u);
+                }
+                mma_commit(&conv_empty[s % nlo]);
                 mma_commit(&empty[slot]);
-                if (sg == kGroup - 1 || s == nchunks - 1) mma_commit(&acc_ready[buf]);
+                if (sg == kGroup - 1 || s == nst - 1) mma_commit(&acc_ready[buf]);
             }
             // all MMAs retired before dealloc: the last group's commit tracks every earlier MMA
             mbar_wait(&acc_ready[(ngroups - 1) & 1], (uint32_t)((ngroups - 1) >> 1) & 1u, abort_flag);
         }
     } else {
-        // converters + two-level sum.  Conversion of a raw chunk (128 rows x 16 FP32 in
-        // 64-byte rows) into the A tile: hi in 16-byte chunk q of the row, lo in 4 + q
-        // (128-byte swizzle).  Lane (j = lane >> 3, k = lane & 7) of converter warp w takes
-        // row 32 u + 8 w + k, quarter q = (k >> 1) ^ j: every 8-lane phase then reads and
-        // writes eight distinct 16-byte bank groups.  Sum: thread (warp % 4, lane) owns row
-        // 32 (warp % 4) + lane (its TMEM lane quadrant) and keeps the row's NB accumulator
-        // columns in registers.
-        const int w = warp - 2, kq = lane & 7, q = (kq >> 1) ^ (lane >> 3);
-        const int q4 = warp & 3;
+        // converters + two-level sum.  Thread t = 0..127 owns row t of the stage: the lo
+        // parts x - trunc_tf32(x), rounded to TF32, of its 8 raw 16-byte chunks go to the
+        // same swizzled positions of the lo tile (lanes = rows: every 8-lane phase touches
+        // eight distinct 16-byte bank groups).  Sum: the same thread owns TMEM lane t (its
+        // warp's lane quadrant) and keeps the row's NB accumulator columns in registers.
+        const int q4 = warp & 3, t = 32 * q4 + lane;
         const uint32_t tl = tmem + ((uint32_t)(32 * q4) << 16);
         float sum[NB];
 #pragma unroll
@@ -409,48 +418,51 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (!ok) return;
             tc_fence_after();
 #pragma unroll
-            for (int c0 = 0; c0 < NB; c0 += 16) {
-                uint32_t v[16];
-                tmem_ld16(tl + 128u * (uint32_t)buf + (uint32_t)c0, v);
+            for (int c0 = 0; c0 < NB; c0 += 48) {  // up to three 16-column loads per wait
+                uint32_t v[48];
+#pragma unroll
+                for (int u = 0; u < 48; u += 16)
+                    if (c0 + u < NB) tmem_ld16(tl + 128u * (uint32_t)buf + (uint32_t)(c0 + u), *reinterpret_cast<uint32_t(*)[16]>(v + u));
                 tmem_wait_ld();
 #pragma unroll
-                for (int u = 0; u < 16; ++u) sum[c0 + u] += __uint_as_float(v[u]);
+                for (int u = 0; u < 48; ++u)
+                    if (c0 + u < NB) sum[c0 + u] += __uint_as_float(v[u]);
             }
             tc_fence_before();
             mbar_arrive(&acc_free[buf]);
         };
-        for (int s = 0; s < nchunks && ok; ++s) {
-            const int slot = s % nr, cs = s & 1;
-            if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], (uint32_t)(s / nr) & 1u, abort_flag) &&
-                                             mbar_wait(&conv_empty[cs], ((uint32_t)(s >> 1) & 1u) ^ 1u, abort_flag))) {
+        for (int s = 0; s < nst && ok; ++s) {
+            const int slot = s % nr;
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], (uint32_t)(s / nr) & 1u, abort_flag))) {
                 ok = false;
                 break;
             }
-            const unsigned char* raw = base + slot * stage + raw_off;
-            unsigned char* at = conv + cs * kTileA;
+            const unsigned char* raw = base + slot * stage + a_off;
+            uint4 lo[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int r = 32 * u + 8 * w + kq;
-                const float4 v = *reinterpret_cast<const float4*>(raw + 64 * r + 16 * q);
-                uint4 hi, lo;
-                hi.x = tf32_rn(v.x);
-                hi.y = tf32_rn(v.y);
-                hi.z = tf32_rn(v.z);
-                hi.w = tf32_rn(v.w);
-                lo.x = tf32_rn(v.x - __uint_as_float(hi.x));
-                lo.y = tf32_rn(v.y - __uint_as_float(hi.y));
-                lo.z = tf32_rn(v.z - __uint_as_float(hi.z));
-                lo.w = tf32_rn(v.w - __uint_as_float(hi.w));
-                *reinterpret_cast<uint4*>(at + swz(r, q)) = hi;
-                *reinterpret_cast<uint4*>(at + swz(r, 4 + q)) = lo;
+            for (int c = 0; c < 8; ++c) {
+                const uint4 v = *reinterpret_cast<const uint4*>(raw + swz(t, c));
+                lo[c].x = tf32_rn(__uint_as_float(v.x) - __uint_as_float(v.x & 0xFFFFE000u));
+                lo[c].y = tf32_rn(__uint_as_float(v.y) - __uint_as_float(v.y & 0xFFFFE000u));
+                lo[c].z = tf32_rn(__uint_as_float(v.z) - __uint_as_float(v.z & 0xFFFFE000u));
+                lo[c].w = tf32_rn(__uint_as_float(v.w) - __uint_as_float(v.w & 0xFFFFE000u));
             }
+            // the MMAs of stage s - nlo are done with this lo tile
+            if (!__all_sync(0xffffffffu, mbar_wait(&conv_empty[s % nlo], ((uint32_t)(s / nlo) & 1u) ^ 1u, abort_flag))) {
+                ok = false;
+                break;
+            }
+            unsigned char* lo_tile = lo_tiles + (s % nlo) * kTileA;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4*>(lo_tile + swz(t, c)) = lo[c];
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(&conv_full[cs]);
-            // groups whose chunks are all converted and kDrainLag behind are drained here
-            while (ok && gd < ngroups && min(gd * kGroup + kGroup - 1, nchunks - 1) + kDrainLag <= s) drain(gd++);
+            mbar_arrive(&conv_full[s % nlo]);
+            // the lo tile of stage s was free, so every MMA up to stage s - nlo has completed:
+            // the groups that ended there are ready
+            while (ok && gd < ngroups && min(gd * kGroup + kGroup - 1, nst - 1) + nlo <= s) drain(gd++);
         }
         while (ok && gd < ngroups) drain(gd++);
-        const int gr = r0 + 32 * q4 + lane;
+        const int gr = r0 + t;
         if (ok && gr < M) {
             float2* __restrict__ C = dp->C + (int64_t)gr * l;
 #pragma unroll
@@ -508,12 +520,12 @@ cudaError_t launch_sketch_tc(const FrameDesc* d, int n_frames, int max_M, int ma
     }
     if (any_split) {
         switch (nb_max) {  // 2 l_pad, l_pad a multiple of 8 up to kLMax
-            case 16: return launch_split<16>(d, grid, pass, tmA_split, tmB_split, s);
-            case 32: return launch_split<32>(d, grid, pass, tmA_split, tmB_split, s);
-            case 48: return launch_split<48>(d, grid, pass, tmA_split, tmB_split, s);
-            case 64: return launch_split<64>(d, grid, pass, tmA_split, tmB_split, s);
-            case 80: return launch_split<80>(d, grid, pass, tmA_split, tmB_split, s);
-            default: return launch_split<96>(d, grid, pass, tmA_split, tmB_split, s);
+            case 16: return launch_split<16>(d, grid, pass, tmA, tmB_split, s);
+            case 32: return launch_split<32>(d, grid, pass, tmA, tmB_split, s);
+            case 48: return launch_split<48>(d, grid, pass, tmA, tmB_split, s);
+            case 64: return launch_split<64>(d, grid, pass, tmA, tmB_split, s);
+            case 80: return launch_split<80>(d, grid, pass, tmA, tmB_split, s);
+            default: return launch_split<96>(d, grid, pass, tmA, tmB_split, s);
         }
     }
     return e;
