@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--method", default="projection", choices=["projection", "sampling"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16"],
-                    help="operand precision of the covariance / sketch / scan GEMMs (FP32 = 3xTF32)")
+                    help="operand precision of the covariance / sketch / scan GEMMs (FP32: three-term split products, TF32 pairs in the covariance and sketch, FP16 pairs in the scan)")
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--no-baseline", action="store_true", help="skip full-eig MUSIC and the CPU oracle")
     ap.add_argument("--cpu-sample", type=int, default=3, help="frames of the workload the oracle times")
@@ -63,7 +63,7 @@ def workload_config(method: str, batch: int, prec: str = "fp32"):
     return {"workload": f"ULA M=512 T=1024 K=8 l=24 t=1 L=15001, {batch} frames per step",
             "method": "random projection (Alg. 2)" if method == "projection" else "random sampling (Alg. 1)",
             "frames_per_step": batch, "M": 512, "T": 1024, "K": 8, "l": 24, "t": 1, "L": 15001,
-            "precision": {"fp32": "FP32 (3xTF32 tensor-core products)", "tf32": "TF32 operands",
+            "precision": {"fp32": "FP32 (split products on the tensor cores: 3xTF32 covariance and sketch, 3xFP16 scan)", "tf32": "TF32 operands",
                           "bf16": "BF16 operands"}[prec],
             "l2_flush": "none: inputs (268 MB/step) exceed the 129 MB L2"}
 
