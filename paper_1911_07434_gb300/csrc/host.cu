@@ -834,8 +834,11 @@ fm_status run_subspace_chain(fm_ctx* c, FrameDesc* dd, int n, const Maxes& mx, c
     auto sketch = [&](int p) {
         const bool tc = sk_maps && tc_pass;
         const char bits = tc ? (*tc_pass)[p] : (char)((p > 0 || mx.any_projection) ? kPassDense : 0);
+        // Omega: only frames whose first product runs on the CUDA cores need omega_kernel (the
+        // B-row preparation of the tensor-core sketch generates the others' Omega)
         cudaError_t e = fm::launch_sketch(dd, n, mx.M, mx.l, p, p == 0 && mx.any_sampling,
-                                          p == 0 && mx.any_projection, (bits & kPassDense) != 0, s);
+                                          p == 0 && mx.any_projection && (bits & kPassDense) != 0,
+                                          (bits & kPassDense) != 0, s);
         if (e == cudaSuccess && (bits & (kPassPlain | kPassSplit))) {
             const size_t m = sizeof(CUtensorMap) * (size_t)n;
             e = fm::launch_sketch_tc(dd, n, mx.M, mx.l, p, (bits & kPassPlain) != 0, (bits & kPassSplit) != 0, sk_maps,

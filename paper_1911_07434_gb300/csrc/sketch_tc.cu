@@ -73,8 +73,10 @@ static_assert(plain_nstages(2 * kLMax) * plain_stage(2 * kLMax) + kSmemExtra <= 
 // core matrix when t = 0).  Consecutive threads then write consecutive 16-byte
 // pieces (split) or complex pairs (plain) of a B row segment.
 constexpr int kBpRows = 64;
+constexpr int kBpThreads = 256;
+constexpr int kBpFill = kBpRows * kLMax / kBpThreads;  // tile entries per thread at most
 constexpr int kBpLd = kLMax + 1;  // odd row stride (in float2) against bank conflicts
-__global__ void __launch_bounds__(256) sketch_bprep_kernel(const FrameDesc* __restrict__ descs, int pass) {
+__global__ void __launch_bounds__(kBpThreads) sketch_bprep_kernel(const FrameDesc* __restrict__ descs, int pass) {
     __shared__ float2 vt[kBpRows * kBpLd];
     const FrameDesc* dp = descs + blockIdx.y;
     if (!dp->sketch_tc || pass > dp->t || !sketch_on_tc(dp->method, pass)) return;
@@ -83,26 +85,36 @@ __global__ void __launch_bounds__(256) sketch_bprep_kernel(const FrameDesc* __re
     if (m0 >= M) return;
     const int rows = min(kBpRows, M - m0);
     const bool gen = pass == 0 && dp->method == FM_RAND_PROJECTION;
-    for (int e = threadIdx.x; e < kBpRows * l; e += blockDim.x) {
-        const int r = e / l, j = e - r * l;
-        float2 v = make_float2(0.f, 0.f);
-        if (r < rows) {
-            const int64_t at = (int64_t)m0 * l + e;
+    // every load (or Omega entry) of the thread in flight at once, then into shared memory
+    float2 vv[kBpFill];
+#pragma unroll
+    for (int u = 0; u < kBpFill; ++u) {
+        const int e = threadIdx.x + kBpThreads * u;
+        vv[u] = make_float2(0.f, 0.f);
+        if (e < rows * l) {
             if (gen) {
-                v = gaussian_entry(dp->seed, dp->frame_id, m0 + r, j);
-                dp->V[at] = v;
+                const int r = e / l;
+                vv[u] = gaussian_entry(dp->seed, dp->frame_id, m0 + r, e - r * l);
             } else {
-                v = dp->V[at];
+                vv[u] = dp->V[(int64_t)m0 * l + e];
             }
         }
-        vt[r * kBpLd + j] = v;
+    }
+#pragma unroll
+    for (int u = 0; u < kBpFill; ++u) {
+        const int e = threadIdx.x + kBpThreads * u;
+        if (e < kBpRows * l) {
+            const int r = e / l;
+            vt[r * kBpLd + (e - r * l)] = vv[u];
+            if (gen && e < rows * l) dp->V[(int64_t)m0 * l + e] = vv[u];
+        }
     }
     __syncthreads();
     const int nrow = 2 * lp;
     if (!sketch_split(dp->prec, dp->t, pass)) {
         // one complex entry m per thread: (re row) [Vr, -Vi], (im row) [Vi, Vr] at 2m
         const int64_t rowlen = 2 * (int64_t)M;
-        for (int t = threadIdx.x; t < nrow * kBpRows; t += blockDim.x) {
+        for (int t = threadIdx.x; t < nrow * kBpRows; t += kBpThreads) {
             const int R = t / kBpRows, r = t - R * kBpRows;
             if (r >= rows) continue;
             const int j = R >> 1;
@@ -117,7 +129,7 @@ __global__ void __launch_bounds__(256) sketch_bprep_kernel(const FrameDesc* __re
     // values 4p .. 4p+3 of its chunk (entries m = 8c + 2p, 8c + 2p + 1), p >= 4 their lo
     const int64_t rowlen = sketch_split_rowlen(M);
     const int nchunks = (2 * M + 15) / 16, c0 = m0 / 8;
-    for (int t = threadIdx.x; t < nrow * 64; t += blockDim.x) {
+    for (int t = threadIdx.x; t < nrow * 64; t += kBpThreads) {
         const int R = t >> 6, cc = (t >> 3) & 7, p = t & 7;
         const int c = c0 + cc;
         if (c >= nchunks) continue;
@@ -504,7 +516,7 @@ cudaError_t launch_sketch_tc(const FrameDesc* d, int n_frames, int max_M, int ma
                              const void* tmB_split, cudaStream_t s) {
     const int lp = sketch_tc_lpad(max_l), nb_max = 2 * lp;
     count_launch();
-    sketch_bprep_kernel<<<dim3((unsigned)((max_M + kBpRows - 1) / kBpRows), n_frames), 256, 0, s>>>(d, pass);
+    sketch_bprep_kernel<<<dim3((unsigned)((max_M + kBpRows - 1) / kBpRows), n_frames), kBpThreads, 0, s>>>(d, pass);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)((max_M + kRows - 1) / kRows), n_frames);
