@@ -269,7 +269,7 @@ __host__ __device__ inline int scan_row_stride(int kpad, int KP) { return KP == 
 inline size_t scan_smem_elems(int M, int kpad, bool pos, int KP) {
     return (size_t)M * (size_t)(scan_row_stride(kpad, KP) + (pos ? 1 : 0));
 }
-cudaError_t launch_peaks(const FrameDesc* d, int n_frames, int max_K, cudaStream_t s);
+cudaError_t launch_peaks(const FrameDesc* d, int n_frames, int max_K, int max_L, cudaStream_t s);
 cudaError_t launch_test_matrix(uint64_t seed, uint64_t frame_id, int M, int l, float2* out, cudaStream_t s);
 cudaError_t launch_sample_indices(uint64_t seed, uint64_t frame_id, int M, int l, int* out, cudaStream_t s);
 size_t small_smem_bytes(int max_M, int l);

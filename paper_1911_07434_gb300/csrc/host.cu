@@ -1125,7 +1125,7 @@ static fm_status enqueue_run(fm_ctx* c, const RunPrep& rp, cudaStream_t s) {
         return cudaSuccess;
     });
     if (st != FM_OK) return st;
-    return stage(c, kStPeaks, s, [&] { return fm::launch_peaks(dd, n, mx.K, s); });
+    return stage(c, kStPeaks, s, [&] { return fm::launch_peaks(dd, n, mx.K, mx.L, s); });
 }
 
 fm_status fm_run(fm_ctx* c, const fm_frame* frames, int n, fm_stream stream) {
@@ -1693,7 +1693,7 @@ fm_status fm_peaks(fm_ctx* c, const float* P, int n, int L, int K, const fm_grid
     st = upload(c, host, c->arena, sizeof(FrameDesc) * n, s);
     if (st != FM_OK) return st;
     FrameDesc* dd = reinterpret_cast<FrameDesc*>(c->arena);
-    return stage(c, kStPeaks, s, [&] { return fm::launch_peaks(dd, n, K, s); });
+    return stage(c, kStPeaks, s, [&] { return fm::launch_peaks(dd, n, K, L, s); });
 }
 
 fm_status fm_test_matrix(fm_ctx* c, uint64_t seed, uint64_t frame_id, int M, int l, void* Pi, fm_stream stream) {

@@ -2,11 +2,14 @@
 //
 // A local maximum is i with P[i] > P[i-1] and P[i] >= P[i+1] (a missing
 // neighbour at either end never blocks).  Candidates are taken in the total
-// order (P descending, index ascending).  One CTA per frame: every thread
-// marks the maxima of its slice in a bit mask, then K rounds of a block-wide
-// argmax (warp shuffles, then one warp over the per-warp winners) extract the
-// winners in order; after each round every thread only considers candidates
-// that come after the winner in that order.
+// order (P descending, index ascending).  One CTA per frame: the frame's P is
+// first copied to shared memory with coalesced loads (grids of up to kSmemL
+// angles; longer ones are read in place) and every thread marks the maxima of
+// its slice in a bit mask.  For K <= kWarpK every warp then extracts its own K
+// best in order (K rounds of warp shuffles, each round taking the best candidate
+// after the previous winner), and one warp merges the 32 sorted lists: every
+// element of the global top K is in its own warp's top K, so the merge is exact.
+// Larger K take K rounds of a block-wide argmax instead.
 #include <float.h>
 #include <limits.h>
 
@@ -16,6 +19,8 @@ namespace fm {
 namespace {
 
 constexpr int kThreads = 1024;  // slice length (L + 1023) / 1024 <= 64 bits of mask (L <= 65536)
+constexpr int kSmemL = 48 * 1024;  // angles staged in shared memory (192 KB)
+constexpr int kWarpK = 64;         // per-warp candidate lists up to this K
 
 __device__ __forceinline__ bool better(float v, int i, float bv, int bi) {
     return (v > bv) || (v == bv && i < bi);
@@ -33,14 +38,20 @@ __device__ __forceinline__ void warp_best(float& v, int& i) {
     }
 }
 
-__global__ void __launch_bounds__(kThreads) peaks_kernel(const FrameDesc* __restrict__ descs) {
+__global__ void __launch_bounds__(kThreads) peaks_kernel(const FrameDesc* __restrict__ descs, int staged) {
+    extern __shared__ float ps[];
     __shared__ float wv[32];
     __shared__ int wi[32];
     __shared__ float gv;
     __shared__ int gi;
     const FrameDesc* dp = descs + blockIdx.x;
     const int L = dp->L, K = dp->K;
-    const float* __restrict__ P = dp->P;
+    const float* P = dp->P;
+    if (staged) {  // every frame of the launch has L <= kSmemL
+        for (int i = threadIdx.x; i < L; i += kThreads) ps[i] = __ldcg(dp->P + i);
+        __syncthreads();
+        P = ps;
+    }
     const int per = (L + kThreads - 1) / kThreads;
     const int i0 = threadIdx.x * per, i1 = min(L, i0 + per);
     uint64_t mask = 0;
@@ -53,6 +64,65 @@ __global__ void __launch_bounds__(kThreads) peaks_kernel(const FrameDesc* __rest
     float lastv = INFINITY;
     int lasti = -1;
     int found = 0;
+    if (K <= kWarpK) {
+        __shared__ float cv[32 * kWarpK];
+        __shared__ int ci[32 * kWarpK];
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int k = 0; k < K; ++k) {  // this warp's k-th best after (lastv, lasti)
+            float bv = -INFINITY;
+            int bi = INT_MAX;
+            uint64_t mm = mask;
+            while (mm) {
+                const int b = __ffsll((long long)mm) - 1;
+                mm &= mm - 1;
+                const int i = i0 + b;
+                const float v = P[i];
+                const bool after = (v < lastv) || (v == lastv && i > lasti);
+                if (after && better(v, i, bv, bi)) {
+                    bv = v;
+                    bi = i;
+                }
+            }
+            warp_best(bv, bi);
+            if (lane == 0) {
+                cv[warp * kWarpK + k] = bv;
+                ci[warp * kWarpK + k] = bi;
+            }
+            if (bi == INT_MAX) break;  // the list ends here (warp-uniform)
+            lastv = bv;
+            lasti = bi;
+        }
+        __syncthreads();
+        if (warp == 0) {  // merge: lane j holds the head of warp j's list
+            int ptr = 0;
+            float hv = cv[lane * kWarpK];
+            int hi = ci[lane * kWarpK];
+            for (int k = 0; k < K; ++k) {
+                float v = hv;
+                int i = hi;
+                warp_best(v, i);
+                if (i == INT_MAX) break;
+                if (hi == i) {  // indices are unique: this lane's head won
+                    ++ptr;
+                    hv = ptr < K ? cv[lane * kWarpK + ptr] : -INFINITY;
+                    hi = ptr < K ? ci[lane * kWarpK + ptr] : INT_MAX;
+                }
+                if (lane == 0) {
+                    dp->peak_idx[k] = i;
+                    dp->peak_deg[k] = (float)(dp->theta0 + (double)i * dp->step);
+                }
+                ++found;
+            }
+            if (lane == 0) {
+                for (int k = found; k < K; ++k) {
+                    dp->peak_idx[k] = -1;
+                    dp->peak_deg[k] = NAN;
+                }
+                *dp->n_peaks = found;
+            }
+        }
+        return;
+    }
     for (int k = 0; k < K; ++k) {
         float bv = -INFINITY;
         int bi = INT_MAX;
@@ -107,10 +177,16 @@ __global__ void __launch_bounds__(kThreads) peaks_kernel(const FrameDesc* __rest
 
 }  // namespace
 
-cudaError_t launch_peaks(const FrameDesc* d, int n_frames, int max_K, cudaStream_t s) {
+cudaError_t launch_peaks(const FrameDesc* d, int n_frames, int max_K, int max_L, cudaStream_t s) {
     (void)max_K;
+    const int staged = max_L <= kSmemL ? 1 : 0;
+    const size_t smem = staged ? sizeof(float) * (size_t)max_L : 0;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(peaks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     count_launch();
-    peaks_kernel<<<n_frames, kThreads, 0, s>>>(d);
+    peaks_kernel<<<n_frames, kThreads, smem, s>>>(d, staged);
     return cudaGetLastError();
 }
 
