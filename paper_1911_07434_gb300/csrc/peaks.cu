@@ -47,8 +47,20 @@ __global__ void __launch_bounds__(kThreads) peaks_kernel(const FrameDesc* __rest
     const FrameDesc* dp = descs + blockIdx.x;
     const int L = dp->L, K = dp->K;
     const float* P = dp->P;
-    if (staged) {  // every frame of the launch has L <= kSmemL
-        for (int i = threadIdx.x; i < L; i += kThreads) ps[i] = __ldcg(dp->P + i);
+    if (staged) {  // every frame of the launch has L <= kSmemL; eight loads in flight per thread
+        for (int base = threadIdx.x; base < L; base += 8 * kThreads) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = base + u * kThreads;
+                v[u] = i < L ? __ldcg(dp->P + i) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = base + u * kThreads;
+                if (i < L) ps[i] = v[u];
+            }
+        }
         __syncthreads();
         P = ps;
     }
@@ -181,7 +193,7 @@ cudaError_t launch_peaks(const FrameDesc* d, int n_frames, int max_K, int max_L,
     (void)max_K;
     const int staged = max_L <= kSmemL ? 1 : 0;
     const size_t smem = staged ? sizeof(float) * (size_t)max_L : 0;
-    if (smem > 48 * 1024) {
+    if (staged) {  // the static candidate lists and this dynamic part together pass the 48 KB default
         cudaError_t e = cudaFuncSetAttribute(peaks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
