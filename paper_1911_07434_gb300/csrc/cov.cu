@@ -30,6 +30,7 @@ __device__ __forceinline__ void tile_coords(int b, int nt, int& ti, int& tj) {
 }
 
 __global__ void __launch_bounds__(kThreads, 2) cov_fp32_kernel(const FrameDesc* __restrict__ descs) {
+    pdl_enter();
     extern __shared__ float4 smem_raw[];
     float2* smem = reinterpret_cast<float2*>(smem_raw);
     float2(*As)[kStage][kTile] = reinterpret_cast<float2(*)[kStage][kTile]>(smem);
@@ -144,6 +145,7 @@ __global__ void __launch_bounds__(kThreads, 2) cov_fp32_kernel(const FrameDesc* 
 // the workspace copy the tensor-core covariance reads (even ldx, 256-byte base).
 // Consecutive threads take consecutive snapshots of a row: coalesced both ways.
 __global__ void repack_kernel(const FrameDesc* __restrict__ descs) {
+    pdl_enter();
     const FrameDesc* dp = descs + blockIdx.y;
     if (!dp->Xin) return;
     const int M = dp->M, T = dp->T;
@@ -160,7 +162,7 @@ cudaError_t launch_repack(const FrameDesc* d, int n_frames, int max_M, int max_T
     const int64_t n = (int64_t)max_M * max_T;
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 256);
     count_launch();
-    repack_kernel<<<dim3(blocks, n_frames), 256, 0, s>>>(d);
+    launch_pdl(repack_kernel, dim3(dim3(blocks, n_frames)), dim3(256), (size_t)(0), s, d);
     return cudaGetLastError();
 }
 
@@ -168,7 +170,7 @@ cudaError_t launch_covariance(const FrameDesc* d, int n_frames, int max_M, cudaS
     const int nt = (max_M + kTile - 1) / kTile;
     dim3 grid(nt * (nt + 1) / 2, n_frames);
     count_launch();
-    cov_fp32_kernel<<<grid, kThreads, kSmemBytes, s>>>(d);
+    launch_pdl(cov_fp32_kernel, dim3(grid), dim3(kThreads), (size_t)(kSmemBytes), s, d);
     return cudaGetLastError();
 }
 

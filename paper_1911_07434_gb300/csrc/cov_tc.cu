@@ -159,6 +159,7 @@ __device__ __forceinline__ void write_tile(const float2* S, float2* __restrict__
 __global__ void __launch_bounds__(kThreads, 1)
     cov_tc_kernel(const FrameDesc* __restrict__ descs, const CUtensorMap* __restrict__ tmaps,
                   const CovItem* __restrict__ items, float2* __restrict__ partials, int* __restrict__ counters) {
+    pdl_enter();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* raw = base;                              // kNRaw x {A, B}
@@ -397,7 +398,7 @@ cudaError_t launch_covariance_tc(const FrameDesc* d, const void* tmaps, const Co
     cudaError_t e = cudaFuncSetAttribute(cov_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     count_launch();
-    cov_tc_kernel<<<n_items, kThreads, kSmemBytes, s>>>(d, reinterpret_cast<const CUtensorMap*>(tmaps), items,
+    launch_pdl(cov_tc_kernel, dim3(n_items), dim3(kThreads), (size_t)(kSmemBytes), s, d, reinterpret_cast<const CUtensorMap*>(tmaps), items,
                                                         partials, counters);
     return cudaGetLastError();
 }

@@ -228,6 +228,34 @@ struct CopyEntry {
 extern thread_local uint64_t g_kernel_launches;
 inline void count_launch() { ++g_kernel_launches; }
 
+// Programmatic dependent launch along a call's chain of kernels.  Every chain kernel
+// starts with pdl_enter(): it waits until the previous kernel of the stream has
+// completed and its writes are visible, so no data is read early, while the launch of
+// this grid itself already overlapped the previous grid's exit (each CTA's exit is its
+// trigger).  Launched without the attribute (or first in the stream) the wait returns
+// at once.  An explicit trigger at CTA entry was measured slower (0.919 vs 0.839 ms per
+// bench step): the next grids' CTAs were placed on the SMs the previous grid's last
+// wave left free, unevenly for their own run.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch of a chain kernel with programmatic stream serialization (the kernel calls
+// pdl_enter() before touching anything an earlier kernel wrote).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Implemented in the .cu files; each returns cudaGetLastError() after launching.
 // counters (nullable): n_counters ints cleared with the status words (the covariance's
 // split-tile counters, so that a run after an aborted one starts from zero)

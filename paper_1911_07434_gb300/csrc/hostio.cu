@@ -8,6 +8,7 @@ namespace {
 
 // One CTA per entry; every output is a whole number of 4-byte words, 4-byte aligned.
 __global__ void __launch_bounds__(256) scatter_kernel(const CopyEntry* __restrict__ tab, int n) {
+    pdl_enter();
     const int e = blockIdx.x;
     if (e >= n) return;
     const CopyEntry c = tab[e];
@@ -22,7 +23,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(const CopyEntry* __restric
 cudaError_t launch_scatter(const CopyEntry* tab, int n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     count_launch();
-    scatter_kernel<<<n, 256, 0, s>>>(tab, n);
+    launch_pdl(scatter_kernel, dim3(n), dim3(256), (size_t)(0), s, tab, n);
     return cudaGetLastError();
 }
 

@@ -39,6 +39,7 @@ __device__ __forceinline__ void warp_best(float& v, int& i) {
 }
 
 __global__ void __launch_bounds__(kThreads) peaks_kernel(const FrameDesc* __restrict__ descs, int staged) {
+    pdl_enter();
     extern __shared__ float ps[];
     __shared__ float wv[32];
     __shared__ int wi[32];
@@ -198,7 +199,7 @@ cudaError_t launch_peaks(const FrameDesc* d, int n_frames, int max_K, int max_L,
         if (e != cudaSuccess) return e;
     }
     count_launch();
-    peaks_kernel<<<n_frames, kThreads, smem, s>>>(d, staged);
+    launch_pdl(peaks_kernel, dim3(n_frames), dim3(kThreads), (size_t)(smem), s, d, staged);
     return cudaGetLastError();
 }
 

@@ -60,6 +60,7 @@ __device__ __forceinline__ void load_chunk(float2* buf, const float2* __restrict
 
 template <bool XH>
 __global__ void __launch_bounds__(kThreads) xgemm_kernel(const FrameDesc* __restrict__ descs) {
+    pdl_enter();
     extern __shared__ float2 smem[];
     const FrameDesc* dp = descs + blockIdx.y;
     if (!dp->refine) return;
@@ -133,12 +134,12 @@ cudaError_t launch_refine(const FrameDesc* d, int n_frames, int max_M, int max_T
     if (e != cudaSuccess) return e;
     dim3 g1((max_T + kRows - 1) / kRows, n_frames);
     count_launch();
-    xgemm_kernel<true><<<g1, kThreads, kSmemBytes, s>>>(d);
+    launch_pdl(xgemm_kernel<true>, dim3(g1), dim3(kThreads), (size_t)(kSmemBytes), s, d);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 g2((max_M + kRows - 1) / kRows, n_frames);
     count_launch();
-    xgemm_kernel<false><<<g2, kThreads, kSmemBytes, s>>>(d);
+    launch_pdl(xgemm_kernel<false>, dim3(g2), dim3(kThreads), (size_t)(kSmemBytes), s, d);
     return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ constexpr int kThreads = 256;
 // split-tile counters (first kernel of a run).
 __global__ void grid_table_kernel(const GridDesc* __restrict__ grids, int n_grids, const FrameDesc* __restrict__ descs,
                                   int n_frames, int* __restrict__ counters, int n_counters) {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if ((int)blockIdx.y == n_grids) {
         if (descs && i < n_frames && descs[i].status) *descs[i].status = 0;
@@ -170,6 +171,7 @@ __device__ __forceinline__ void load_us(const float2* __restrict__ Us, float2* U
 
 template <int KP, int NB, bool FIXUP>
 __global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restrict__ descs) {
+    pdl_enter();
     extern __shared__ float4 smem_raw[];
     float2* Usm = reinterpret_cast<float2*>(smem_raw);  // [M][kp4]
     const FrameDesc* dp = descs + blockIdx.y;
@@ -258,7 +260,7 @@ cudaError_t launch_kp(const FrameDesc* d, int n_frames, int max_L, size_t smem_e
     }
     dim3 grid(FIXUP ? kFixCtas : (max_L + kThreads - 1) / kThreads, n_frames);
     count_launch();
-    scan_kernel<KP, NB, FIXUP><<<grid, kThreads, smem, s>>>(d);
+    launch_pdl(scan_kernel<KP, NB, FIXUP>, dim3(grid), dim3(kThreads), (size_t)(smem), s, d);
     return cudaGetLastError();
 }
 
@@ -286,7 +288,7 @@ cudaError_t launch_grid_table(const GridDesc* g, int n_grids, int max_L, const F
     const int gx = (max(max(max_L, d ? n_frames : 0), counters ? n_counters : 0) + 255) / 256;
     dim3 grid(gx, n_grids + 1);
     count_launch();
-    grid_table_kernel<<<grid, 256, 0, s>>>(g, n_grids, d, n_frames, counters, n_counters);
+    launch_pdl(grid_table_kernel, dim3(grid), dim3(256), (size_t)(0), s, g, n_grids, d, n_frames, counters, n_counters);
     return cudaGetLastError();
 }
 

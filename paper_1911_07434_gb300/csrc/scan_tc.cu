@@ -63,6 +63,7 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t* hi, uint32_t*
 // then [hi | lo] of antennas 16s+8 .. 16s+15, scaled by 2^8 (the first half of the row).
 __global__ void scan_bprep_kernel(const FrameDesc* __restrict__ descs, int n_frames, int M, int Mp, int ncp, int prec,
                                   float* __restrict__ Bp) {
+    pdl_enter();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (f, k, m)
     const int64_t total = (int64_t)n_frames * ncp * Mp;
     if (e >= total) return;
@@ -135,6 +136,7 @@ template <int NCP, bool POS>
 __global__ void __launch_bounds__(kThreads, 1)
     scan_tc_kernel(const FrameDesc* __restrict__ descs, int n_frames, const CUtensorMap* __restrict__ tmB, int M,
                    int Mp, int L, int prec) {
+    pdl_enter();
     constexpr int kRowsPerFrame = 2 * NCP;
     constexpr int kFramesPerCta = kRowsB / kRowsPerFrame;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -400,7 +402,7 @@ cudaError_t launch_ncp_t(const FrameDesc* d, int n_frames, const void* tmB, int 
     const int fpc = kRowsB / (2 * NCP);
     dim3 grid((L + kRowsA - 1) / kRowsA, (n_frames + fpc - 1) / fpc);
     count_launch();
-    scan_tc_kernel<NCP, POS><<<grid, kThreads, kSmemBytes, s>>>(d, n_frames, reinterpret_cast<const CUtensorMap*>(tmB),
+    launch_pdl(scan_tc_kernel<NCP, POS>, dim3(grid), dim3(kThreads), (size_t)(kSmemBytes), s, d, n_frames, reinterpret_cast<const CUtensorMap*>(tmB),
                                                                 M, Mp, L, prec);
     return cudaGetLastError();
 }
@@ -426,7 +428,7 @@ cudaError_t launch_scan_tc(const FrameDesc* d, int n_frames, int M, int ncols, i
     const int Mp = scan_tc_mp(M);
     const int64_t total = (int64_t)n_frames * ncp * Mp;
     count_launch();
-    scan_bprep_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(d, n_frames, M, Mp, ncp, prec, bprep);
+    launch_pdl(scan_bprep_kernel, dim3((unsigned)((total + 255) / 256)), dim3(256), (size_t)(0), s, d, n_frames, M, Mp, ncp, prec, bprep);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     switch (ncp) {

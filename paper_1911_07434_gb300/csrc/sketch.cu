@@ -36,6 +36,7 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid
 
 template <int NQ>
 __global__ void __launch_bounds__(kThreads) sketch_dense_kernel(const FrameDesc* __restrict__ descs, int pass) {
+    pdl_enter();
     extern __shared__ float4 smem_raw[];
     float2(*As)[kRows][kKc + 1] = reinterpret_cast<float2(*)[kRows][kKc + 1]>(smem_raw);
     float2* Bbase = reinterpret_cast<float2*>(smem_raw) + 2 * kRows * (kKc + 1);
@@ -130,6 +131,7 @@ __global__ void __launch_bounds__(kThreads) sketch_dense_kernel(const FrameDesc*
 // Omega -> V for projection frames (pass 0), one thread per entry.  Frames whose first
 // product runs on the tensor cores get Omega from the B-row preparation instead.
 __global__ void omega_kernel(const FrameDesc* __restrict__ descs) {
+    pdl_enter();
     const FrameDesc* dp = descs + blockIdx.y;
     if (dp->method != FM_RAND_PROJECTION || dp->sketch_tc) return;
     const int M = dp->M, l = dp->l;
@@ -140,6 +142,7 @@ __global__ void omega_kernel(const FrameDesc* __restrict__ descs) {
 
 // pass 0, sampling: C[i][j] = conj(R[I[j]][i])
 __global__ void __launch_bounds__(256) sketch_gather_kernel(const FrameDesc* __restrict__ descs) {
+    pdl_enter();
     extern __shared__ int ismem[];
     const FrameDesc* dp = descs + blockIdx.y;
     if (dp->method != FM_RAND_SAMPLING) return;
@@ -184,7 +187,7 @@ cudaError_t launch_dense(const FrameDesc* d, int n_frames, int max_M, int max_l,
         if (e != cudaSuccess) return e;
     }
     count_launch();
-    sketch_dense_kernel<NQ><<<dim3((max_M + kRows - 1) / kRows, n_frames), kThreads, smem, s>>>(d, pass);
+    launch_pdl(sketch_dense_kernel<NQ>, dim3(dim3((max_M + kRows - 1) / kRows, n_frames)), dim3(kThreads), (size_t)(smem), s, d, pass);
     return cudaGetLastError();
 }
 
@@ -195,13 +198,13 @@ cudaError_t launch_sketch(const FrameDesc* d, int n_frames, int max_M, int max_l
     if (pass == 0 && any_gather) {
         const size_t gsm = sizeof(int) * (size_t)(max_M + max_l);
         count_launch();
-        sketch_gather_kernel<<<dim3((max_M + 255) / 256, n_frames), 256, gsm, s>>>(d);
+        launch_pdl(sketch_gather_kernel, dim3(dim3((max_M + 255) / 256, n_frames)), dim3(256), (size_t)(gsm), s, d);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (pass == 0 && any_omega) {
         count_launch();
-        omega_kernel<<<dim3((max_M * max_l + 255) / 256, n_frames), 256, 0, s>>>(d);
+        launch_pdl(omega_kernel, dim3(dim3((max_M * max_l + 255) / 256, n_frames)), dim3(256), (size_t)(0), s, d);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -77,6 +77,7 @@ constexpr int kBpThreads = 256;
 constexpr int kBpFill = kBpRows * kLMax / kBpThreads;  // tile entries per thread at most
 constexpr int kBpLd = kLMax + 1;  // odd row stride (in float2) against bank conflicts
 __global__ void __launch_bounds__(kBpThreads) sketch_bprep_kernel(const FrameDesc* __restrict__ descs, int pass) {
+    pdl_enter();
     __shared__ float2 vt[kBpRows * kBpLd];
     const FrameDesc* dp = descs + blockIdx.y;
     if (!dp->sketch_tc || pass > dp->t || !sketch_on_tc(dp->method, pass)) return;
@@ -236,6 +237,7 @@ __device__ __forceinline__ void tmem_teardown(const FrameDesc* dp, const Ring& r
 __global__ void __launch_bounds__(kThreads, 2)
     sketch_tc_kernel(const FrameDesc* __restrict__ descs, const CUtensorMap* __restrict__ tmA,
                      const CUtensorMap* __restrict__ tmB, int pass, int nb_max) {
+    pdl_enter();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -302,6 +304,7 @@ template <int NB>
 __global__ void __launch_bounds__(kThreads, 2)
     sketch_split_kernel(const FrameDesc* __restrict__ descs, const CUtensorMap* __restrict__ tmA,
                         const CUtensorMap* __restrict__ tmB, int pass) {
+    pdl_enter();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -500,7 +503,7 @@ cudaError_t launch_split(const FrameDesc* d, dim3 grid, int pass, const void* tm
     cudaError_t e = cudaFuncSetAttribute(sketch_split_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     count_launch();
-    sketch_split_kernel<NB><<<grid, kThreads, smem, s>>>(d, reinterpret_cast<const CUtensorMap*>(tmA),
+    launch_pdl(sketch_split_kernel<NB>, dim3(grid), dim3(kThreads), (size_t)(smem), s, d, reinterpret_cast<const CUtensorMap*>(tmA),
                                                          reinterpret_cast<const CUtensorMap*>(tmB), pass);
     return cudaGetLastError();
 }
@@ -516,7 +519,7 @@ cudaError_t launch_sketch_tc(const FrameDesc* d, int n_frames, int max_M, int ma
                              const void* tmB_split, cudaStream_t s) {
     const int lp = sketch_tc_lpad(max_l), nb_max = 2 * lp;
     count_launch();
-    sketch_bprep_kernel<<<dim3((unsigned)((max_M + kBpRows - 1) / kBpRows), n_frames), kBpThreads, 0, s>>>(d, pass);
+    launch_pdl(sketch_bprep_kernel, dim3(dim3((unsigned)((max_M + kBpRows - 1) / kBpRows), n_frames)), dim3(kBpThreads), (size_t)(0), s, d, pass);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)((max_M + kRows - 1) / kRows), n_frames);
@@ -525,7 +528,7 @@ cudaError_t launch_sketch_tc(const FrameDesc* d, int n_frames, int max_M, int ma
         e = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         count_launch();
-        sketch_tc_kernel<<<grid, kThreads, smem, s>>>(d, reinterpret_cast<const CUtensorMap*>(tmA),
+        launch_pdl(sketch_tc_kernel, dim3(grid), dim3(kThreads), (size_t)(smem), s, d, reinterpret_cast<const CUtensorMap*>(tmA),
                                                       reinterpret_cast<const CUtensorMap*>(tmB), pass, nb_max);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

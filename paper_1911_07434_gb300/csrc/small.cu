@@ -1137,6 +1137,7 @@ __device__ void apply_d(const float2* A, float2* __restrict__ dst, int rows, int
 // ---------------------------------------------------------------- kernel ----
 __global__ void __launch_bounds__(kThreads, 3) small_cluster_kernel(const FrameDesc* __restrict__ descs, int mode,
                                                                  int pass) {
+    pdl_enter();
     extern __shared__ float4 smem_raw[];
     cg::cluster_group cl = cg::this_cluster();
     const int nc = (int)cl.num_blocks();
@@ -1305,13 +1306,15 @@ cudaError_t launch_small(const FrameDesc* d, int n_frames, int max_M, int max_l,
     cfg.blockDim = dim3(kThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)nc;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // a chain kernel (pdl_enter)
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     count_launch();
     e = cudaLaunchKernelEx(&cfg, small_cluster_kernel, d, mode, pass);
     if (e != cudaSuccess) return e;
