@@ -260,6 +260,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int i = i0 + r;
         const float2 qq = (i < L) ? descs[0].qtab[i] : make_float2(0.f, 0.f);
         const float2* __restrict__ pos = descs[0].pos;
+        // FP32 mode, uniform array: a_{m + u} = a_m a_u, so this thread's 8 antennas of a stage
+        // (16 s + 8 g + u) are one exactly reduced base value times a_u (u < 8, computed once);
+        // each product adds about 2u of rounding to entries accurate to about u
+        float2 w8[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) w8[u] = steer_exact(u, qq.x, qq.y);
         for (int s = 0; s < nstages; ++s) {
             const int slot = s % kNStages;
             if (!mbar_wait(&empty[slot], ((uint32_t)(s / kNStages) & 1u) ^ 1u, abort_flag)) break;
@@ -280,14 +286,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (prec == FM_PREC_FP32) {  // antennas 16s + 8g .. +7: FP16 hi in 16-byte chunks 4g, 4g+1, lo in 4g+2, 4g+3
 #pragma unroll
+                const int mb = 16 * s + 8 * g;
+                const float2 ab = POS ? make_float2(0.f, 0.f) : steer_exact(mb, qq.x, qq.y);
                 for (int cc = 0; cc < 2; ++cc) {
                     uint4 hi, lo;
                     uint32_t* hv = reinterpret_cast<uint32_t*>(&hi);
                     uint32_t* lv = reinterpret_cast<uint32_t*>(&lo);
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const int m = 16 * s + 8 * g + 4 * cc + u;
-                        const float2 a = (i < L && m < M) ? steer_elem<POS>(m, qq, pos) : make_float2(0.f, 0.f);
+                        const int m = mb + 4 * cc + u;
+                        float2 a = make_float2(0.f, 0.f);
+                        if (i < L && m < M) a = POS ? steer_elem<POS>(m, qq, pos) : cmul(ab, w8[4 * cc + u]);
                         split_f16x2(kScaleF16 * a.x, kScaleF16 * a.y, hv[u], lv[u]);
                     }
                     *reinterpret_cast<uint4*>(arow + swz(r, 4 * g + cc)) = hi;
@@ -333,10 +342,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float us = prec == FM_PREC_FP32 ? kUnscaleF16 : 1.f;  // exact power of two
             if constexpr (kRowsPerFrame <= 16) {
                 const int nchunks = (nrows + 15) / 16;
-                for (int ch = half; ch < nchunks; ch += 2) {
-                    uint32_t v[16];
-                    tmem_ld16(tl + 16 * ch, v);
+                constexpr int kB = 4;  // TMEM loads in flight per wait
+                for (int c0 = half; c0 < nchunks; c0 += 2 * kB) {
+                    uint32_t vb[kB][16];
+#pragma unroll
+                    for (int b = 0; b < kB; ++b)
+                        if (c0 + 2 * b < nchunks) tmem_ld16(tl + 16 * (c0 + 2 * b), vb[b]);
                     tmem_wait_ld();
+#pragma unroll
+                    for (int b = 0; b < kB; ++b) {
+                    const int ch = c0 + 2 * b;
+                    if (ch >= nchunks) break;
+                    const uint32_t* v = vb[b];
 #pragma unroll
                     for (int j = 0; j < 16; j += kRowsPerFrame) {
                         float acc = 0.f;
@@ -354,6 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if (dp->Pdb) dp->Pdb[ia] = 10.0f * log10f(fminf(P, 3.402823466e38f));
                         }
                         list_main_lobe(descs + f0 + min(f, nf - 1), f < nf, ia, L, Mf, den, lane);
+                    }
                     }
                 }
             } else {
