@@ -110,18 +110,28 @@ __global__ void scan_bprep_kernel(const FrameDesc* __restrict__ descs, int n_fra
 
 // Steering entry m of angle row (q_hi, q_lo): a uniform array, or the element
 // positions of the scan group (POS; every frame of a group shares them).
-// Angle ia of frame dp goes to the main-lobe recompute when ||U_s^H a||^2 = M - den
+// Angle ia of frame fo goes to the main-lobe recompute when ||U_s^H a||^2 = M - den
 // exceeds 4 ncols (or den is NaN).  Warp-wide: the flagged lanes take consecutive
-// entries of the frame's list (one atomic per warp); `frame_ok` and dp are uniform.
-__device__ __forceinline__ void list_main_lobe(const FrameDesc* dp, bool frame_ok, int ia, int L, float Mf, float den,
+// entries of the frame's list (one atomic per warp); `frame_ok` and fo are uniform.
+// The epilogue's per-frame outputs, copied from the descriptors to shared memory once per
+// CTA (the epilogue would otherwise wait on a descriptor load for every frame it writes).
+struct FrameOut {
+    float* P;
+    float* Pdb;
+    int* fix_count;
+    int* fix_list;
+    float lobe;  // main-lobe threshold 4 ncols
+};
+
+__device__ __forceinline__ void list_main_lobe(const FrameOut& fo, bool frame_ok, int ia, int L, float Mf, float den,
                                                int lane) {
-    const bool flag = frame_ok && ia < L && !(den >= Mf - 4.0f * (float)dp->ncols);
+    const bool flag = frame_ok && ia < L && !(den >= Mf - fo.lobe);
     const unsigned bal = __ballot_sync(0xffffffffu, flag);
     if (!bal) return;
     int base = 0;
-    if (lane == 0) base = atomicAdd(dp->fix_count, __popc(bal));
+    if (lane == 0) base = atomicAdd(fo.fix_count, __popc(bal));
     base = __shfl_sync(0xffffffffu, base, 0);
-    if (flag) dp->fix_list[base + __popc(bal & ((1u << lane) - 1u))] = ia;
+    if (flag) fo.fix_list[base + __popc(bal & ((1u << lane) - 1u))] = ia;
 }
 
 template <bool POS>
@@ -175,6 +185,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                      "r"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __shared__ FrameOut fout[kFramesPerCta];
+    for (int f = threadIdx.x; f < nf; f += kThreads) {
+        const FrameDesc* dp = descs + f0 + f;
+        fout[f] = FrameOut{dp->P, dp->Pdb, dp->fix_count, dp->fix_list, 4.0f * (float)dp->ncols};
     }
     tc_fence_before();
     __syncthreads();
@@ -364,13 +379,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                         const int f = (16 * ch + j) / kRowsPerFrame;
                         const float den = Mf - acc;
+                        const FrameOut& fo = fout[min(f, nf - 1)];
                         if (f < nf && ia < L) {
-                            const FrameDesc* dp = descs + f0 + f;
                             const float P = (den > 0.f) ? 1.0f / den : INFINITY;
-                            dp->P[ia] = P;
-                            if (dp->Pdb) dp->Pdb[ia] = 10.0f * log10f(fminf(P, 3.402823466e38f));
+                            fo.P[ia] = P;
+                            if (fo.Pdb) fo.Pdb[ia] = 10.0f * log10f(fminf(P, 3.402823466e38f));
                         }
-                        list_main_lobe(descs + f0 + min(f, nf - 1), f < nf, ia, L, Mf, den, lane);
+                        list_main_lobe(fo, f < nf, ia, L, Mf, den, lane);
                     }
                     }
                 }
@@ -389,13 +404,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                     const float den = Mf - acc;
+                    const FrameOut& fo = fout[f];
                     if (ia < L) {
-                        const FrameDesc* dp = descs + f0 + f;
                         const float P = (den > 0.f) ? 1.0f / den : INFINITY;
-                        dp->P[ia] = P;
-                        if (dp->Pdb) dp->Pdb[ia] = 10.0f * log10f(fminf(P, 3.402823466e38f));
+                        fo.P[ia] = P;
+                        if (fo.Pdb) fo.Pdb[ia] = 10.0f * log10f(fminf(P, 3.402823466e38f));
                     }
-                    list_main_lobe(descs + f0 + f, true, ia, L, Mf, den, lane);
+                    list_main_lobe(fo, true, ia, L, Mf, den, lane);
                 }
             }
         }
