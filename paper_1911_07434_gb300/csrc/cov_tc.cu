@@ -314,39 +314,45 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
             const float invT = (float)(1.0 / (double)T);
             const int h = (warp - 2) >> 2;
-            if (diag) {  // the ri block first: Im R_II = (ri^T - ri) / T
-                for (int cc = 64 * h; cc < 64 * h + 64; cc += 16) {
-                    uint32_t ri[16];
-                    tmem_ld16(tl + 128 + cc, ri);
-                    tmem_wait_ld();
+            if (diag) {  // the ri block first: Im R_II = (ri^T - ri) / T (four TMEM loads per wait)
+                uint32_t ri[4][16];
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) T1[row * kLd + cc + c] = __uint_as_float(ri[c]);
-                }
-                epi_sync();
-            }
-            for (int cc = 64 * h; cc < 64 * h + 64; cc += 16) {
-                uint32_t rr_[16], a1[16], a2[16];
-                tmem_ld16(tl + cc, rr_);
-                if (diag) {
-                    tmem_ld16(tl + 256 + cc, a1);  // ii
-                } else {
-                    tmem_ld16(tl + 256 + cc, a2);  // ir
-                    tmem_ld16(tl + 384 + cc, a1);  // ii
-                }
-                uint32_t riv[16];
-                if (!diag) tmem_ld16(tl + 128 + cc, riv);
+                for (int b = 0; b < 4; ++b) tmem_ld16(tl + 128 + 64 * h + 16 * b, ri[b]);
                 tmem_wait_ld();
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    const int col = cc + c;
-                    const float re = (__uint_as_float(rr_[c]) + __uint_as_float(a1[c])) * invT;
-                    float im;
-                    if (diag)
-                        im = (col == row) ? 0.f : (T1[col * kLd + row] - T1[row * kLd + col]) * invT;
-                    else
-                        im = (__uint_as_float(a2[c]) - __uint_as_float(riv[c])) * invT;
-                    S[row * kLd + col] = make_float2(re, im);
+                for (int b = 0; b < 4; ++b)
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) T1[row * kLd + 64 * h + 16 * b + c] = __uint_as_float(ri[b][c]);
+                epi_sync();
+            }
+            for (int c2 = 64 * h; c2 < 64 * h + 64; c2 += 32) {  // two 16-column chunks per TMEM wait
+                uint32_t rr_[2][16], a1[2][16], a2[2][16], riv[2][16];
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const int cc = c2 + 16 * b;
+                    tmem_ld16(tl + cc, rr_[b]);
+                    if (diag) {
+                        tmem_ld16(tl + 256 + cc, a1[b]);  // ii
+                    } else {
+                        tmem_ld16(tl + 256 + cc, a2[b]);  // ir
+                        tmem_ld16(tl + 384 + cc, a1[b]);  // ii
+                        tmem_ld16(tl + 128 + cc, riv[b]);
+                    }
                 }
+                tmem_wait_ld();
+#pragma unroll
+                for (int b = 0; b < 2; ++b)
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        const int col = c2 + 16 * b + c;
+                        const float re = (__uint_as_float(rr_[b][c]) + __uint_as_float(a1[b][c])) * invT;
+                        float im;
+                        if (diag)
+                            im = (col == row) ? 0.f : (T1[col * kLd + row] - T1[row * kLd + col]) * invT;
+                        else
+                            im = (__uint_as_float(a2[b][c]) - __uint_as_float(riv[b][c])) * invT;
+                        S[row * kLd + col] = make_float2(re, im);
+                    }
             }
             epi_sync();
             if (it.split < 0) {
