@@ -1093,8 +1093,12 @@ __device__ void orthonormalize_cols_d(float2* Z, int n, int k, const Sm& sm) {
         if (i != j) sm.Gd[j * k + i] = zpack(zd{g.re, dd_neg(g.im)});
     }
     __syncthreads();
-    chol_d(sm.Gd, k, sm);
-    trinv_d(sm.Gd, sm.part, k, sm);
+    if (2 * k * k <= n * n) {  // the elimination's scratch fits in part beside the inverse
+        chol_inv_d(sm.Gd, sm.part, sm.part + k * k, k, sm);
+    } else {
+        chol_d(sm.Gd, k, sm);
+        trinv_d(sm.Gd, sm.part, k, sm);
+    }
     apply_upper_d(Z, n, k, sm.part);
 }
 
