@@ -395,6 +395,60 @@ std::vector<int> longest_first(const std::vector<int64_t>& w) {
     return order;
 }
 
+// Second launch order, for batches of a few waves: the SMs in two lanes, one running
+// the off-diagonal tiles and one the cheaper diagonal tiles, each lane list-scheduled
+// in frame order, the lane sizes balancing the two makespans.  The items launch in the
+// order of their planned start times (lane by lane at equal times), so the SM that
+// frees up next takes the next item of its own lane.  Equal frames then reach the
+// packing bound where the frame order leaves a last partial wave: 64 frames of
+// M = 512 on 152 SMs give 96 SMs four off-diagonal tiles each and 56 SMs four or five
+// diagonal ones (simulated makespan 1280 against 1408 quarter stages).
+void order_in_lanes(std::vector<fm::CovItem>& tiles, std::vector<int64_t>& w, int n_sm) {
+    std::vector<int> ia, ib;
+    for (size_t i = 0; i < tiles.size(); ++i) (tiles[i].ti != tiles[i].tj ? ia : ib).push_back((int)i);
+    if (ia.empty() || ib.empty() || n_sm < 2) return;
+    auto lane = [&](const std::vector<int>& idx, int nsm, std::vector<int64_t>* starts) {
+        std::vector<int64_t> wl(idx.size()), ends;
+        for (size_t k = 0; k < idx.size(); ++k) wl[k] = w[idx[k]] + kCovCtaCost;
+        const int64_t mk = lpt_makespan(wl, nsm, starts ? &ends : nullptr);
+        if (starts) {
+            starts->resize(idx.size());
+            for (size_t k = 0; k < idx.size(); ++k) (*starts)[k] = ends[k] - wl[k];
+        }
+        return mk;
+    };
+    auto both = [&](int na) { return std::max(lane(ia, na, nullptr), lane(ib, n_sm - na, nullptr)); };
+    // the smallest lane a whose makespan is at most lane b's (a's shrinks, b's grows with na)
+    int lo = 1, hi = n_sm - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (lane(ia, mid, nullptr) <= lane(ib, n_sm - mid, nullptr))
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    int na = lo;
+    if (lo > 1 && both(lo - 1) < both(lo)) na = lo - 1;
+    std::vector<int64_t> sa_, sb_;
+    lane(ia, na, &sa_);
+    lane(ib, n_sm - na, &sb_);
+    std::vector<std::tuple<int64_t, int, int>> ev;
+    ev.reserve(tiles.size());
+    for (size_t k = 0; k < ia.size(); ++k) ev.emplace_back(sa_[k], 0, ia[k]);
+    for (size_t k = 0; k < ib.size(); ++k) ev.emplace_back(sb_[k], 1, ib[k]);
+    std::sort(ev.begin(), ev.end());
+    std::vector<fm::CovItem> t2;
+    std::vector<int64_t> w2;
+    t2.reserve(tiles.size());
+    w2.reserve(tiles.size());
+    for (const auto& e : ev) {
+        t2.push_back(tiles[std::get<2>(e)]);
+        w2.push_back(w[std::get<2>(e)]);
+    }
+    tiles.swap(t2);
+    w.swap(w2);
+}
+
 CovPlan plan_cov_items(const fm_frame* f, int n, int n_sm, bool allow_split) {
     // frames by total tile work, largest first (ties in the caller's order)
     std::vector<int64_t> fw(n);
@@ -416,6 +470,17 @@ CovPlan plan_cov_items(const fm_frame* f, int n, int n_sm, bool allow_split) {
         for (int ti = 0; ti < nt; ++ti) {
             tiles.push_back(fm::CovItem{b, ti, ti, 0, ns, -1, 0, 0, 1});
             w.push_back((int64_t)ns * 3);
+        }
+    }
+    if (n_sm > 1 && (int64_t)tiles.size() <= 8 * (int64_t)n_sm) {
+        std::vector<fm::CovItem> t2 = tiles;
+        std::vector<int64_t> w2 = w, wo1(w.size()), wo2;
+        order_in_lanes(t2, w2, n_sm);
+        for (size_t i = 0; i < w.size(); ++i) wo1[i] = w[i] + kCovCtaCost;
+        for (int64_t x : w2) wo2.push_back(x + kCovCtaCost);
+        if ((double)lpt_makespan(wo2, n_sm) < 0.99 * (double)lpt_makespan(wo1, n_sm)) {
+            tiles.swap(t2);
+            w.swap(w2);
         }
     }
     CovPlan plan;
