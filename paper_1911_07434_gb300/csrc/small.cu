@@ -133,8 +133,7 @@ struct Sm {
     float2* Vs;    // Mr x l   rows of V (FINAL, until H is formed)
     float4* Gd;    // l x l    double-float Gram / Cholesky factor   (aliases Vs)
     float4* Xd;    // l x l    double-float inverse                  (aliases Vs)
-    float2* Gf;    // l x l    FP32 Gram / Cholesky factor           (aliases Vs)
-    float2* Xf;    // l x l    FP32 inverse                          (aliases Vs)
+    float2* Xf;    // l x l    FP32 scratch of the one-sided Jacobi  (aliases Gd)
     float4* part;  // l x l    per-CTA partial Gram (float4 or float2 view)
     float2* T;     // l x l    temp                                  (aliases part)
     float2* Rc;    // l x l    R factor of C = Q R_c
@@ -183,7 +182,6 @@ __host__ __device__ inline size_t smem_layout(int Mr, int l, Sm* sm, char* base)
         sm->Vs = reinterpret_cast<float2*>(U1);
         sm->Gd = reinterpret_cast<float4*>(U1);
         sm->Xd = reinterpret_cast<float4*>(U1) + ll;
-        sm->Gf = reinterpret_cast<float2*>(U1);
         sm->Xf = reinterpret_cast<float2*>(U1) + ll;
         sm->part = reinterpret_cast<float4*>(part);
         sm->T = reinterpret_cast<float2*>(part);
@@ -302,28 +300,8 @@ __device__ void gram_part_d(const float2* A, int rows, int l, float4* part) {
     }
 }
 
-// Sum the cluster's partials (rank order) into out (l x l, full).  herm: the
-// partials hold the upper triangle and out receives the Hermitian matrix.
-__device__ void reduce_f(cg::cluster_group& cl, float2* part, float2* out, int l, bool herm) {
-    const int n = herm ? l * (l + 1) / 2 : l * l;
-    const unsigned nc = cl.num_blocks();
-    cl.sync();
-    for (int e = threadIdx.x; e < n; e += kThreads) {
-        float2 s = make_float2(0.f, 0.f);
-        for (unsigned r = 0; r < nc; ++r) s = cadd(s, cl.map_shared_rank(part, r)[e]);
-        if (herm) {
-            int i, j;
-            tri_coords(e, l, i, j);
-            if (i == j) s.y = 0.f;
-            out[i * l + j] = s;
-            if (i != j) out[j * l + i] = cconj(s);
-        } else {
-            out[e] = s;
-        }
-    }
-    cl.sync();
-}
-
+// Sum the cluster's double-float partials (upper triangle, rank order) into the
+// Hermitian out (l x l).
 __device__ void reduce_d(cg::cluster_group& cl, float4* part, float4* out, int l) {
     const int n = l * (l + 1) / 2;
     const unsigned nc = cl.num_blocks();
@@ -340,54 +318,33 @@ __device__ void reduce_d(cg::cluster_group& cl, float4* part, float4* out, int l
     cl.sync();
 }
 
-// ------------------------------------------------------ Cholesky / inverse --
-// In place, G = R^H R with R upper (FP32).  Returns false on a non-positive pivot.
-// floor_rel > 0 (CholeskyQR of a sketch): a pivot below floor_rel x the largest
-// diagonal entry, i.e. a numerically rank-deficient C, is raised to that floor, so
-// Q = C R^{-1} stays finite and spans range(C); only a non-finite pivot fails.
-// floor_rel = 0 (the core matrix H): any non-positive pivot fails.
-__device__ bool chol_f(float2* G, int l, const Sm& sm, float floor_rel = 0.f) {
-    if (threadIdx.x == 0) {
-        sm.flags[kMaxSweeps + 4] = 0;
-        float dmax = 0.f;
-        for (int k = 0; k < l; ++k) dmax = fmaxf(dmax, G[k * l + k].x);
-        sm.scal[2] = floor_rel * dmax;
-    }
-    __syncthreads();
-    const float dfloor = sm.scal[2];
-    for (int k = 0; k < l; ++k) {
-        if (threadIdx.x == 0) {
-            float d = G[k * l + k].x;
-            if (!isfinite(d) || (floor_rel == 0.f && !(d > 0.f))) {
-                sm.flags[kMaxSweeps + 4] = 1;
-                d = 1e-30f;
-            } else if (!(d > dfloor)) {
-                d = dfloor > 0.f ? dfloor : 1e-30f;
-            }
-            const float r = sqrtf(d);
-            G[k * l + k] = make_float2(r, 0.f);
-            sm.scal[0] = 1.f / r;
+// The sums of full l x l FP32 partials (pf -> of) and of double-float upper-triangle
+// partials (pd -> od, as reduce_d) over the cluster in rank order, in one pass between
+// one pair of cluster barriers.
+__device__ void reduce_fd(cg::cluster_group& cl, float2* pf, float2* of, float4* pd, float4* od, int l) {
+    const int nf = l * l, nd = l * (l + 1) / 2;
+    const unsigned nc = cl.num_blocks();
+    cl.sync();
+    for (int e = threadIdx.x; e < nf + nd; e += kThreads) {
+        if (e < nf) {
+            float2 s = make_float2(0.f, 0.f);
+            for (unsigned r = 0; r < nc; ++r) s = cadd(s, cl.map_shared_rank(pf, r)[e]);
+            of[e] = s;
+        } else {
+            const int u = e - nf;
+            zd s = zload(cl.map_shared_rank(pd, 0u)[u]);
+            for (unsigned r = 1; r < nc; ++r) s = zadd(s, zload(cl.map_shared_rank(pd, r)[u]));
+            int i, j;
+            tri_coords(u, l, i, j);
+            if (i == j) s.im = df{0.f, 0.f};
+            od[i * l + j] = zpack(s);
+            if (i != j) od[j * l + i] = zpack(zd{s.re, dd_neg(s.im)});
         }
-        __syncthreads();
-        const float inv = sm.scal[0];
-        for (int j = k + 1 + threadIdx.x; j < l; j += kThreads) G[k * l + j] = cscale(G[k * l + j], inv);
-        __syncthreads();
-        const int n = l - k - 1;
-        for (int e = threadIdx.x; e < n * n; e += kThreads) {
-            const int i = k + 1 + e / n, j = k + 1 + e % n;
-            if (i <= j) {
-                const float2 a = G[k * l + i], b = G[k * l + j];
-                G[i * l + j] = csub(G[i * l + j], cmulc(a, b));
-            }
-        }
-        __syncthreads();
     }
-    for (int e = threadIdx.x; e < l * l; e += kThreads)
-        if (e / l > e % l) G[e] = make_float2(0.f, 0.f);
-    __syncthreads();
-    return sm.flags[kMaxSweeps + 4] == 0;
+    cl.sync();
 }
 
+// ------------------------------------------------------ Cholesky / inverse --
 // Pivots below 2^-40 x the largest diagonal entry (a numerically rank-deficient
 // sketch) are raised to that floor; only a non-finite pivot fails.
 __device__ bool chol_d(float4* G, int l, const Sm& sm) {
@@ -434,25 +391,6 @@ __device__ bool chol_d(float4* G, int l, const Sm& sm) {
 // X = R^{-1}, R upper with real positive diagonal; right-looking back
 // substitution (row i finalised as (delta_ij - S_ij)/R_ii, then R_ki X_ij added to
 // the partial sums S_kj of all rows k < i in parallel).
-__device__ void trinv_f(const float2* R, float2* X, int l) {
-    for (int e = threadIdx.x; e < l * l; e += kThreads) X[e] = make_float2(0.f, 0.f);
-    __syncthreads();
-    for (int i = l - 1; i >= 0; --i) {
-        const float inv = 1.f / R[i * l + i].x;
-        for (int j = i + threadIdx.x; j < l; j += kThreads) {
-            const float2 s = X[i * l + j];
-            X[i * l + j] = make_float2((((j == i) ? 1.f : 0.f) - s.x) * inv, -s.y * inv);
-        }
-        __syncthreads();
-        const int w = l - i;
-        for (int e = threadIdx.x; e < i * w; e += kThreads) {
-            const int k = e / w, j = i + e % w;
-            cfma(X[k * l + j], R[k * l + i], X[i * l + j]);
-        }
-        __syncthreads();
-    }
-}
-
 __device__ void trinv_d(const float4* R, float4* X, int l, const Sm& sm) {
     for (int e = threadIdx.x; e < l * l; e += kThreads) X[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
@@ -572,58 +510,119 @@ __device__ bool chol_inv_d(float4* G, float4* X, float4* Aw, int l, const Sm& sm
     return sm.flags[kMaxSweeps + 4] == 0;
 }
 
-// FP32, any non-positive pivot fails (the core matrix H: W then falls back to the
-// eigenvalue pseudo-inverse).  G (in place) becomes R (upper, zero below), X = R^{-1}.
-__device__ bool chol_inv_f(float2* G, float2* X, float2* Aw, int l, const Sm& sm) {
-    if (threadIdx.x == 0) sm.flags[kMaxSweeps + 4] = 0;
+// The double-float sweep of chol_inv_d on the Gram of C and the same sweep in FP32 on
+// the core matrix H, side by side: the two chains are independent until
+// F = R_c R_h^{-1}, so each column phase takes the tasks of both behind one barrier --
+// double-float tasks from the low thread indices, FP32 tasks from the high ones, so
+// that a thread takes both only while the double-float phase still fills the block --
+// and the FP32 sweep adds no barriers of its own.  Gd becomes R_c and Xd = R_c^{-1}
+// (false on a non-finite pivot, pivots floored as in chol_inv_d); Gf becomes R_h and
+// the upper triangle of XEf R_h^{-1}, where any non-positive pivot sets *pd false (W
+// then falls back to the eigenvalue pseudo-inverse of H).  The FP32 E shares XEf with
+// the inverse: E is unit lower triangular (its diagonal is never stored) and its row k
+// is read in the phase that writes column k of the inverse above the diagonal.
+__device__ bool chol_inv_pair(float4* Gd, float4* Xd, float4* Awd, float2* Gf, float2* XEf, int l, const Sm& sm,
+                              bool* pd) {
+    if (threadIdx.x == 0) {
+        sm.flags[kMaxSweeps + 4] = 0;
+        sm.flags[kMaxSweeps + 5] = 0;
+        float dmax = 0.f;
+        for (int k = 0; k < l; ++k) dmax = fmaxf(dmax, Gd[k * l + k].x);
+        sm.scal[2] = 0x1p-40f * dmax;
+    }
     for (int e = threadIdx.x; e < l * l; e += kThreads) {
-        Aw[e] = make_float2((e / l == e % l) ? 1.f : 0.f, 0.f);
-        X[e] = make_float2(0.f, 0.f);
+        const float one = (e / l == e % l) ? 1.f : 0.f;
+        Awd[e] = make_float4(one, 0.f, 0.f, 0.f);
+        Xd[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        XEf[e] = make_float2(0.f, 0.f);
     }
     __syncthreads();
-    float rprev = 0.f;
+    const float dfloor = sm.scal[2];
+    df rprev{0.f, 0.f};
+    float rprevf = 0.f;
     for (int k = 0; k < l; ++k) {
-        if (k > 0 && threadIdx.x == 0) G[(k - 1) * l + k - 1] = make_float2(rprev, 0.f);
-        float d = G[k * l + k].x;
-        const bool bad = !isfinite(d) || !(d > 0.f);
-        if (bad) d = 1e-30f;
-        const float r = sqrtf(d);
-        const float inv = 1.f / r;
+        // the previous pivots' R entries: every thread has read them by now
+        if (k > 0 && threadIdx.x == 0) Gd[(k - 1) * l + k - 1] = make_float4(rprev.hi, rprev.lo, 0.f, 0.f);
+        if (k > 0 && threadIdx.x == kThreads - 1) Gf[(k - 1) * l + k - 1] = make_float2(rprevf, 0.f);
+        df d = zload(Gd[k * l + k]).re;
+        const bool bad = !isfinite(d.hi);
+        if (bad) {
+            d = df{1e-30f, 0.f};
+        } else if (!(d.hi > dfloor)) {
+            d = df{dfloor > 0.f ? dfloor : 1e-30f, 0.f};
+        }
+        const df r = dd_sqrt(d);
+        const df inv = dd_div(df{1.f, 0.f}, r);
         if (bad && threadIdx.x == 0) sm.flags[kMaxSweeps + 4] = 1;
         rprev = r;
+        float dff = Gf[k * l + k].x;
+        const bool badf = !isfinite(dff) || !(dff > 0.f);
+        if (badf) dff = 1e-30f;
+        const float rf = sqrtf(dff);
+        const float invf = 1.f / rf;
+        if (badf && threadIdx.x == kThreads - 1) sm.flags[kMaxSweeps + 5] = 1;
+        rprevf = rf;
         const int n = l - k - 1;
-        const int nt = ((n + 1) / 2) * (n + 1);
-        const int na = n * (k + 1);
-        const int ntot = nt + na + n + k + 1;
+        const int nt = ((n + 1) / 2) * (n + 1);  // trailing upper-triangle slots
+        const int na = n * (k + 1);              // E entries of the rows below
+        const int ntot = nt + na + n + k + 1;    // + R row k (right of the pivot) + E row k
         for (int t = threadIdx.x; t < ntot; t += kThreads) {
             if (t < nt) {
                 int a, b;
                 if (!trailing_slot(t, n, a, b)) continue;
                 const int i = k + 1 + a, j = k + 1 + b;
-                G[i * l + j] = csub(G[i * l + j], cmulc(cscale(G[k * l + i], inv), cscale(G[k * l + j], inv)));
+                const zd ri = zscale(zload(Gd[k * l + i]), inv), rj = zscale(zload(Gd[k * l + j]), inv);
+                Gd[i * l + j] = zpack(zadd(zload(Gd[i * l + j]), zneg(zmulc(ri, rj))));
             } else if (t < nt + na) {
                 const int u = t - nt, a = u / (k + 1), m = u - a * (k + 1);
                 const int i = k + 1 + a;
-                Aw[i * l + m] = csub(Aw[i * l + m], cmulc(cscale(G[k * l + i], inv), cscale(Aw[k * l + m], inv)));
+                const zd ri = zscale(zload(Gd[k * l + i]), inv), em = zscale(zload(Awd[k * l + m]), inv);
+                Awd[i * l + m] = zpack(zadd(zload(Awd[i * l + m]), zneg(zmulc(ri, em))));
             } else if (t < nt + na + n) {
                 const int j = k + 1 + (t - nt - na);
-                G[j * l + k] = cscale(G[k * l + j], inv);
+                Gd[j * l + k] = zpack(zscale(zload(Gd[k * l + j]), inv));  // R[k][j], parked
             } else {
                 const int m = t - nt - na - n;
-                X[m * l + k] = cconj(cscale(Aw[k * l + m], inv));
+                const zd em = zscale(zload(Awd[k * l + m]), inv);
+                Xd[m * l + k] = zpack(zd{em.re, dd_neg(em.im)});
+            }
+        }
+        for (int t = kThreads - 1 - threadIdx.x; t < ntot; t += kThreads) {
+            if (t < nt) {
+                int a, b;
+                if (!trailing_slot(t, n, a, b)) continue;
+                const int i = k + 1 + a, j = k + 1 + b;
+                Gf[i * l + j] = csub(Gf[i * l + j], cmulc(cscale(Gf[k * l + i], invf), cscale(Gf[k * l + j], invf)));
+            } else if (t < nt + na) {
+                const int u = t - nt, a = u / (k + 1), m = u - a * (k + 1);
+                const int i = k + 1 + a;
+                const float2 ekm = (m == k) ? make_float2(1.f, 0.f) : XEf[k * l + m];
+                XEf[i * l + m] = csub(XEf[i * l + m], cmulc(cscale(Gf[k * l + i], invf), cscale(ekm, invf)));
+            } else if (t < nt + na + n) {
+                const int j = k + 1 + (t - nt - na);
+                Gf[j * l + k] = cscale(Gf[k * l + j], invf);
+            } else {
+                const int m = t - nt - na - n;
+                const float2 ekm = (m == k) ? make_float2(1.f, 0.f) : XEf[k * l + m];
+                XEf[m * l + k] = cconj(cscale(ekm, invf));
             }
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) G[(l - 1) * l + l - 1] = make_float2(rprev, 0.f);
+    if (threadIdx.x == 0) Gd[(l - 1) * l + l - 1] = make_float4(rprev.hi, rprev.lo, 0.f, 0.f);
+    if (threadIdx.x == kThreads - 1) Gf[(l - 1) * l + l - 1] = make_float2(rprevf, 0.f);
+    // R's rows back above the diagonal, zeros below
     for (int e = threadIdx.x; e < l * l; e += kThreads) {
         const int i = e / l, j = e % l;
         if (i < j) {
-            G[e] = G[j * l + i];
-            G[j * l + i] = make_float2(0.f, 0.f);
+            Gd[e] = Gd[j * l + i];
+            Gd[j * l + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            Gf[e] = Gf[j * l + i];
+            Gf[j * l + i] = make_float2(0.f, 0.f);
         }
     }
     __syncthreads();
+    *pd = sm.flags[kMaxSweeps + 5] == 0;
     return sm.flags[kMaxSweeps + 4] == 0;
 }
 
@@ -1179,19 +1178,30 @@ __global__ void __launch_bounds__(kThreads, 3) small_cluster_kernel(const FrameD
     // sampling without power steps: H = C(I, :) (Alg. 1); after a refinement step the
     // sketch is V-based as in Alg. 2, so H = V^H C
     const bool sampled0 = (dp->method == FM_RAND_SAMPLING && dp->t == 0 && !dp->refine);
+    // C = Q R_c with Q = C R_c^{-1} left implicit: R_c from the double-float Gram of C
+    // (Cholesky, pivot floor as in CholeskyQR), X = R_c^{-1} kept in Xd until U_s = C (X W)
+    // is formed at the end for the ncols selected eigenvectors W only.  U_s^H U_s =
+    // W^H X^H (C^H C) X W = W^H W up to double-float rounding, so one pass gives the
+    // orthonormality of a second CholeskyQR pass without forming Q.  The Gram partials
+    // of H (in Z) and of C (in part) are summed over the cluster in one pass; V rows are
+    // dead once H is formed (Gd aliases them).
     if (!sampled0) {
         load_rows(dp->V, sm.Vs, r0, rows, l);
         __syncthreads();
-        gram_part_f(sm.Vs, sm.Cs, rows, l, false, reinterpret_cast<float2*>(sm.part));
-        reduce_f(cl, reinterpret_cast<float2*>(sm.part), sm.H, l, false);
+        gram_part_f(sm.Vs, sm.Cs, rows, l, false, sm.Z);
+        gram_part_d(sm.Cs, rows, l, sm.part);
+        reduce_fd(cl, sm.Z, sm.H, sm.part, sm.Gd, l);
     } else {
         for (int e = threadIdx.x; e < l * l; e += kThreads) {
             const int i = e / l, j = e % l;
             sm.H[e] = dp->C[(int64_t)dp->idx[i] * l + j];
         }
         __syncthreads();
+        gram_part_d(sm.Cs, rows, l, sm.part);
+        reduce_d(cl, sm.part, sm.Gd, l);
     }
-    // exact Hermitian part
+    // exact Hermitian part, kept in H and copied to Z (the FP32 sweep below factors Z in
+    // place; H stays for the pseudo-inverse branch)
     for (int e = threadIdx.x; e < l * l; e += kThreads) {
         const int i = e / l, j = e % l;
         if (i < j) {
@@ -1199,37 +1209,29 @@ __global__ void __launch_bounds__(kThreads, 3) small_cluster_kernel(const FrameD
             const float2 h = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
             sm.H[i * l + j] = h;
             sm.H[j * l + i] = cconj(h);
+            sm.Z[i * l + j] = h;
+            sm.Z[j * l + i] = cconj(h);
         } else if (i == j) {
             sm.H[e].y = 0.f;
+            sm.Z[e] = make_float2(sm.H[e].x, 0.f);
         }
     }
     __syncthreads();
 
-    // C = Q R_c with Q = C R_c^{-1} left implicit: R_c from the double-float Gram of C
-    // (Cholesky, pivot floor as in CholeskyQR), X = R_c^{-1} kept in Xd until U_s = C (X W)
-    // is formed at the end for the ncols selected eigenvectors W only.  U_s^H U_s =
-    // W^H X^H (C^H C) X W = W^H W up to double-float rounding, so one pass gives the
-    // orthonormality of a second CholeskyQR pass without forming Q.  V rows are dead
-    // from here on.
-    gram_part_d(sm.Cs, rows, l, sm.part);
-    reduce_d(cl, sm.part, sm.Gd, l);
-    bool ok = chol_inv_d(sm.Gd, sm.Xd, sm.part, l, sm);  // part is free after the reduction
-    for (int e = threadIdx.x; e < l * l; e += kThreads) {
-        const float4 g = sm.Gd[e];
-        sm.Rc[e] = make_float2(g.x + g.y, g.z + g.w);
-    }
-    __syncthreads();  // Gf (next) aliases Gd
-
-    // B = R_c H^+ R_c^H
-    for (int e = threadIdx.x; e < l * l; e += kThreads) sm.Gf[e] = sm.H[e];
-    __syncthreads();
-    const bool pd = chol_inv_f(sm.Gf, sm.Xf, reinterpret_cast<float2*>(sm.part), l, sm);
+    // B = R_c H^+ R_c^H: in the same column sweep as R_c and X (part is free after the
+    // reduction), H = R_h^H R_h in FP32 (in Z) with R_h^{-1} into Rc
+    bool pd;
+    bool ok = chol_inv_pair(sm.Gd, sm.Xd, sm.part, sm.Z, sm.Rc, l, sm, &pd);
     if (pd) {
-        // F = R_c R_h^{-1} (upper) into T, B = F F^H into H
+        // F = R_c R_h^{-1} (upper, R_c rounded to FP32; R_h^{-1} from the upper triangle of
+        // Rc) into T, B = F F^H into H
         for (int e = threadIdx.x; e < l * l; e += kThreads) {
             const int i = e / l, j = e % l;
             float2 s = make_float2(0.f, 0.f);
-            for (int k = i; k <= j; ++k) cfma(s, sm.Rc[i * l + k], sm.Xf[k * l + j]);
+            for (int k = i; k <= j; ++k) {
+                const float4 g = sm.Gd[i * l + k];
+                cfma(s, make_float2(g.x + g.y, g.z + g.w), sm.Rc[k * l + j]);
+            }
             sm.T[e] = s;
         }
         __syncthreads();
@@ -1257,7 +1259,10 @@ __global__ void __launch_bounds__(kThreads, 3) small_cluster_kernel(const FrameD
         for (int e = threadIdx.x; e < l * l; e += kThreads) {
             const int i = e / l, k = e % l;
             float2 s = make_float2(0.f, 0.f);
-            for (int m = i; m < l; ++m) cfma(s, sm.Rc[i * l + m], sm.Z[m * l + k]);
+            for (int m = i; m < l; ++m) {
+                const float4 g = sm.Gd[i * l + m];
+                cfma(s, make_float2(g.x + g.y, g.z + g.w), sm.Z[m * l + k]);
+            }
             sm.T[e] = s;
         }
         __syncthreads();
@@ -1279,7 +1284,7 @@ __global__ void __launch_bounds__(kThreads, 3) small_cluster_kernel(const FrameD
     // Jacobi on B
     int s2;
     if (pd) {
-        s2 = eig_onesided(sm.T, sm.Xf, sm.Z, sm.w, sm.perm, l, sm, cap);  // Xf is free after F was formed
+        s2 = eig_onesided(sm.T, sm.Xf, sm.Z, sm.w, sm.perm, l, sm, cap);  // Gd (under Xf) is dead once F is formed
         for (int e = threadIdx.x; e < l * l; e += kThreads) sm.T[e] = sm.H[e];
         __syncthreads();
     } else {
