@@ -449,7 +449,7 @@ void order_in_lanes(std::vector<fm::CovItem>& tiles, std::vector<int64_t>& w, in
     w.swap(w2);
 }
 
-CovPlan plan_cov_items(const fm_frame* f, int n, int n_sm, bool allow_split) {
+CovPlan plan_cov_items_uncached(const fm_frame* f, int n, int n_sm, bool allow_split) {
     // frames by total tile work, largest first (ties in the caller's order)
     std::vector<int64_t> fw(n);
     for (int b = 0; b < n; ++b) {
@@ -472,7 +472,7 @@ CovPlan plan_cov_items(const fm_frame* f, int n, int n_sm, bool allow_split) {
             w.push_back((int64_t)ns * 3);
         }
     }
-    if (n_sm > 1 && (int64_t)tiles.size() <= 8 * (int64_t)n_sm) {
+    if (n_sm > 1 && (int64_t)tiles.size() > n_sm && (int64_t)tiles.size() <= 8 * (int64_t)n_sm) {
         std::vector<fm::CovItem> t2 = tiles;
         std::vector<int64_t> w2 = w, wo1(w.size()), wo2;
         order_in_lanes(t2, w2, n_sm);
@@ -533,6 +533,28 @@ CovPlan plan_cov_items(const fm_frame* f, int n, int n_sm, bool allow_split) {
         }
         ++plan.n_split;
         plan.n_slots += best_s;
+    }
+    return plan;
+}
+
+// The plan depends only on each frame's M and T (in the order given), the SM count and
+// allow_split; a caller that repeats its batch shape (a stream of equal batches, the
+// serving slots) gets the last plan of its thread back without the simulations, which
+// take a few hundred microseconds of host time for a 64-frame batch.
+CovPlan plan_cov_items(const fm_frame* f, int n, int n_sm, bool allow_split) {
+    thread_local std::vector<int64_t> key;
+    thread_local CovPlan plan;
+    std::vector<int64_t> k;
+    k.reserve(2 * (size_t)n + 2);
+    k.push_back(n_sm);
+    k.push_back(allow_split ? 1 : 0);
+    for (int b = 0; b < n; ++b) {
+        k.push_back(f[b].arr.M);
+        k.push_back(f[b].T);
+    }
+    if (k != key) {
+        plan = plan_cov_items_uncached(f, n, n_sm, allow_split);
+        key.swap(k);
     }
     return plan;
 }
