@@ -25,6 +25,8 @@ struct FrameDesc {
     int scan_tc;       // 1: scanned by the tensor-core kernel (then main lobes by the fixup scan)
     int sketch_tc;     // 1: the tensor-core sketch is prepared for this frame (Bsk, tensor maps)
     int sweep_cap;     // Jacobi sweeps allowed in the l x l eigensolves (0: the solver's own cap)
+    int bsk_orth_nc;   // > 0: the power-step orthonormalisation (clusters of this many CTAs)
+                       // writes the B rows of the tensor-core sketch passes >= 1 itself
     float2* R;         // M x M
     float2* C;         // M x l  sketch
     float2* V;         // M x l  basis (power steps) / Q
@@ -277,9 +279,16 @@ cudaError_t launch_final(const FrameDesc* d, int n_frames, int max_M, int max_l,
 cudaError_t launch_refine(const FrameDesc* d, int n_frames, int max_M, int max_T, cudaStream_t s);
 cudaError_t launch_wait_timeout(int* status, long long limit_cycles, cudaStream_t s);
 cudaError_t launch_scatter(const CopyEntry* tab, int n, cudaStream_t s);
+// prep: launch the B-row preparation (false when the orthonormalisation before this pass
+// wrote every frame's B rows)
 cudaError_t launch_sketch_tc(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, bool any_plain,
                              bool any_split, const void* tmA, const void* tmB, const void* tmA_split,
-                             const void* tmB_split, cudaStream_t s);
+                             const void* tmB_split, cudaStream_t s, bool prep = true);
+// Cluster size of the l x l kernels for a launch over n_frames frames (small.cu).
+int orth_cluster_size(int max_M, int max_l, int n_frames);
+// Whether a frame's rows split into whole 8-entry chunks of the split B layout over nc
+// CTAs of ceil(M / nc) rows each (then each CTA writes the B rows of its own rows).
+__host__ __device__ inline bool brows_by_cluster(int M, int nc) { return nc == 1 || ((M + nc - 1) / nc) % 8 == 0; }
 size_t sketch_tc_smem_bytes(int max_l, bool split);
 // smem_elems: the largest M * (scan_row_stride(kpad, KP) + (positions ? 1 : 0)) over the
 // frames, KP = scan_kp_class(the launch's largest kpad) (float2 elements of shared memory

@@ -917,7 +917,8 @@ enum : char { kPassPlain = 1, kPassSplit = 2, kPassDense = 4 };
 // B rows, n over R in raw boxes, n over the split B rows.  Without them every
 // product runs on the CUDA cores.
 fm_status run_subspace_chain(fm_ctx* c, FrameDesc* dd, int n, const Maxes& mx, cudaStream_t s,
-                             const char* sk_maps = nullptr, const std::vector<char>* tc_pass = nullptr) {
+                             const char* sk_maps = nullptr, const std::vector<char>* tc_pass = nullptr,
+                             bool prep_late = true) {
     auto sketch = [&](int p) {
         const bool tc = sk_maps && tc_pass;
         const char bits = tc ? (*tc_pass)[p] : (char)((p > 0 || mx.any_projection) ? kPassDense : 0);
@@ -929,7 +930,7 @@ fm_status run_subspace_chain(fm_ctx* c, FrameDesc* dd, int n, const Maxes& mx, c
         if (e == cudaSuccess && (bits & (kPassPlain | kPassSplit))) {
             const size_t m = sizeof(CUtensorMap) * (size_t)n;
             e = fm::launch_sketch_tc(dd, n, mx.M, mx.l, p, (bits & kPassPlain) != 0, (bits & kPassSplit) != 0, sk_maps,
-                                     sk_maps + m, sk_maps + 2 * m, sk_maps + 3 * m, s);
+                                     sk_maps + m, sk_maps + 2 * m, sk_maps + 3 * m, s, p == 0 || prep_late);
         }
         return e;
     };
@@ -1065,6 +1066,7 @@ struct RunPrep {
     bool cov_tc = false, scan_tc = false, scan_simt = true, any_repack = false;
     std::vector<char> group_tc;  // per scan group: runs on the tensor cores
     std::vector<char> tc_pass;   // per sketch pass: kPass* bits of the kernels it needs
+    bool prep_late = true;       // a tensor-core frame needs the B-row kernel at passes >= 1
     FrameDesc* dd = nullptr;
     GridDesc* dg = nullptr;
 };
@@ -1119,10 +1121,17 @@ static fm_status prepare_run(fm_ctx* c, const fm_frame* frames, int n, cudaStrea
     memset(skmaps.data(), 0, sizeof(CUtensorMap) * skmaps.size());
     rp.tc_pass.assign(9, 0);
     int n_sk_tc = 0, n_sk_any = 0;
+    // the power-step orthonormalisation writes the B rows of passes >= 1 where its clusters
+    // split the frame's rows into whole chunks of the split layout
+    const Maxes mx0 = maxes_of(ds);
+    const int onc = mx0.t >= 1 ? fm::orth_cluster_size(mx0.M, mx0.l, n) : 0;
+    rp.prep_late = false;
     for (int k = 0; k < n; ++k) {
         FrameDesc& d = ds[k];
         if (d.sketch_tc && !encode_sketch_tmaps(d, &skmaps[k], &skmaps[n + k], &skmaps[2 * n + k], &skmaps[3 * n + k]))
             d.sketch_tc = 0;  // the CUDA-core sketch takes every pass of this frame
+        d.bsk_orth_nc = (d.sketch_tc && d.t >= 1 && onc > 0 && fm::brows_by_cluster(d.M, onc)) ? onc : 0;
+        if (d.sketch_tc && d.t >= 1 && d.bsk_orth_nc == 0) rp.prep_late = true;
         bool has_product = false;
         for (int p = 0; p <= d.t; ++p) {
             if (!fm::sketch_on_tc(d.method, p)) continue;  // sampling, pass 0: a gather
@@ -1189,7 +1198,7 @@ static fm_status enqueue_run(fm_ctx* c, const RunPrep& rp, cudaStream_t s) {
                     s);
     if (st != FM_OK) return st;
     st = run_subspace_chain(c, dd, n, mx, s, c->arena + pl.tmap_off + sizeof(CUtensorMap) * 2 * (size_t)n,
-                            &rp.tc_pass);
+                            &rp.tc_pass, rp.prep_late);
     if (st != FM_OK) return st;
     st = stage(c, kStScan, s, [&] {
         if (rp.scan_simt) {  // frames without a tensor-core group (the kernel skips the others)

@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(kBpThreads) sketch_bprep_kernel(const FrameDes
     __shared__ float2 vt[kBpRows * kBpLd];
     const FrameDesc* dp = descs + blockIdx.y;
     if (!dp->sketch_tc || pass > dp->t || !sketch_on_tc(dp->method, pass)) return;
+    if (pass > 0 && dp->bsk_orth_nc > 0) return;  // written by the orthonormalisation
     const int M = dp->M, l = dp->l, lp = sketch_tc_lpad(l);
     const int m0 = blockIdx.x * kBpRows;
     if (m0 >= M) return;
@@ -516,12 +517,15 @@ size_t sketch_tc_smem_bytes(int max_l, bool split) {
 
 cudaError_t launch_sketch_tc(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, bool any_plain,
                              bool any_split, const void* tmA, const void* tmB, const void* tmA_split,
-                             const void* tmB_split, cudaStream_t s) {
+                             const void* tmB_split, cudaStream_t s, bool prep) {
     const int lp = sketch_tc_lpad(max_l), nb_max = 2 * lp;
-    count_launch();
-    launch_pdl(sketch_bprep_kernel, dim3(dim3((unsigned)((max_M + kBpRows - 1) / kBpRows), n_frames)), dim3(kBpThreads), (size_t)(0), s, d, pass);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (prep) {
+        count_launch();
+        launch_pdl(sketch_bprep_kernel, dim3(dim3((unsigned)((max_M + kBpRows - 1) / kBpRows), n_frames)), dim3(kBpThreads), (size_t)(0), s, d, pass);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     const dim3 grid((unsigned)((max_M + kRows - 1) / kRows), n_frames);
     if (any_plain) {
         const int smem = (int)sketch_tc_smem_bytes(max_l, false);

@@ -41,6 +41,7 @@
 #include <float.h>
 
 #include "fm_internal.cuh"
+#include "tc_common.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -1140,6 +1141,56 @@ __device__ void apply_d(const float2* A, float2* __restrict__ dst, int rows, int
     }
 }
 
+// B rows of the next tensor-core sketch pass from this CTA's rows of V (rows x l in
+// shared memory, entries r0 .. r0 + rows - 1), in the layout sketch_bprep_kernel writes:
+// plain, rows [Vr, -Vi] and [Vi, Vr] rounded to TF32 at 2m; split, chunks of 8 entries
+// (16 values) as [hi 16 | lo 16], hi = rn_tf32(v), lo = rn_tf32(v - hi).  r0 is a multiple
+// of 8 (brows_by_cluster), so the CTA owns whole chunks; the last chunk's entries past M
+// are written as zeros.
+__device__ void write_brows(const FrameDesc* dp, const float2* Vs, int r0, int rows, int pass) {
+    const int M = dp->M, l = dp->l, nrow = 2 * sketch_tc_lpad(l);
+    if (!sketch_split(dp->prec, dp->t, pass)) {
+        const int64_t rowlen = 2 * (int64_t)M;
+        for (int t = threadIdx.x; t < nrow * rows; t += kThreads) {
+            const int R = t / rows, r = t - R * rows, j = R >> 1;
+            const float2 v = j < l ? Vs[r * l + j] : make_float2(0.f, 0.f);
+            const float a = (R & 1) ? v.y : v.x, b = (R & 1) ? v.x : -v.y;
+            *reinterpret_cast<float2*>(dp->Bsk + R * rowlen + 2 * (int64_t)(r0 + r)) =
+                make_float2(__uint_as_float(tc::tf32_rn(a)), __uint_as_float(tc::tf32_rn(b)));
+        }
+        return;
+    }
+    // a row segment of chunk c is 8 pieces of 16 bytes: piece p < 4 holds the hi values
+    // of entries 8c + 2p and 8c + 2p + 1, piece p + 4 their lo values.  A thread takes one
+    // piece of both B rows of column j (re row 2j, im row 2j + 1: the same two entries).
+    const int64_t rowlen = sketch_split_rowlen(M);
+    const int nchunks = (2 * M + 15) / 16, c0 = r0 / 8, W = 8 * ((rows + 7) / 8);
+    for (int t = threadIdx.x; t < (nrow / 2) * W; t += kThreads) {
+        const int j = t / W, q = t - j * W, cc = q >> 3, p = q & 7;
+        const int c = c0 + cc;
+        if (c >= nchunks) continue;
+        const int ra = 8 * cc + 2 * (p & 3);
+        float2 va = make_float2(0.f, 0.f), vb = va;
+        if (j < l) {
+            if (ra < rows) va = Vs[ra * l + j];
+            if (ra + 1 < rows) vb = Vs[(ra + 1) * l + j];
+        }
+        const float xr[4] = {va.x, -va.y, vb.x, -vb.y}, xi[4] = {va.y, va.x, vb.y, vb.x};
+        uint4 orr, oi;
+        uint32_t* vr = reinterpret_cast<uint32_t*>(&orr);
+        uint32_t* vi = reinterpret_cast<uint32_t*>(&oi);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t hr = tc::tf32_rn(xr[u]), hi = tc::tf32_rn(xi[u]);
+            vr[u] = p < 4 ? hr : tc::tf32_rn(xr[u] - __uint_as_float(hr));
+            vi[u] = p < 4 ? hi : tc::tf32_rn(xi[u] - __uint_as_float(hi));
+        }
+        float* dst = dp->Bsk + (2 * j) * rowlen + 32 * (int64_t)c + 4 * p;
+        *reinterpret_cast<uint4*>(dst) = orr;
+        *reinterpret_cast<uint4*>(dst + rowlen) = oi;
+    }
+}
+
 // ---------------------------------------------------------------- kernel ----
 __global__ void __launch_bounds__(kThreads, 3) small_cluster_kernel(const FrameDesc* __restrict__ descs, int mode,
                                                                  int pass) {
@@ -1170,6 +1221,14 @@ __global__ void __launch_bounds__(kThreads, 3) small_cluster_kernel(const FrameD
         __syncthreads();
         const bool ok = cholqr_pass_d(cl, sm.Cs, rows, l, sm, sm.Rc);
         store_rows(sm.Cs, dp->V, r0, rows, l);
+        // the next sketch pass's B rows, straight from the rows in shared memory (the host
+        // planned this cluster size; any other would leave them unwritten)
+        if (pass >= 1 && dp->bsk_orth_nc > 0) {
+            if (dp->bsk_orth_nc == nc && brows_by_cluster(M, nc))
+                write_brows(dp, sm.Cs, r0, rows, pass);
+            else if (rank == 0 && threadIdx.x == 0)
+                set_status(dp->status, FM_ERR_CUDA);
+        }
         if (!ok && rank == 0 && threadIdx.x == 0) set_status(dp->status, FM_ERR_NO_CONVERGENCE);
         return;
     }
@@ -1395,6 +1454,8 @@ size_t small_smem_bytes(int max_M, int l) {
     const int nc = cluster_size_for(max_M);
     return smem_layout((max_M + nc - 1) / nc, l, nullptr, nullptr);
 }
+
+int orth_cluster_size(int max_M, int max_l, int n_frames) { return cluster_size_for(max_M, max_l, n_frames); }
 
 cudaError_t launch_orth(const FrameDesc* d, int n_frames, int max_M, int max_l, int pass, cudaStream_t s) {
     return launch_small(d, n_frames, max_M, max_l, kOrth, pass, s);
