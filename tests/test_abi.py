@@ -89,3 +89,28 @@ def test_array_positions_are_validated_and_sized_on_the_host(lib):
     both = binding.fm_workspace_bytes([g1, g2])
     p2[3] += 0.25
     assert binding.fm_workspace_bytes([g1, g2]) >= both + 64 * 8
+
+
+def test_covariance_plan_follows_the_batch_shape(lib):
+    """The covariance work plan is kept per host thread for a repeated batch shape (each
+    frame's M and T); sizing a batch must not depend on which batch was sized before it.
+    One M = 512 frame splits its tiles along T (partial-tile workspace), a 64-frame batch
+    does not, and a frame whose T differs changes the split stages."""
+    one = [_frame(M=512, T=1024, K=8, l=24, L=15001)]
+    many = [_frame(M=512, T=1024, K=8, l=24, L=15001, X=4096 * (i + 1)) for i in range(64)]
+    other_t = [_frame(M=512, T=1040, K=8, l=24, L=15001)]
+    w1 = binding.fm_workspace_bytes(one)
+    w64 = binding.fm_workspace_bytes(many)
+    wt = binding.fm_workspace_bytes(other_t)
+    assert w1 > 0 and w64 > 0 and wt > 0
+    for _ in range(2):
+        assert binding.fm_workspace_bytes(many) == w64
+        assert binding.fm_workspace_bytes(one) == w1
+        assert binding.fm_workspace_bytes(other_t) == wt
+        assert binding.fm_workspace_bytes(one) == w1
+    # the lone frame's split tiles need partial-tile workspace (at least 40 parts of
+    # 128 x 128 complex) that the frames of a 64-frame batch do not: a frame's own share
+    # is the step from 32 to 64 frames (the grid table is shared)
+    w32 = binding.fm_workspace_bytes(many[:32])
+    own = (w64 - w32) / 32
+    assert w1 - own >= 40 * 128 * 128 * 8
