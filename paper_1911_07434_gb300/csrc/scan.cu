@@ -135,15 +135,17 @@ __device__ __forceinline__ void store_spectrum(const FrameDesc* dp, int i, int M
 // u M ||U_s^H a||^2 and is biased, while the sums here stay far below that, so
 // near a peak, where M - ||U_s^H a||^2 cancels, the CUDA-core value is kept.
 // The tensor-core scan's epilogue lists those angles per frame (fix_list); CTA x of
-// the kFixCtas of a frame takes chunks x, x + kFixCtas, ... of kFixChunk entries (one
+// the fix_ctas(KP) of a frame takes chunks x, x + fix_ctas, ... of fix_chunk(KP) entries (one
 // U_s load serves them; a frame with a short list leaves the other CTAs idle).  Each
 // angle is shared by fix_groups(KP) warps, warp g taking the
 // m0 residue class g (all lanes of a warp read the same U_s row: a shared-memory
 // broadcast), and the partial c_k are summed in shared memory in a fixed order, so
 // an angle's value does not depend on where it sits in the list.
 __host__ __device__ constexpr int fix_groups(int kp) { return kp <= 8 ? 8 : (kp == 16 ? 4 : 2); }
-constexpr int kFixCtas = 8;
-constexpr int kFixChunk = 64;
+// one round of angles per chunk (32 angles for KP <= 8), chunks spread over the CTAs so
+// that one pass of a frame's CTAs covers 512 list entries
+__host__ __device__ constexpr int fix_chunk(int kp) { return kThreads / 32 / fix_groups(kp) * 32; }
+__host__ __device__ constexpr int fix_ctas(int kp) { return 512 / fix_chunk(kp); }
 
 // Usm (M x kp4, zero-padded columns) <- U_s (M x kp): float4 copies issued four at a
 // time when the layouts agree, else element by element.
@@ -184,9 +186,9 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restr
     __shared__ float2 s_red[FIXUP ? kThreads * 8 : 1];  // [warp][k % 8][lane]
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int n_all = 0;
-    if (FIXUP) {  // chunks x, x + kFixCtas, ... of kFixChunk entries of the frame's list
+    if (FIXUP) {  // chunks x, x + fix_ctas, ... of fix_chunk entries of the frame's list
         n_all = *dp->fix_count;
-        if ((int)blockIdx.x * kFixChunk >= n_all) return;
+        if ((int)blockIdx.x * fix_chunk(KP) >= n_all) return;
     }
     load_us(Us, Usm, M, kp, kp4);
     // element positions of a non-uniform array follow U_s in shared memory
@@ -210,7 +212,8 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const FrameDesc* __restr
     constexpr int kPerRound = kWarps / G * 32;   // angles per round
     const int g = w % G, grp = w / G;
     // uniform trip count: every thread reaches every __syncthreads
-    for (int base = (int)blockIdx.x * kFixChunk; base < n_all; base += kFixChunk * kFixCtas)
+    constexpr int kFixChunk = fix_chunk(KP);
+    for (int base = (int)blockIdx.x * kFixChunk; base < n_all; base += kFixChunk * fix_ctas(KP))
     for (int sub = 0; sub < kFixChunk; sub += kPerRound) {
         const int a = base + sub + grp * 32 + lane;
         const bool act = sub + grp * 32 + lane < kFixChunk && a < n_all;
@@ -258,7 +261,7 @@ cudaError_t launch_kp(const FrameDesc* d, int n_frames, int max_L, size_t smem_e
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    dim3 grid(FIXUP ? kFixCtas : (max_L + kThreads - 1) / kThreads, n_frames);
+    dim3 grid(FIXUP ? fix_ctas(KP) : (max_L + kThreads - 1) / kThreads, n_frames);
     count_launch();
     launch_pdl(scan_kernel<KP, NB, FIXUP>, dim3(grid), dim3(kThreads), (size_t)(smem), s, d);
     return cudaGetLastError();
